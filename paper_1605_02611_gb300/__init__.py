@@ -1,0 +1,225 @@
+"""Thin ctypes binding of libgbdmrg.so (C-ABI declared in include/gbdmrg.h).
+
+Argument marshalling only: every step of the DMRG hot path runs in the CUDA
+library.  Importing works without a GPU; using a context needs the built
+library and a CUDA device, and fails loudly otherwise (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgbdmrg.so")
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ETIMEOUT", 6: "EIO",
+          7: "ESMALL", 8: "ESTATE"}
+
+# exported symbol -> (restype, argtypes)
+_P = C.c_void_p
+_I32 = C.c_int32
+_PI32 = C.POINTER(C.c_int32)
+_PI64 = C.POINTER(C.c_int64)
+_PD = C.POINTER(C.c_double)
+
+
+class Problem(C.Structure):
+    _fields_ = [("K", C.c_int32), ("N", C.c_int32), ("two_sz", C.c_int32),
+                ("h1", _PD), ("eri", _PD), ("ecore", C.c_double)]
+
+
+class Schedule(C.Structure):
+    _fields_ = [("nsweeps", C.c_int32), ("M", _PI32), ("dav_tol", _PD), ("dav_max_iter", C.c_int32),
+                ("precision", C.c_int32)]
+
+
+SIGNATURES = {
+    "gbdmrg_create": (C.c_int, [C.POINTER(Problem), _P, C.POINTER(_P)]),
+    "gbdmrg_destroy": (None, [_P]),
+    "gbdmrg_last_error": (C.c_char_p, [_P]),
+    "gbdmrg_mpo_build_host": (C.c_int, [C.POINTER(Problem), _PI32, _PD]),
+    "gbdmrg_mpo_bond_dims": (C.c_int, [_P, _PI32]),
+    "gbdmrg_mpo_dense": (C.c_int, [_P, _PD]),
+    "gbdmrg_set_mps": (C.c_int, [_P, _I32, _I32, _I32, _PI32, _PI32, _PD]),
+    "gbdmrg_get_mps": (C.c_int, [_P, _I32, _PI32, _PI32, _PD]),
+    "gbdmrg_get_bond": (C.c_int, [_P, _I32, _PI32, _PI32]),
+    "gbdmrg_prepare": (C.c_int, [_P, _I32]),
+    "gbdmrg_psi_layout": (C.c_int, [_P, _PI64, _PI64, _PI64]),
+    "gbdmrg_sigma": (C.c_int, [_P, _P, _P, _I32, _PD]),
+    "gbdmrg_diag": (C.c_int, [_P, _P, _I32]),
+    "gbdmrg_sigma_timing": (C.c_int, [_P, _I32, _P, _P, _PD]),
+    "gbdmrg_run": (C.c_int, [_P, C.POINTER(Schedule), _PD, _PD]),
+    "gbdmrg_run_stats": (C.c_int, [_P, _PD, _PD, _PD, _PI32]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1605_02611_gb300.build.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class GbdmrgError(RuntimeError):
+    pass
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_PD)
+
+
+def mpo_build_host(h1, eri, N: int, two_sz: int = 0, dense: bool = False):
+    """Host-only MPO build (no GPU): returns (bond dims, dense matrix or None)."""
+    lib = load()
+    h1 = np.ascontiguousarray(h1, dtype=np.float64)
+    eri = np.ascontiguousarray(eri, dtype=np.float64)
+    K = h1.shape[0]
+    prob = Problem(K, N, two_sz, _dptr(h1), _dptr(eri), 0.0)
+    dims = np.zeros(K + 1, dtype=np.int32)
+    out = np.zeros((4 ** K, 4 ** K)) if dense else None
+    st = lib.gbdmrg_mpo_build_host(C.byref(prob), dims.ctypes.data_as(_PI32), _dptr(out) if dense else None)
+    if st != 0:
+        raise GbdmrgError(f"gbdmrg_mpo_build_host failed: {STATUS.get(st, st)}")
+    return dims, out
+
+
+class Context:
+    """One DMRG problem on the current CUDA device (gbdmrg_create)."""
+
+    def __init__(self, h1, eri, N: int, two_sz: int = 0, ecore: float = 0.0, stream: int | None = None):
+        self.lib = load()
+        h1 = np.ascontiguousarray(h1, dtype=np.float64)
+        eri = np.ascontiguousarray(eri, dtype=np.float64)
+        self.K = h1.shape[0]
+        self.N, self.two_sz = N, two_sz
+        self.Na, self.Nb = (N + two_sz) // 2, (N - two_sz) // 2
+        prob = Problem(self.K, N, two_sz, _dptr(h1), _dptr(eri), ecore)
+        h = _P()
+        st = self.lib.gbdmrg_create(C.byref(prob), _P(stream or 0), C.byref(h))
+        if st != 0:
+            raise GbdmrgError(f"gbdmrg_create failed: {STATUS.get(st, st)}")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gbdmrg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int, what: str):
+        if st != 0:
+            msg = self.lib.gbdmrg_last_error(self.h).decode()
+            raise GbdmrgError(f"{what}: {STATUS.get(st, st)}: {msg}")
+
+    # ---- MPO
+    def mpo_bond_dims(self) -> np.ndarray:
+        d = np.zeros(self.K + 1, dtype=np.int32)
+        self._check(self.lib.gbdmrg_mpo_bond_dims(self.h, d.ctypes.data_as(_PI32)), "mpo_bond_dims")
+        return d
+
+    def mpo_dense(self) -> np.ndarray:
+        out = np.zeros((4 ** self.K, 4 ** self.K))
+        self._check(self.lib.gbdmrg_mpo_dense(self.h, _dptr(out)), "mpo_dense")
+        return out
+
+    # ---- MPS
+    def set_mps(self, tensors, labels):
+        for k, A in enumerate(tensors):
+            A = np.ascontiguousarray(A, dtype=np.float64)
+            ql = np.ascontiguousarray(labels[k], dtype=np.int32).reshape(-1)
+            qr = np.ascontiguousarray(labels[k + 1], dtype=np.int32).reshape(-1)
+            self._check(self.lib.gbdmrg_set_mps(self.h, k, A.shape[0], A.shape[2], ql.ctypes.data_as(_PI32),
+                                                qr.ctypes.data_as(_PI32), _dptr(A)), f"set_mps({k})")
+
+    def get_mps(self, k: int) -> np.ndarray:
+        dl, dr = C.c_int32(), C.c_int32()
+        self._check(self.lib.gbdmrg_get_mps(self.h, k, C.byref(dl), C.byref(dr), None), "get_mps")
+        A = np.zeros((dl.value, 4, dr.value))
+        self._check(self.lib.gbdmrg_get_mps(self.h, k, C.byref(dl), C.byref(dr), _dptr(A)), "get_mps")
+        return A
+
+    def get_bond(self, b: int) -> np.ndarray:
+        d = C.c_int32()
+        self._check(self.lib.gbdmrg_get_bond(self.h, b, C.byref(d), None), "get_bond")
+        q = np.zeros((d.value, 2), dtype=np.int32)
+        self._check(self.lib.gbdmrg_get_bond(self.h, b, C.byref(d), q.ctypes.data_as(_PI32)), "get_bond")
+        return q
+
+    # ---- two-site problem
+    def prepare(self, k: int):
+        self._check(self.lib.gbdmrg_prepare(self.h, k), "prepare")
+        nb, nnz = C.c_int64(), C.c_int64()
+        self._check(self.lib.gbdmrg_psi_layout(self.h, C.byref(nb), C.byref(nnz), None), "psi_layout")
+        blk = np.zeros((nb.value, 7), dtype=np.int64)
+        self._check(self.lib.gbdmrg_psi_layout(self.h, C.byref(nb), C.byref(nnz), blk.ctypes.data_as(_PI64)),
+                    "psi_layout")
+        self.layout = blk
+        self.nnz = nnz.value
+        return blk
+
+    def pack(self, psi: np.ndarray) -> np.ndarray:
+        out = np.zeros(self.nnz)
+        for (l0, ld, n1, n2, r0, rd, off) in self.layout:
+            out[off:off + ld * rd] = psi[l0:l0 + ld, n1, n2, r0:r0 + rd].reshape(-1)
+        return out
+
+    def unpack(self, v: np.ndarray, shape) -> np.ndarray:
+        out = np.zeros(shape)
+        for (l0, ld, n1, n2, r0, rd, off) in self.layout:
+            out[l0:l0 + ld, n1, n2, r0:r0 + rd] = v[off:off + ld * rd].reshape(ld, rd)
+        return out
+
+    def sigma(self, psi_packed: np.ndarray):
+        x = np.ascontiguousarray(psi_packed, dtype=np.float64)
+        y = np.zeros_like(x)
+        fl = C.c_double()
+        self._check(self.lib.gbdmrg_sigma(self.h, x.ctypes.data_as(_P), y.ctypes.data_as(_P), 0, C.byref(fl)),
+                    "sigma")
+        return y, fl.value
+
+    def sigma_device(self, x_ptr: int, y_ptr: int) -> float:
+        fl = C.c_double()
+        self._check(self.lib.gbdmrg_sigma(self.h, _P(x_ptr), _P(y_ptr), 1, C.byref(fl)), "sigma")
+        return fl.value
+
+    def sigma_timing(self, reps: int, x_ptr: int, y_ptr: int) -> float:
+        ms = C.c_double()
+        self._check(self.lib.gbdmrg_sigma_timing(self.h, reps, _P(x_ptr), _P(y_ptr), C.byref(ms)), "sigma_timing")
+        return ms.value
+
+    def diag(self) -> np.ndarray:
+        d = np.zeros(self.nnz)
+        self._check(self.lib.gbdmrg_diag(self.h, d.ctypes.data_as(_P), 0), "diag")
+        return d
+
+    # ---- sweeps
+    def run(self, M, dav_tol, max_iter: int = 200):
+        M = np.ascontiguousarray(M, dtype=np.int32)
+        tol = np.ascontiguousarray(np.broadcast_to(dav_tol, M.shape), dtype=np.float64)
+        s = Schedule(len(M), M.ctypes.data_as(_PI32), _dptr(tol), max_iter, 0)
+        e = np.zeros(len(M))
+        d = np.zeros(len(M))
+        self._check(self.lib.gbdmrg_run(self.h, C.byref(s), _dptr(e), _dptr(d)), "run")
+        sec, fl, ss = np.zeros(len(M)), np.zeros(len(M)), np.zeros(len(M))
+        it = np.zeros(len(M), dtype=np.int32)
+        self._check(self.lib.gbdmrg_run_stats(self.h, _dptr(sec), _dptr(fl), _dptr(ss), it.ctypes.data_as(_PI32)),
+                    "run_stats")
+        return dict(energy=e, discarded=d, seconds=sec, sigma_flops=fl, sigma_seconds=ss, davidson_iters=it)

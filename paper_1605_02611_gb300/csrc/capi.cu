@@ -1,0 +1,297 @@
+// extern "C" boundary of the library (declarations and contracts: include/gbdmrg.h).
+#include <cmath>
+#include <cstring>
+#include <exception>
+#include <memory>
+
+#include "../../include/gbdmrg.h"
+#include "engine.hpp"
+
+struct gbdmrg_ctx {
+  gbdmrg::Context c;
+  gbdmrg::SweepStats stats;
+};
+
+namespace {
+
+template <class F>
+gbdmrg_status guard(gbdmrg_ctx* ctx, F&& f) {
+  try {
+    f();
+    if (ctx) ctx->c.last_error.clear();
+    return GBDMRG_OK;
+  } catch (const gbdmrg::Error& e) {
+    if (ctx) ctx->c.last_error = e.what();
+    return (gbdmrg_status)e.code;
+  } catch (const std::bad_alloc&) {
+    if (ctx) ctx->c.last_error = "host allocation failed";
+    return GBDMRG_ENOMEM;
+  } catch (const std::exception& e) {
+    if (ctx) ctx->c.last_error = e.what();
+    return GBDMRG_EINVAL;
+  } catch (...) {
+    if (ctx) ctx->c.last_error = "unknown error";
+    return GBDMRG_ECUDA;
+  }
+}
+
+void check_problem(const gbdmrg_problem* p) {
+  using gbdmrg::Error;
+  using gbdmrg::ST_EINVAL;
+  if (!p || !p->h1 || !p->eri) throw Error(ST_EINVAL, "null problem or integrals");
+  const int K = p->K;
+  if (K < 1 || K > 128) throw Error(ST_EINVAL, "K must be in [1, 128]");
+  if (p->N < 0 || p->N > 2 * K) throw Error(ST_EINVAL, "N must be in [0, 2K]");
+  if (((p->N + p->two_sz) & 1) != 0) throw Error(ST_EINVAL, "two_sz must have the parity of N");
+  int na = (p->N + p->two_sz) / 2, nb = (p->N - p->two_sz) / 2;
+  if (na < 0 || nb < 0 || na > K || nb > K) throw Error(ST_EINVAL, "S_z out of range");
+  if (!std::isfinite(p->ecore)) throw Error(ST_EINVAL, "non-finite ecore");
+  for (int i = 0; i < K; ++i)
+    for (int j = 0; j < K; ++j) {
+      double a = p->h1[i * K + j], b = p->h1[j * K + i];
+      if (!std::isfinite(a)) throw Error(ST_EINVAL, "non-finite h1");
+      if (std::fabs(a - b) > 1e-12 * (1 + std::fabs(a))) throw Error(ST_EINVAL, "h1 not symmetric");
+    }
+  auto E = [&](int a, int b, int c, int d) { return p->eri[((size_t)(a * K + b) * K + c) * K + d]; };
+  for (int a = 0; a < K; ++a)
+    for (int b = 0; b < K; ++b)
+      for (int c = 0; c < K; ++c)
+        for (int d = 0; d < K; ++d) {
+          double v = E(a, b, c, d);
+          if (!std::isfinite(v)) throw Error(ST_EINVAL, "non-finite eri");
+          double tol = 1e-12 * (1 + std::fabs(v));
+          if (std::fabs(v - E(b, a, c, d)) > tol || std::fabs(v - E(a, b, d, c)) > tol ||
+              std::fabs(v - E(c, d, a, b)) > tol)
+            throw Error(ST_EINVAL, "eri not 8-fold symmetric");
+        }
+}
+
+}  // namespace
+
+extern "C" {
+
+gbdmrg_status gbdmrg_create(const gbdmrg_problem* prob, void* stream, gbdmrg_ctx** out) {
+  if (!out) return GBDMRG_EINVAL;
+  *out = nullptr;
+  std::unique_ptr<gbdmrg_ctx> ctx;
+  try {
+    check_problem(prob);
+    ctx.reset(new gbdmrg_ctx());
+  } catch (const gbdmrg::Error& e) {
+    return (gbdmrg_status)e.code;
+  } catch (...) {
+    return GBDMRG_ENOMEM;
+  }
+  gbdmrg_status st = guard(ctx.get(), [&] {
+    auto& c = ctx->c;
+    c.K = prob->K;
+    c.N = prob->N;
+    c.two_sz = prob->two_sz;
+    c.Na = (prob->N + prob->two_sz) / 2;
+    c.Nb = (prob->N - prob->two_sz) / 2;
+    c.ecore = prob->ecore;
+    const size_t K = prob->K;
+    c.h1.assign(prob->h1, prob->h1 + K * K);
+    c.eri.assign(prob->eri, prob->eri + K * K * K * K);
+    c.stream = (cudaStream_t)stream;
+    gbdmrg::ctx_init(c);
+  });
+  if (st != GBDMRG_OK) return st;
+  *out = ctx.release();
+  return GBDMRG_OK;
+}
+
+void gbdmrg_destroy(gbdmrg_ctx* ctx) { delete ctx; }
+
+const char* gbdmrg_last_error(const gbdmrg_ctx* ctx) { return ctx ? ctx->c.last_error.c_str() : "null context"; }
+
+gbdmrg_status gbdmrg_mpo_build_host(const gbdmrg_problem* prob, int32_t* dims, double* dense) {
+  if (!dims) return GBDMRG_EINVAL;
+  return guard(nullptr, [&] {
+    check_problem(prob);
+    gbdmrg::MPO m = gbdmrg::build_mpo(prob->K, prob->h1, prob->eri);
+    for (int b = 0; b <= prob->K; ++b) dims[b] = (int32_t)m.bonds[b].size();
+    if (dense) {
+      if (prob->K > 5) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "dense MPO needs K <= 5");
+      std::vector<double> d;
+      gbdmrg::mpo_to_dense(m, d);
+      std::memcpy(dense, d.data(), d.size() * sizeof(double));
+    }
+  });
+}
+
+gbdmrg_status gbdmrg_mpo_bond_dims(gbdmrg_ctx* ctx, int32_t* dims) {
+  if (!ctx || !dims) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    for (int b = 0; b <= ctx->c.K; ++b) dims[b] = (int32_t)ctx->c.mpo.bonds[b].size();
+  });
+}
+
+gbdmrg_status gbdmrg_mpo_dense(gbdmrg_ctx* ctx, double* out) {
+  if (!ctx || !out) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    if (ctx->c.K > 5) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "gbdmrg_mpo_dense needs K <= 5");
+    std::vector<double> m;
+    gbdmrg::mpo_to_dense(ctx->c.mpo, m);
+    std::memcpy(out, m.data(), m.size() * sizeof(double));
+  });
+}
+
+gbdmrg_status gbdmrg_set_mps(gbdmrg_ctx* ctx, int32_t site, int32_t Dl, int32_t Dr, const int32_t* qn_l,
+                             const int32_t* qn_r, const double* A) {
+  if (!ctx || !qn_l || !qn_r || !A || Dl <= 0 || Dr <= 0) return GBDMRG_EINVAL;
+  return guard(ctx, [&] { gbdmrg::set_site_dense(ctx->c, site, Dl, Dr, qn_l, qn_r, A); });
+}
+
+gbdmrg_status gbdmrg_get_mps(gbdmrg_ctx* ctx, int32_t site, int32_t* Dl, int32_t* Dr, double* A) {
+  if (!ctx || !Dl || !Dr) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    auto& c = ctx->c;
+    if (site < 0 || site >= c.K || !c.site_set[site]) throw gbdmrg::Error(gbdmrg::ST_ESTATE, "site not set");
+    *Dl = c.sites[site].L.total;
+    *Dr = c.sites[site].R.total;
+    if (A) {
+      std::vector<double> d;
+      gbdmrg::get_site_dense(c, site, d);
+      std::memcpy(A, d.data(), d.size() * sizeof(double));
+    }
+  });
+}
+
+gbdmrg_status gbdmrg_get_bond(gbdmrg_ctx* ctx, int32_t bond, int32_t* D, int32_t* qn) {
+  if (!ctx || !D) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    auto& c = ctx->c;
+    if (bond < 0 || bond > c.K) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "bond out of range");
+    int s = bond < c.K ? bond : c.K - 1;
+    if (!c.site_set[s]) throw gbdmrg::Error(gbdmrg::ST_ESTATE, "site not set");
+    const gbdmrg::Bond& b = bond < c.K ? c.sites[s].L : c.sites[s].R;
+    *D = b.total;
+    if (qn)
+      for (int i = 0; i < b.nsec(); ++i)
+        for (int j = 0; j < b.dim[i]; ++j) {
+          qn[2 * (b.off[i] + j)] = b.qa[i];
+          qn[2 * (b.off[i] + j) + 1] = b.qb[i];
+        }
+  });
+}
+
+gbdmrg_status gbdmrg_prepare(gbdmrg_ctx* ctx, int32_t k) {
+  if (!ctx) return GBDMRG_EINVAL;
+  return guard(ctx, [&] { gbdmrg::prepare_two_site(ctx->c, k); });
+}
+
+gbdmrg_status gbdmrg_psi_layout(gbdmrg_ctx* ctx, int64_t* nblocks, int64_t* nnz, int64_t* blocks) {
+  if (!ctx || !nblocks || !nnz) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    auto& c = ctx->c;
+    if (c.prepared < 0) throw gbdmrg::Error(gbdmrg::ST_ESTATE, "call gbdmrg_prepare first");
+    const auto& P = c.plan.psi;
+    *nblocks = (int64_t)P.blocks.size();
+    *nnz = P.nnz;
+    if (blocks)
+      for (size_t i = 0; i < P.blocks.size(); ++i) {
+        const auto& b = P.blocks[i];
+        int64_t* r = blocks + 7 * i;
+        r[0] = P.L.off[b.rs];
+        r[1] = b.rows;
+        r[2] = P.b1[i];
+        r[3] = P.b2[i];
+        r[4] = P.R.off[b.cs];
+        r[5] = b.cols;
+        r[6] = b.off;
+      }
+  });
+}
+
+gbdmrg_status gbdmrg_sigma(gbdmrg_ctx* ctx, const double* psi, double* sigma, int32_t on_device, double* flops) {
+  if (!ctx || !psi || !sigma) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    auto& c = ctx->c;
+    if (c.prepared < 0) throw gbdmrg::Error(gbdmrg::ST_ESTATE, "call gbdmrg_prepare first");
+    auto& plan = c.plan;
+    const size_t bytes = plan.psi.nnz * sizeof(double);
+    if (on_device) {
+      gbdmrg::run_sigma(c, plan, psi, sigma);
+    } else {
+      gbdmrg::cuda_check(cudaMemcpyAsync(plan.in.p, psi, bytes, cudaMemcpyHostToDevice, c.stream), "h2d");
+      gbdmrg::run_sigma(c, plan, plan.in.p, plan.out.p);
+      gbdmrg::cuda_check(cudaMemcpyAsync(sigma, plan.out.p, bytes, cudaMemcpyDeviceToHost, c.stream), "d2h");
+    }
+    gbdmrg::cuda_check(cudaStreamSynchronize(c.stream), "sync");
+    if (flops) *flops = plan.flops;
+  });
+}
+
+gbdmrg_status gbdmrg_diag(gbdmrg_ctx* ctx, double* diag, int32_t on_device) {
+  if (!ctx || !diag) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    auto& c = ctx->c;
+    if (c.prepared < 0) throw gbdmrg::Error(gbdmrg::ST_ESTATE, "call gbdmrg_prepare first");
+    const auto& P = c.plan.psi;
+    if (on_device) {
+      gbdmrg::compute_diag(c, c.lt, c.rt, c.prepared, P, diag);
+    } else {
+      gbdmrg::DArr<double> d;
+      d.alloc(P.nnz, c.stream);
+      gbdmrg::compute_diag(c, c.lt, c.rt, c.prepared, P, d.p);
+      gbdmrg::cuda_check(cudaMemcpyAsync(diag, d.p, P.nnz * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "d2h");
+    }
+    gbdmrg::cuda_check(cudaStreamSynchronize(c.stream), "sync");
+  });
+}
+
+gbdmrg_status gbdmrg_sigma_timing(gbdmrg_ctx* ctx, int32_t reps, const double* psi_dev, double* sigma_dev,
+                                  double* ms_per_call) {
+  if (!ctx || !psi_dev || !sigma_dev || !ms_per_call || reps <= 0) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    auto& c = ctx->c;
+    if (c.prepared < 0) throw gbdmrg::Error(gbdmrg::ST_ESTATE, "call gbdmrg_prepare first");
+    cudaEvent_t e0, e1;
+    gbdmrg::cuda_check(cudaEventCreate(&e0), "event");
+    gbdmrg::cuda_check(cudaEventCreate(&e1), "event");
+    gbdmrg::cuda_check(cudaEventRecord(e0, c.stream), "record");
+    for (int r = 0; r < reps; ++r) gbdmrg::run_sigma(c, c.plan, psi_dev, sigma_dev);
+    gbdmrg::cuda_check(cudaEventRecord(e1, c.stream), "record");
+    gbdmrg::cuda_check(cudaEventSynchronize(e1), "sync");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_per_call = ms / reps;
+  });
+}
+
+gbdmrg_status gbdmrg_run(gbdmrg_ctx* ctx, const gbdmrg_schedule* s, double* energies, double* discarded) {
+  if (!ctx || !s || !energies || s->nsweeps <= 0 || !s->M || !s->dav_tol) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    for (int i = 0; i < s->nsweeps; ++i) {
+      if (s->M[i] <= 0) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "M must be positive");
+      if (!(s->dav_tol[i] > 0)) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "dav_tol must be positive");
+    }
+    if (s->precision != 0) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "only precision 0 (FP64) is supported");
+    ctx->stats = gbdmrg::SweepStats();
+    gbdmrg::run_sweeps(ctx->c, s->nsweeps, s->M, s->dav_tol, s->dav_max_iter > 0 ? s->dav_max_iter : 200,
+                       ctx->stats);
+    for (int i = 0; i < s->nsweeps; ++i) {
+      energies[i] = ctx->stats.energy[i];
+      if (discarded) discarded[i] = ctx->stats.discarded[i];
+    }
+  });
+}
+
+gbdmrg_status gbdmrg_run_stats(gbdmrg_ctx* ctx, double* seconds, double* sigma_flops, double* sigma_seconds,
+                               int32_t* iters) {
+  if (!ctx) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    const auto& st = ctx->stats;
+    for (size_t i = 0; i < st.energy.size(); ++i) {
+      if (seconds) seconds[i] = st.seconds[i];
+      if (sigma_flops) sigma_flops[i] = st.sigma_flops[i];
+      if (sigma_seconds) sigma_seconds[i] = st.sigma_seconds[i];
+      if (iters) iters[i] = st.davidson_iters[i];
+    }
+  });
+}
+
+}  // extern "C"

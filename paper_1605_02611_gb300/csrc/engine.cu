@@ -1,0 +1,1279 @@
+// Two-site DMRG engine (see engine.hpp).  Host code here only plans work
+// lists; every arithmetic step on the MPS, environments and wavefunctions runs
+// in the kernels of kernels.cu (cuSOLVER syevd serves the dense symmetric
+// eigenproblems of the decimation step).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+
+#include "engine.hpp"
+
+namespace gbdmrg {
+
+void cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return;
+  if (e == cudaErrorMemoryAllocation)
+    throw Error(ST_ENOMEM, std::string(what) + ": " + cudaGetErrorString(e));
+  throw Error(ST_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static void solver_check(cusolverStatus_t s, const char* what) {
+  if (s != CUSOLVER_STATUS_SUCCESS) throw Error(ST_ECUDA, std::string(what) + ": cusolver status " + std::to_string((int)s));
+}
+
+void* dev_alloc(size_t bytes, cudaStream_t s) {
+  void* p = nullptr;
+  if (bytes == 0) return nullptr;
+  cuda_check(cudaMallocAsync(&p, bytes, s), "cudaMallocAsync");
+  return p;
+}
+void dev_free(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+int Bond::find(int a, int b) const {
+  int lo = 0, hi = nsec() - 1;
+  while (lo <= hi) {
+    int mid = (lo + hi) >> 1;
+    if (qa[mid] == a && qb[mid] == b) return mid;
+    if (qa[mid] < a || (qa[mid] == a && qb[mid] < b)) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return -1;
+}
+
+void Bond::add(int a, int b, int d) {
+  qa.push_back(a);
+  qb.push_back(b);
+  dim.push_back(d);
+  off.push_back(total);
+  total += d;
+}
+
+OpLayout make_op_layout(const Bond& b, int da, int db) {
+  OpLayout L;
+  L.da = da;
+  L.db = db;
+  L.blk_of_col.assign(b.nsec(), -1);
+  long off = 0;
+  for (int j = 0; j < b.nsec(); ++j) {
+    int i = b.find(b.qa[j] + da, b.qb[j] + db);
+    if (i < 0) continue;
+    L.blk_of_col[j] = (int)L.blocks.size();
+    L.blocks.push_back({i, j, b.dim[i], b.dim[j], off});
+    off += (long)b.dim[i] * b.dim[j];
+  }
+  L.nnz = off;
+  return L;
+}
+
+size_t Env::bytes() const {
+  size_t s = 0;
+  for (size_t i = 0; i < cls.size(); ++i) s += (size_t)nslot[i] * cls[i].nnz * sizeof(double);
+  return s;
+}
+
+void SiteT::layout(const Bond& l, const Bond& r) {
+  L = l;
+  R = r;
+  blocks.clear();
+  bn.clear();
+  lookup.assign((size_t)l.nsec() * 4, -1);
+  long off = 0;
+  for (int ql = 0; ql < l.nsec(); ++ql)
+    for (int n = 0; n < 4; ++n) {
+      int qr = r.find(l.qa[ql] + LQA[n], l.qb[ql] + LQB[n]);
+      if (qr < 0) continue;
+      lookup[ql * 4 + n] = (int)blocks.size();
+      blocks.push_back({ql, qr, l.dim[ql], r.dim[qr], off});
+      bn.push_back(n);
+      off += (long)l.dim[ql] * r.dim[qr];
+    }
+  nnz = off;
+}
+
+void PsiLayout::build(const Bond& l, const Bond& r, int sa, int sb) {
+  L = l;
+  R = r;
+  da = sa;
+  db = sb;
+  blocks.clear();
+  b1.clear();
+  b2.clear();
+  lookup.assign((size_t)l.nsec() * 16, -1);
+  long off = 0;
+  for (int ql = 0; ql < l.nsec(); ++ql)
+    for (int n1 = 0; n1 < 4; ++n1)
+      for (int n2 = 0; n2 < 4; ++n2) {
+        int qr = r.find(l.qa[ql] + LQA[n1] + LQA[n2] + sa, l.qb[ql] + LQB[n1] + LQB[n2] + sb);
+        if (qr < 0) continue;
+        lookup[(ql * 4 + n1) * 4 + n2] = (int)blocks.size();
+        blocks.push_back({ql, qr, l.dim[ql], r.dim[qr], off});
+        b1.push_back(n1);
+        b2.push_back(n2);
+        off += (long)l.dim[ql] * r.dim[qr];
+      }
+  nnz = off;
+}
+
+// ---------------------------------------------------------------- GEMM plans
+
+int GemmBuilder::begin(double* C, int ldc, int m, int n, int beta) {
+  tasks.push_back({C, ldc, m, n, beta, (int)terms.size(), (int)terms.size()});
+  return (int)tasks.size() - 1;
+}
+
+void GemmBuilder::term(const double* A, int lda, const double* B, int ldb, int k, int flags, double alpha,
+                       int m, int n) {
+  if (k <= 0 || m <= 0 || n <= 0) return;
+  terms.push_back({A, B, lda, ldb, k, flags, alpha});
+  tasks.back().t1 = (int)terms.size();
+  flops += 2.0 * m * n * k;
+}
+
+void GemmBuilder::end() {
+  GemmTask& t = tasks.back();
+  if (t.t1 == t.t0) {
+    tasks.pop_back();
+    return;
+  }
+  int idx = (int)tasks.size() - 1;
+  for (int r0 = 0; r0 < t.m; r0 += GEMM_TM)
+    for (int c0 = 0; c0 < t.n; c0 += GEMM_TN) tiles.push_back({idx, r0, c0});
+}
+
+void GemmPlan::upload(const std::vector<GemmTile>& ti, const std::vector<GemmTask>& ta,
+                      const std::vector<GemmTerm>& te, cudaStream_t s) {
+  tiles.upload(ti, s);
+  tasks.upload(ta, s);
+  terms.upload(te, s);
+  ntiles = (int)ti.size();
+}
+
+void GemmPlan::run(cudaStream_t s) const {
+  if (ntiles == 0) return;
+  launch_gemm(tiles.p, ntiles, tasks.p, terms.p, s);
+  cuda_check(cudaGetLastError(), "gemm launch");
+}
+
+static void run_builder(Context& c, GemmBuilder& g) {
+  if (g.tasks.empty()) return;
+  GemmPlan p;
+  p.upload(g.tiles, g.tasks, g.terms, c.stream);
+  p.run(c.stream);
+  // host vectors must outlive the async upload: synchronise before they go
+  cuda_check(cudaStreamSynchronize(c.stream), "sync");
+}
+
+static void run_copies(Context& c, const std::vector<CopyJob>& jobs) {
+  if (jobs.empty()) return;
+  int mx = 0;
+  for (auto& j : jobs) mx = std::max(mx, j.rows * j.cols);
+  DArr<CopyJob> d;
+  d.upload(jobs, c.stream);
+  launch_copy(d.p, (int)jobs.size(), mx, c.stream);
+  cuda_check(cudaGetLastError(), "copy launch");
+  cuda_check(cudaStreamSynchronize(c.stream), "sync");
+}
+
+// ---------------------------------------------------------------- context
+
+Context::~Context() {
+  left.clear();
+  right.clear();
+  sites.clear();
+  lt.combo.release();
+  rt.combo.release();
+  plan = SigmaPlan();
+  if (stream) cudaStreamSynchronize(stream);
+  if (solver) cusolverDnDestroy(solver);
+  if (own_stream && stream) cudaStreamDestroy(stream);
+}
+
+void ctx_init(Context& c) {
+  if (!c.stream) {
+    cuda_check(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking), "stream create");
+    c.own_stream = true;
+  }
+  int dev = 0;
+  cuda_check(cudaGetDevice(&dev), "get device");
+  cudaMemPool_t pool;
+  cuda_check(cudaDeviceGetDefaultMemPool(&pool, dev), "mem pool");
+  uint64_t thr = UINT64_MAX;
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  solver_check(cusolverDnCreate(&c.solver), "cusolverDnCreate");
+  solver_check(cusolverDnSetStream(c.solver, c.stream), "cusolverDnSetStream");
+  c.mpo = build_mpo(c.K, c.h1.data(), c.eri.data());
+  c.sites.resize(c.K);
+  c.site_set.assign(c.K, false);
+  c.left.resize(c.K + 1);
+  c.right.resize(c.K + 1);
+}
+
+static Bond bond_from_labels(int D, const int* qn) {
+  Bond b;
+  int i = 0;
+  while (i < D) {
+    int a = qn[2 * i], bb = qn[2 * i + 1];
+    int j = i;
+    while (j < D && qn[2 * j] == a && qn[2 * j + 1] == bb) ++j;
+    if (b.nsec() && (a < b.qa.back() || (a == b.qa.back() && bb <= b.qb.back())))
+      throw Error(ST_EINVAL, "bond labels must be grouped and sorted by (n_alpha, n_beta)");
+    b.add(a, bb, j - i);
+    i = j;
+  }
+  return b;
+}
+
+static bool same_bond(const Bond& x, const Bond& y) {
+  return x.qa == y.qa && x.qb == y.qb && x.dim == y.dim;
+}
+
+void set_site_dense(Context& c, int k, int Dl, int Dr, const int* qn_l, const int* qn_r, const double* A) {
+  if (k < 0 || k >= c.K) throw Error(ST_EINVAL, "site out of range");
+  Bond l = bond_from_labels(Dl, qn_l), r = bond_from_labels(Dr, qn_r);
+  if (k == 0 && !(l.nsec() == 1 && l.qa[0] == 0 && l.qb[0] == 0 && l.dim[0] == 1))
+    throw Error(ST_EINVAL, "left boundary bond must be one state with (0,0)");
+  if (k == c.K - 1 && !(r.nsec() == 1 && r.qa[0] == c.Na && r.qb[0] == c.Nb && r.dim[0] == 1))
+    throw Error(ST_EINVAL, "right boundary bond must be one state with (N_alpha, N_beta)");
+  if (k > 0 && c.site_set[k - 1] && !same_bond(c.sites[k - 1].R, l))
+    throw Error(ST_EINVAL, "left bond does not match the right bond of the previous site");
+  if (k + 1 < c.K && c.site_set[k + 1] && !same_bond(c.sites[k + 1].L, r))
+    throw Error(ST_EINVAL, "right bond does not match the left bond of the next site");
+  SiteT& s = c.sites[k];
+  s.layout(l, r);
+  std::vector<double> h(s.nnz, 0.0);
+  for (size_t b = 0; b < s.blocks.size(); ++b) {
+    const Block& B = s.blocks[b];
+    int n = s.bn[b];
+    for (int i = 0; i < B.rows; ++i)
+      for (int j = 0; j < B.cols; ++j) {
+        double v = A[((size_t)(l.off[B.rs] + i) * 4 + n) * Dr + r.off[B.cs] + j];
+        if (!std::isfinite(v)) throw Error(ST_EINVAL, "non-finite MPS entry");
+        h[B.off + (long)i * B.cols + j] = v;
+      }
+  }
+  s.d.upload(h, c.stream);
+  cuda_check(cudaStreamSynchronize(c.stream), "sync");
+  c.site_set[k] = true;
+  c.prepared = -1;
+}
+
+void get_site_dense(Context& c, int k, std::vector<double>& A) {
+  SiteT& s = c.sites[k];
+  std::vector<double> h(s.nnz);
+  if (s.nnz) cuda_check(cudaMemcpy(h.data(), s.d.p, s.nnz * sizeof(double), cudaMemcpyDeviceToHost), "d2h");
+  int Dl = s.L.total, Dr = s.R.total;
+  A.assign((size_t)Dl * 4 * Dr, 0.0);
+  for (size_t b = 0; b < s.blocks.size(); ++b) {
+    const Block& B = s.blocks[b];
+    int n = s.bn[b];
+    for (int i = 0; i < B.rows; ++i)
+      for (int j = 0; j < B.cols; ++j)
+        A[((size_t)(s.L.off[B.rs] + i) * 4 + n) * Dr + s.R.off[B.cs] + j] = h[B.off + (long)i * B.cols + j];
+  }
+}
+
+// ---------------------------------------------------------------- environments
+
+static void env_alloc(Context& c, Env& e, const Bond& b, const std::vector<BondState>& st) {
+  e = Env();
+  e.bond = b;
+  std::map<std::pair<int, int>, int> cmap;
+  e.st_cls.assign(st.size(), -1);
+  e.st_slot.assign(st.size(), -1);
+  for (size_t i = 0; i < st.size(); ++i) {
+    auto key = std::make_pair(st[i].dna, st[i].dnb);
+    auto it = cmap.find(key);
+    int ci;
+    if (it == cmap.end()) {
+      ci = (int)e.cls.size();
+      cmap[key] = ci;
+      e.cls.push_back(make_op_layout(b, key.first, key.second));
+      e.nslot.push_back(0);
+    } else ci = it->second;
+    e.st_cls[i] = ci;
+    e.st_slot[i] = e.nslot[ci]++;
+  }
+  e.data.resize(e.cls.size());
+  for (size_t ci = 0; ci < e.cls.size(); ++ci) {
+    size_t n = (size_t)e.nslot[ci] * e.cls[ci].nnz;
+    e.data[ci].alloc(n, c.stream);
+    if (n) cuda_check(cudaMemsetAsync(e.data[ci].p, 0, n * sizeof(double), c.stream), "memset");
+  }
+  e.valid = true;
+}
+
+void env_boundary_left(Context& c, Env& e) {
+  Bond b;
+  b.add(0, 0, 1);
+  env_alloc(c, e, b, c.mpo.bonds[0]);
+  int I = c.mpo.state_I(0);
+  double one = 1.0;
+  cuda_check(cudaMemcpyAsync(e.op(I), &one, sizeof(double), cudaMemcpyHostToDevice, c.stream), "h2d");
+  cuda_check(cudaStreamSynchronize(c.stream), "sync");
+}
+
+void env_boundary_right(Context& c, Env& e) {
+  Bond b;
+  b.add(c.Na, c.Nb, 1);
+  env_alloc(c, e, b, c.mpo.bonds[c.K]);
+  int H = c.mpo.state_H(c.K);
+  double one = 1.0;
+  cuda_check(cudaMemcpyAsync(e.op(H), &one, sizeof(double), cudaMemcpyHostToDevice, c.stream), "h2d");
+  cuda_check(cudaStreamSynchronize(c.stream), "sync");
+}
+
+// lists[beta*16 + nn] = (env state, coefficient) pairs -> references / combinations
+static void finish_tilde(Context& c, Env& env, std::vector<std::vector<std::pair<int, double>>>& lists,
+                         Tilde& t) {
+  t.env = &env;
+  t.ref.assign(t.nmid, {});
+  size_t total = 0;
+  std::vector<long> off(lists.size(), -1);
+  for (size_t i = 0; i < lists.size(); ++i) {
+    auto& L = lists[i];
+    if (L.empty()) continue;
+    int cls = env.st_cls[L[0].first];
+    for (auto& pr : L)
+      if (env.st_cls[pr.first] != cls) throw Error(ST_ECUDA, "internal: mixed operator classes in a blocking sum");
+    if (L.size() > 1) {
+      off[i] = (long)total;
+      total += env.cls[cls].nnz;
+    }
+  }
+  t.combo.alloc(total, c.stream);
+  std::vector<ComboOut> outs;
+  std::vector<ComboTerm> terms;
+  long mx = 0;
+  t.combo_flops = 0;
+  for (size_t i = 0; i < lists.size(); ++i) {
+    auto& L = lists[i];
+    if (L.empty()) continue;
+    int cls = env.st_cls[L[0].first];
+    TRef& r = t.ref[i / 16][i % 16];
+    r.cls = cls;
+    if (L.size() == 1) {
+      r.p = env.op(L[0].first);
+      r.coef = L[0].second;
+    } else {
+      r.p = t.combo.p + off[i];
+      r.coef = 1.0;
+      ComboOut o{t.combo.p + off[i], env.cls[cls].nnz, (int)terms.size(), 0};
+      for (auto& pr : L) terms.push_back({env.op(pr.first), pr.second});
+      o.t1 = (int)terms.size();
+      outs.push_back(o);
+      mx = std::max(mx, o.nnz);
+      t.combo_flops += 2L * (long)L.size() * o.nnz;
+    }
+  }
+  if (!outs.empty()) {
+    DArr<ComboOut> d_o;
+    DArr<ComboTerm> d_t;
+    d_o.upload(outs, c.stream);
+    d_t.upload(terms, c.stream);
+    launch_combo(d_o.p, (int)outs.size(), mx, d_t.p, c.stream);
+    cuda_check(cudaGetLastError(), "combo launch");
+    cuda_check(cudaStreamSynchronize(c.stream), "sync");
+  }
+}
+
+void build_tilde_left(Context& c, Env& L, int site, Tilde& t) {
+  t.nmid = (int)c.mpo.bonds[site + 1].size();
+  std::vector<std::vector<std::pair<int, double>>> lists((size_t)t.nmid * 16);
+  for (const auto& e : c.mpo.W[site])
+    for (int nn = 0; nn < 16; ++nn)
+      if (e.m[nn] != 0.0) lists[(size_t)e.col * 16 + nn].push_back({e.row, e.m[nn]});
+  finish_tilde(c, L, lists, t);
+}
+
+void build_tilde_right(Context& c, Env& R, int site, Tilde& t) {
+  t.nmid = (int)c.mpo.bonds[site].size();
+  std::vector<std::vector<std::pair<int, double>>> lists((size_t)t.nmid * 16);
+  for (const auto& e : c.mpo.W[site])
+    for (int nn = 0; nn < 16; ++nn)
+      if (e.m[nn] != 0.0) lists[(size_t)e.row * 16 + nn].push_back({e.col, e.m[nn]});
+  finish_tilde(c, R, lists, t);
+}
+
+// column sector of a W-contracted operator block whose row sector is `row`
+static inline int tilde_col(const Bond& b, const OpLayout& L, int row) {
+  return b.find(b.qa[row] - L.da, b.qb[row] - L.db);
+}
+
+static size_t budget_elems(Context& c) { return (size_t)c.chunk_budget_mb * (1u << 20) / sizeof(double); }
+
+void env_update_left(Context& c, Tilde& lt, const SiteT& A, int site, Env& out) {
+  const auto& st = c.mpo.bonds[site + 1];
+  const Bond& Lb = A.L;
+  const Bond& Rb = A.R;
+  Env& Lenv = *lt.env;
+  env_alloc(c, out, Rb, st);
+  const int nR = Rb.nsec();
+  // intermediate sizes per state
+  std::vector<size_t> tsz(st.size(), 0);
+  for (size_t beta = 0; beta < st.size(); ++beta)
+    for (int n1 = 0; n1 < 4; ++n1)
+      for (int j = 0; j < nR; ++j) {
+        int ql = Lb.find(Rb.qa[j] + st[beta].dna - LQA[n1], Rb.qb[j] + st[beta].dnb - LQB[n1]);
+        if (ql >= 0) tsz[beta] += (size_t)Lb.dim[ql] * Rb.dim[j];
+      }
+  size_t budget = budget_elems(c);
+  size_t b0 = 0;
+  while (b0 < st.size()) {
+    size_t b1 = b0, tot = 0;
+    while (b1 < st.size() && (b1 == b0 || tot + tsz[b1] <= budget)) tot += tsz[b1++];
+    DArr<double> T;
+    T.alloc(tot, c.stream);
+    GemmBuilder g1, g2;
+    size_t toff = 0;
+    for (size_t beta = b0; beta < b1; ++beta) {
+      std::vector<long> tpos((size_t)4 * nR, -1);
+      for (int n1 = 0; n1 < 4; ++n1)
+        for (int j = 0; j < nR; ++j) {
+          int ql = Lb.find(Rb.qa[j] + st[beta].dna - LQA[n1], Rb.qb[j] + st[beta].dnb - LQB[n1]);
+          if (ql < 0) continue;
+          int m = Lb.dim[ql], n = Rb.dim[j];
+          g1.begin(T.p + toff, n, m, n, 0);
+          for (int n1p = 0; n1p < 4; ++n1p) {
+            const TRef& r = lt.ref[beta][n1 * 4 + n1p];
+            if (!r.p) continue;
+            const OpLayout& Lay = Lenv.cls[r.cls];
+            int qlp = tilde_col(Lb, Lay, ql);
+            if (qlp < 0) continue;
+            int bl = Lay.blk_of_col[qlp];
+            if (bl < 0 || Lay.blocks[bl].rs != ql) continue;
+            int ab = A.blk(qlp, n1p);
+            if (ab < 0 || A.blocks[ab].cs != j) continue;
+            g1.term(r.p + Lay.blocks[bl].off, Lb.dim[qlp], A.d.p + A.blocks[ab].off, n, Lb.dim[qlp], GT_BN,
+                    r.coef, m, n);
+          }
+          size_t before = g1.tasks.size();
+          g1.end();
+          if (g1.tasks.size() == before) {
+            tpos[n1 * nR + j] = (long)toff;
+            toff += (size_t)m * n;
+          }
+        }
+      const OpLayout& Lo = out.lay((int)beta);
+      double* obase = out.op((int)beta);
+      for (const Block& ob : Lo.blocks) {
+        int qa = ob.rs, qap = ob.cs;
+        g2.begin(obase + ob.off, ob.cols, ob.rows, ob.cols, 0);
+        for (int n1 = 0; n1 < 4; ++n1) {
+          int ql = Lb.find(Rb.qa[qa] - LQA[n1], Rb.qb[qa] - LQB[n1]);
+          if (ql < 0) continue;
+          int ab = A.blk(ql, n1);
+          if (ab < 0 || A.blocks[ab].cs != qa) continue;
+          long tp = tpos[n1 * nR + qap];
+          if (tp < 0) continue;
+          g2.term(A.d.p + A.blocks[ab].off, Rb.dim[qa], T.p + tp, Rb.dim[qap], Lb.dim[ql], GT_TA | GT_BN, 1.0,
+                  ob.rows, ob.cols);
+        }
+        g2.end();
+      }
+    }
+    run_builder(c, g1);
+    run_builder(c, g2);
+    b0 = b1;
+  }
+}
+
+void env_update_right(Context& c, Tilde& rt, const SiteT& B, int site, Env& out) {
+  const auto& st = c.mpo.bonds[site];
+  const Bond& Lb = B.L;
+  const Bond& Rb = B.R;
+  Env& Renv = *rt.env;
+  env_alloc(c, out, Lb, st);
+  const int nL = Lb.nsec();
+  std::vector<size_t> tsz(st.size(), 0);
+  for (size_t beta = 0; beta < st.size(); ++beta)
+    for (int n2 = 0; n2 < 4; ++n2)
+      for (int j = 0; j < nL; ++j) {
+        int qr = Rb.find(Lb.qa[j] + st[beta].dna + LQA[n2], Lb.qb[j] + st[beta].dnb + LQB[n2]);
+        if (qr >= 0) tsz[beta] += (size_t)Lb.dim[j] * Rb.dim[qr];
+      }
+  size_t budget = budget_elems(c);
+  size_t b0 = 0;
+  while (b0 < st.size()) {
+    size_t b1 = b0, tot = 0;
+    while (b1 < st.size() && (b1 == b0 || tot + tsz[b1] <= budget)) tot += tsz[b1++];
+    DArr<double> T;
+    T.alloc(tot, c.stream);
+    GemmBuilder g1, g2;
+    size_t toff = 0;
+    for (size_t beta = b0; beta < b1; ++beta) {
+      std::vector<long> tpos((size_t)4 * nL, -1);
+      for (int n2 = 0; n2 < 4; ++n2)
+        for (int j = 0; j < nL; ++j) {
+          int qr = Rb.find(Lb.qa[j] + st[beta].dna + LQA[n2], Lb.qb[j] + st[beta].dnb + LQB[n2]);
+          if (qr < 0) continue;
+          int m = Lb.dim[j], n = Rb.dim[qr];
+          g1.begin(T.p + toff, n, m, n, 0);
+          for (int n2p = 0; n2p < 4; ++n2p) {
+            const TRef& r = rt.ref[beta][n2 * 4 + n2p];
+            if (!r.p) continue;
+            const OpLayout& Lay = Renv.cls[r.cls];
+            int qrp = Rb.find(Lb.qa[j] + LQA[n2p], Lb.qb[j] + LQB[n2p]);
+            if (qrp < 0) continue;
+            int bl = Lay.blk_of_col[qrp];
+            if (bl < 0 || Lay.blocks[bl].rs != qr) continue;
+            int bb = B.blk(j, n2p);
+            if (bb < 0 || B.blocks[bb].cs != qrp) continue;
+            g1.term(B.d.p + B.blocks[bb].off, Rb.dim[qrp], r.p + Lay.blocks[bl].off, Rb.dim[qrp], Rb.dim[qrp], 0,
+                    r.coef, m, n);
+          }
+          size_t before = g1.tasks.size();
+          g1.end();
+          if (g1.tasks.size() == before) {
+            tpos[n2 * nL + j] = (long)toff;
+            toff += (size_t)m * n;
+          }
+        }
+      const OpLayout& Lo = out.lay((int)beta);
+      double* obase = out.op((int)beta);
+      for (const Block& ob : Lo.blocks) {
+        int qb = ob.rs, qbp = ob.cs;
+        g2.begin(obase + ob.off, ob.cols, ob.rows, ob.cols, 0);
+        for (int n2 = 0; n2 < 4; ++n2) {
+          int qr = Rb.find(Lb.qa[qb] + LQA[n2], Lb.qb[qb] + LQB[n2]);
+          if (qr < 0) continue;
+          int bb = B.blk(qb, n2);
+          if (bb < 0 || B.blocks[bb].cs != qr) continue;
+          long tp = tpos[n2 * nL + qbp];
+          if (tp < 0) continue;
+          g2.term(B.d.p + B.blocks[bb].off, Rb.dim[qr], T.p + tp, Rb.dim[qr], Rb.dim[qr], 0, 1.0, ob.rows,
+                  ob.cols);
+        }
+        g2.end();
+      }
+    }
+    run_builder(c, g1);
+    run_builder(c, g2);
+    b0 = b1;
+  }
+}
+
+// ---------------------------------------------------------------- sigma
+
+void build_sigma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) {
+  const auto& mid = c.mpo.bonds[k + 1];
+  Env& Lenv = *lt.env;
+  Env& Renv = *rt.env;
+  const Bond& Lb = Lenv.bond;
+  const Bond& Rb = Renv.bond;
+  plan = SigmaPlan();
+  PsiLayout& P = plan.psi;
+  P.build(Lb, Rb);
+  plan.in.alloc(P.nnz, c.stream);
+  plan.out.alloc(P.nnz, c.stream);
+  const int nL = Lb.nsec();
+  // X_beta layout = psi layout shifted by dQ_beta; X stored transposed per block
+  std::vector<size_t> xsz(mid.size(), 0);
+  for (size_t beta = 0; beta < mid.size(); ++beta)
+    for (int ql = 0; ql < nL; ++ql)
+      for (int n1 = 0; n1 < 4; ++n1)
+        for (int n2 = 0; n2 < 4; ++n2) {
+          int qr = Rb.find(Lb.qa[ql] + LQA[n1] + LQA[n2] + mid[beta].dna,
+                           Lb.qb[ql] + LQB[n1] + LQB[n2] + mid[beta].dnb);
+          if (qr >= 0) xsz[beta] += (size_t)Lb.dim[ql] * Rb.dim[qr];
+        }
+  size_t budget = budget_elems(c);
+  size_t maxchunk = 0;
+  std::vector<std::pair<size_t, size_t>> chunks;
+  {
+    size_t b0 = 0;
+    while (b0 < mid.size()) {
+      size_t b1 = b0, tot = 0;
+      while (b1 < mid.size() && (b1 == b0 || tot + xsz[b1] <= budget)) tot += xsz[b1++];
+      chunks.push_back({b0, b1});
+      maxchunk = std::max(maxchunk, tot);
+      b0 = b1;
+    }
+  }
+  plan.X.alloc(maxchunk, c.stream);
+  for (auto ch : chunks) {
+    GemmBuilder g1, g2;
+    size_t xoff = 0;
+    std::vector<std::vector<long>> xpos(ch.second - ch.first);
+    for (size_t beta = ch.first; beta < ch.second; ++beta) {
+      auto& xp = xpos[beta - ch.first];
+      xp.assign((size_t)nL * 16, -1);
+      for (int qlp = 0; qlp < nL; ++qlp)
+        for (int n1p = 0; n1p < 4; ++n1p)
+          for (int n2 = 0; n2 < 4; ++n2) {
+            int qr = Rb.find(Lb.qa[qlp] + LQA[n1p] + LQA[n2] + mid[beta].dna,
+                             Lb.qb[qlp] + LQB[n1p] + LQB[n2] + mid[beta].dnb);
+            if (qr < 0) continue;
+            int m = Rb.dim[qr], n = Lb.dim[qlp];  // X^T block: qr rows, ql' cols
+            g1.begin(plan.X.p + xoff, n, m, n, 0);
+            for (int n2p = 0; n2p < 4; ++n2p) {
+              const TRef& r = rt.ref[beta][n2 * 4 + n2p];
+              if (!r.p) continue;
+              int pb = P.blk(qlp, n1p, n2p);
+              if (pb < 0) continue;
+              int qrp = P.blocks[pb].cs;
+              const OpLayout& Lay = Renv.cls[r.cls];
+              int bl = Lay.blk_of_col[qrp];
+              if (bl < 0 || Lay.blocks[bl].rs != qr) continue;
+              g1.term(r.p + Lay.blocks[bl].off, Rb.dim[qrp], plan.in.p + P.blocks[pb].off, Rb.dim[qrp],
+                      Rb.dim[qrp], 0, r.coef, m, n);
+            }
+            size_t before = g1.tasks.size();
+            g1.end();
+            if (g1.tasks.size() == before) {
+              xp[(qlp * 4 + n1p) * 4 + n2] = (long)xoff;
+              xoff += (size_t)m * n;
+            }
+          }
+    }
+    for (size_t pb = 0; pb < P.blocks.size(); ++pb) {
+      const Block& ob = P.blocks[pb];
+      int ql = ob.rs, n1 = P.b1[pb], n2 = P.b2[pb];
+      g2.begin(plan.out.p + ob.off, ob.cols, ob.rows, ob.cols, 1);
+      for (size_t beta = ch.first; beta < ch.second; ++beta) {
+        const auto& xp = xpos[beta - ch.first];
+        for (int n1p = 0; n1p < 4; ++n1p) {
+          const TRef& r = lt.ref[beta][n1 * 4 + n1p];
+          if (!r.p) continue;
+          const OpLayout& Lay = Lenv.cls[r.cls];
+          int qlp = tilde_col(Lb, Lay, ql);
+          if (qlp < 0) continue;
+          int bl = Lay.blk_of_col[qlp];
+          if (bl < 0 || Lay.blocks[bl].rs != ql) continue;
+          long xo = xp[(qlp * 4 + n1p) * 4 + n2];
+          if (xo < 0) continue;
+          g2.term(r.p + Lay.blocks[bl].off, Lb.dim[qlp], plan.X.p + xo, Lb.dim[qlp], Lb.dim[qlp], 0, r.coef,
+                  ob.rows, ob.cols);
+        }
+      }
+      g2.end();
+    }
+    plan.stage1.emplace_back();
+    plan.stage1.back().upload(g1.tiles, g1.tasks, g1.terms, c.stream);
+    plan.stage2.emplace_back();
+    plan.stage2.back().upload(g2.tiles, g2.tasks, g2.terms, c.stream);
+    plan.flops += g1.flops + g2.flops;
+    cuda_check(cudaStreamSynchronize(c.stream), "sync");
+  }
+}
+
+void run_sigma(Context& c, SigmaPlan& plan, const double* x, double* y) {
+  const size_t bytes = plan.psi.nnz * sizeof(double);
+  if (x != plan.in.p) cuda_check(cudaMemcpyAsync(plan.in.p, x, bytes, cudaMemcpyDeviceToDevice, c.stream), "d2d");
+  cuda_check(cudaMemsetAsync(plan.out.p, 0, bytes, c.stream), "memset");
+  for (size_t i = 0; i < plan.stage1.size(); ++i) {
+    plan.stage1[i].run(c.stream);
+    plan.stage2[i].run(c.stream);
+  }
+  if (y != plan.out.p) cuda_check(cudaMemcpyAsync(y, plan.out.p, bytes, cudaMemcpyDeviceToDevice, c.stream), "d2d");
+}
+
+void compute_diag(Context& c, Tilde& lt, Tilde& rt, int k, const PsiLayout& P, double* diag) {
+  const auto& mid = c.mpo.bonds[k + 1];
+  Env& Lenv = *lt.env;
+  Env& Renv = *rt.env;
+  const Bond& Lb = Lenv.bond;
+  const Bond& Rb = Renv.bond;
+  std::vector<int> zb;
+  for (size_t beta = 0; beta < mid.size(); ++beta)
+    if (mid[beta].dna == 0 && mid[beta].dnb == 0) zb.push_back((int)beta);
+  const int nz = (int)zb.size();
+  cuda_check(cudaMemsetAsync(diag, 0, P.nnz * sizeof(double), c.stream), "memset");
+  if (nz == 0) return;
+  DArr<double> DL, DR;
+  DL.alloc((size_t)4 * Lb.total * nz, c.stream);
+  DR.alloc((size_t)4 * Rb.total * nz, c.stream);
+  cuda_check(cudaMemsetAsync(DL.p, 0, DL.n * sizeof(double), c.stream), "memset");
+  cuda_check(cudaMemsetAsync(DR.p, 0, DR.n * sizeof(double), c.stream), "memset");
+  std::vector<DiagJob> jobs;
+  int mx = 0;
+  for (int z = 0; z < nz; ++z) {
+    int beta = zb[z];
+    for (int n = 0; n < 4; ++n) {
+      const TRef& rl = lt.ref[beta][n * 5];
+      if (rl.p) {
+        const OpLayout& Lay = Lenv.cls[rl.cls];
+        for (const Block& b : Lay.blocks) {
+          if (b.rs != b.cs) continue;
+          jobs.push_back({rl.p + b.off, DL.p + ((size_t)n * Lb.total + Lb.off[b.rs]) * nz + z, b.rows, b.cols, nz,
+                          rl.coef});
+          mx = std::max(mx, b.rows);
+        }
+      }
+      const TRef& rr = rt.ref[beta][n * 5];
+      if (rr.p) {
+        const OpLayout& Lay = Renv.cls[rr.cls];
+        for (const Block& b : Lay.blocks) {
+          if (b.rs != b.cs) continue;
+          jobs.push_back({rr.p + b.off, DR.p + ((size_t)n * Rb.total + Rb.off[b.rs]) * nz + z, b.rows, b.cols, nz,
+                          rr.coef});
+          mx = std::max(mx, b.rows);
+        }
+      }
+    }
+  }
+  if (!jobs.empty()) {
+    DArr<DiagJob> dj;
+    dj.upload(jobs, c.stream);
+    launch_diag_extract(dj.p, (int)jobs.size(), mx, c.stream);
+    cuda_check(cudaGetLastError(), "diag extract");
+    cuda_check(cudaStreamSynchronize(c.stream), "sync");
+  }
+  GemmBuilder g;
+  for (size_t pb = 0; pb < P.blocks.size(); ++pb) {
+    const Block& ob = P.blocks[pb];
+    int n1 = P.b1[pb], n2 = P.b2[pb];
+    g.begin(diag + ob.off, ob.cols, ob.rows, ob.cols, 0);
+    g.term(DL.p + ((size_t)n1 * Lb.total + Lb.off[ob.rs]) * nz, nz, DR.p + ((size_t)n2 * Rb.total + Rb.off[ob.cs]) * nz,
+           nz, nz, 0, 1.0, ob.rows, ob.cols);
+    g.end();
+  }
+  run_builder(c, g);
+}
+
+void make_psi(Context& c, const SiteT& TL, const SiteT& TR, const PsiLayout& P, double* psi) {
+  cuda_check(cudaMemsetAsync(psi, 0, P.nnz * sizeof(double), c.stream), "memset");
+  GemmBuilder g;
+  for (size_t pb = 0; pb < P.blocks.size(); ++pb) {
+    const Block& ob = P.blocks[pb];
+    int ql = ob.rs, n1 = P.b1[pb], n2 = P.b2[pb];
+    int tl = TL.blk(ql, n1);
+    if (tl < 0) continue;
+    int qm = TL.blocks[tl].cs;
+    int tr = TR.blk(qm, n2);
+    if (tr < 0 || TR.blocks[tr].cs != ob.cs) continue;
+    g.begin(psi + ob.off, ob.cols, ob.rows, ob.cols, 0);
+    g.term(TL.d.p + TL.blocks[tl].off, TL.R.dim[qm], TR.d.p + TR.blocks[tr].off, ob.cols, TL.R.dim[qm], GT_BN, 1.0,
+           ob.rows, ob.cols);
+    g.end();
+  }
+  run_builder(c, g);
+}
+
+void prepare_two_site(Context& c, int k) {
+  if (k < 0 || k + 1 >= c.K) throw Error(ST_EINVAL, "two-site position out of range");
+  for (int j = 0; j < c.K; ++j)
+    if (!c.site_set[j]) throw Error(ST_ESTATE, "MPS tensor of site " + std::to_string(j) + " not set");
+  env_boundary_left(c, c.left[0]);
+  for (int j = 0; j < k; ++j) {
+    Tilde t;
+    build_tilde_left(c, c.left[j], j, t);
+    env_update_left(c, t, c.sites[j], j, c.left[j + 1]);
+  }
+  env_boundary_right(c, c.right[c.K]);
+  for (int j = c.K - 1; j >= k + 2; --j) {
+    Tilde t;
+    build_tilde_right(c, c.right[j + 1], j, t);
+    env_update_right(c, t, c.sites[j], j, c.right[j]);
+  }
+  build_tilde_left(c, c.left[k], k, c.lt);
+  build_tilde_right(c, c.right[k + 2], k + 1, c.rt);
+  build_sigma_plan(c, c.lt, c.rt, k, c.plan);
+  cuda_check(cudaStreamSynchronize(c.stream), "sync");
+  c.prepared = k;
+}
+
+// ---------------------------------------------------------------- Davidson
+
+// cyclic Jacobi for a small symmetric matrix (row-major n x n); eigenvalues
+// ascending in w, eigenvectors as columns of V
+static void jacobi_eigh(int n, std::vector<double> a, std::vector<double>& w, std::vector<double>& V) {
+  V.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0, tot = 0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        tot += a[i * n + j] * a[i * n + j];
+        if (i != j) off += a[i * n + j] * a[i * n + j];
+      }
+    if (off <= 1e-30 * tot || off == 0.0) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double apq = a[p * n + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        double app = a[p * n + p], aqq = a[q * n + q];
+        double theta = (aqq - app) / (2 * apq);
+        double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1));
+        double cs = 1 / std::sqrt(t * t + 1), sn = t * cs;
+        for (int k = 0; k < n; ++k) {
+          double akp = a[k * n + p], akq = a[k * n + q];
+          a[k * n + p] = cs * akp - sn * akq;
+          a[k * n + q] = sn * akp + cs * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          double apk = a[p * n + k], aqk = a[q * n + k];
+          a[p * n + k] = cs * apk - sn * aqk;
+          a[q * n + k] = sn * apk + cs * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          double vkp = V[k * n + p], vkq = V[k * n + q];
+          V[k * n + p] = cs * vkp - sn * vkq;
+          V[k * n + q] = sn * vkp + cs * vkq;
+        }
+      }
+  }
+  std::vector<int> ord(n);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::sort(ord.begin(), ord.end(), [&](int x, int y) { return a[x * n + x] < a[y * n + y]; });
+  w.resize(n);
+  std::vector<double> V2((size_t)n * n);
+  for (int j = 0; j < n; ++j) {
+    w[j] = a[ord[j] * n + ord[j]];
+    for (int i = 0; i < n; ++i) V2[i * n + j] = V[i * n + ord[j]];
+  }
+  V.swap(V2);
+}
+
+struct DotHelper {
+  DArr<double> part, out;
+  int nblk = 128;
+  std::vector<double> host;
+  void init(int maxm, cudaStream_t s) {
+    part.alloc((size_t)maxm * nblk, s);
+    out.alloc(maxm, s);
+    host.resize(maxm);
+  }
+  // dots of rows V[0..m) (stride ldv) with x, returned on host
+  const std::vector<double>& dots(Context& c, const double* V, long ldv, int m, const double* x, long n) {
+    launch_multidot(V, ldv, m, x, n, part.p, nblk, out.p, c.stream);
+    cuda_check(cudaMemcpyAsync(host.data(), out.p, m * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "d2h");
+    cuda_check(cudaStreamSynchronize(c.stream), "sync");
+    return host;
+  }
+};
+
+double davidson(Context& c, SigmaPlan& plan, const double* diag, double* psi, const DavidsonOpts& o, int* iters) {
+  const long n = plan.psi.nnz;
+  const int ms = (int)std::max<long>(2, std::min<long>(o.max_sub, n));
+  DArr<double> V, S, x, hx, r, t, coef;
+  V.alloc((size_t)ms * n, c.stream);
+  S.alloc((size_t)ms * n, c.stream);
+  x.alloc(n, c.stream);
+  hx.alloc(n, c.stream);
+  r.alloc(n, c.stream);
+  t.alloc(n, c.stream);
+  coef.alloc(ms, c.stream);
+  DotHelper dh;
+  dh.init(ms, c.stream);
+  std::vector<double> G((size_t)ms * ms, 0.0);
+  auto sigma_of = [&](const double* in, double* out) {
+    auto t0 = std::chrono::steady_clock::now();
+    run_sigma(c, plan, in, out);
+    cuda_check(cudaStreamSynchronize(c.stream), "sync");
+    auto t1 = std::chrono::steady_clock::now();
+    c.sigma_time_total += std::chrono::duration<double>(t1 - t0).count();
+    c.sigma_flops_total += plan.flops;
+    c.sigma_calls++;
+  };
+  double nrm = std::sqrt(dh.dots(c, psi, 0, 1, psi, n)[0]);
+  if (!(nrm > 0) || !std::isfinite(nrm)) throw Error(ST_EINVAL, "Davidson: zero or non-finite start vector");
+  launch_axpby(n, 1.0 / nrm, psi, 0.0, V.p, c.stream);
+  sigma_of(V.p, S.p);
+  G[0] = dh.dots(c, V.p, 0, 1, S.p, n)[0];
+  int m = 1;
+  double theta = G[0];
+  int it = 0;
+  std::vector<double> w, Y, sub;
+  for (; it < o.max_iter; ++it) {
+    sub.assign((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) sub[i * m + j] = 0.5 * (G[i * ms + j] + G[j * ms + i]);
+    jacobi_eigh(m, sub, w, Y);
+    theta = w[0];
+    std::vector<double> y(m);
+    for (int i = 0; i < m; ++i) y[i] = Y[i * m + 0];
+    cuda_check(cudaMemcpyAsync(coef.p, y.data(), m * sizeof(double), cudaMemcpyHostToDevice, c.stream), "h2d");
+    launch_combine_vectors(V.p, n, m, coef.p, n, x.p, c.stream);
+    launch_combine_vectors(S.p, n, m, coef.p, n, hx.p, c.stream);
+    cuda_check(cudaMemcpyAsync(r.p, hx.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "d2d");
+    launch_axpby(n, -theta, x.p, 1.0, r.p, c.stream);
+    double rn = std::sqrt(dh.dots(c, r.p, 0, 1, r.p, n)[0]);
+    if (!std::isfinite(rn)) throw Error(ST_ENOCONV, "Davidson: non-finite residual");
+    if (rn <= o.tol) break;
+    launch_precond(n, r.p, diag, theta, 1e-8, t.p, c.stream);
+    if (m == ms) {  // restart from the Ritz vector
+      cuda_check(cudaMemcpyAsync(V.p, x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "d2d");
+      cuda_check(cudaMemcpyAsync(S.p, hx.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "d2d");
+      double xn = dh.dots(c, V.p, 0, 1, V.p, n)[0];
+      G.assign((size_t)ms * ms, 0.0);
+      G[0] = theta / xn;  // x normalised up to rounding
+      m = 1;
+    }
+    double tn = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+      const auto& d = dh.dots(c, V.p, n, m, t.p, n);
+      std::vector<double> neg(m);
+      for (int i = 0; i < m; ++i) neg[i] = -d[i];
+      cuda_check(cudaMemcpyAsync(coef.p, neg.data(), m * sizeof(double), cudaMemcpyHostToDevice, c.stream), "h2d");
+      launch_combine_vectors(V.p, n, m, coef.p, n, hx.p, c.stream);
+      launch_axpby(n, 1.0, hx.p, 1.0, t.p, c.stream);
+    }
+    tn = std::sqrt(dh.dots(c, t.p, 0, 1, t.p, n)[0]);
+    if (!(tn > 1e-14)) break;  // subspace exhausted: the Ritz pair is exact in it
+    launch_axpby(n, 1.0 / tn, t.p, 0.0, V.p + (size_t)m * n, c.stream);
+    sigma_of(V.p + (size_t)m * n, S.p + (size_t)m * n);
+    const auto& g = dh.dots(c, V.p, n, m + 1, S.p + (size_t)m * n, n);
+    for (int i = 0; i <= m; ++i) G[i * ms + m] = G[m * ms + i] = g[i];
+    ++m;
+  }
+  double xn = std::sqrt(dh.dots(c, x.p, 0, 1, x.p, n)[0]);
+  launch_axpby(n, 1.0 / xn, x.p, 0.0, psi, c.stream);
+  cuda_check(cudaStreamSynchronize(c.stream), "sync");
+  if (iters) *iters = it;
+  return theta;
+}
+
+// ---------------------------------------------------------------- decimation
+
+double decimate(Context& c, const PsiLayout& P, const double* psi, int M, int direction, SiteT& left, SiteT& right) {
+  const Bond& Lb = P.L;
+  const Bond& Rb = P.R;
+  struct Seg { int q, n, off; };
+  std::map<std::pair<int, int>, std::pair<std::vector<Seg>, std::vector<Seg>>> gm;
+  for (int ql = 0; ql < Lb.nsec(); ++ql)
+    for (int n1 = 0; n1 < 4; ++n1) {
+      auto key = std::make_pair(Lb.qa[ql] + LQA[n1], Lb.qb[ql] + LQB[n1]);
+      gm[key].first.push_back({ql, n1, 0});
+    }
+  for (int qr = 0; qr < Rb.nsec(); ++qr)
+    for (int n2 = 0; n2 < 4; ++n2) {
+      auto key = std::make_pair(Rb.qa[qr] - LQA[n2], Rb.qb[qr] - LQB[n2]);
+      gm[key].second.push_back({qr, n2, 0});
+    }
+  struct Group { int qa, qb, nr, nc; std::vector<Seg> rows, cols; size_t moff, goff; };
+  std::vector<Group> groups;
+  size_t mtot = 0, gtot = 0;
+  for (auto& kv : gm) {
+    if (kv.second.first.empty() || kv.second.second.empty()) continue;
+    Group g;
+    g.qa = kv.first.first;
+    g.qb = kv.first.second;
+    g.rows = kv.second.first;
+    g.cols = kv.second.second;
+    g.nr = g.nc = 0;
+    for (auto& s : g.rows) { s.off = g.nr; g.nr += Lb.dim[s.q]; }
+    for (auto& s : g.cols) { s.off = g.nc; g.nc += Rb.dim[s.q]; }
+    int d = direction == 0 ? g.nr : g.nc;
+    g.moff = mtot;
+    g.goff = gtot;
+    mtot += (size_t)g.nr * g.nc;
+    gtot += (size_t)d * d;
+    groups.push_back(g);
+  }
+  DArr<double> Mat, Gram;
+  Mat.alloc(mtot, c.stream);
+  Gram.alloc(gtot, c.stream);
+  cuda_check(cudaMemsetAsync(Mat.p, 0, mtot * sizeof(double), c.stream), "memset");
+  // gather psi blocks into the dense group matrices
+  std::vector<CopyJob> jobs;
+  for (auto& g : groups)
+    for (auto& rs : g.rows)
+      for (auto& cs : g.cols) {
+        int pb = P.blk(rs.q, rs.n, cs.n);
+        if (pb < 0 || P.blocks[pb].cs != cs.q) continue;
+        const Block& b = P.blocks[pb];
+        jobs.push_back({psi + b.off, Mat.p + g.moff + (size_t)rs.off * g.nc + cs.off, b.rows, b.cols, b.cols, g.nc, 0,
+                        1.0});
+      }
+  run_copies(c, jobs);
+  GemmBuilder gb;
+  for (auto& g : groups) {
+    double* Mg = Mat.p + g.moff;
+    if (direction == 0) {
+      gb.begin(Gram.p + g.goff, g.nr, g.nr, g.nr, 0);
+      gb.term(Mg, g.nc, Mg, g.nc, g.nc, 0, 1.0, g.nr, g.nr);
+    } else {
+      gb.begin(Gram.p + g.goff, g.nc, g.nc, g.nc, 0);
+      gb.term(Mg, g.nc, Mg, g.nc, g.nr, GT_TA | GT_BN, 1.0, g.nc, g.nc);
+    }
+    gb.end();
+  }
+  run_builder(c, gb);
+  // eigen-decomposition of every group Gram matrix
+  int maxd = 0;
+  for (auto& g : groups) maxd = std::max(maxd, direction == 0 ? g.nr : g.nc);
+  DArr<double> evals;
+  size_t etot = 0;
+  for (auto& g : groups) etot += direction == 0 ? g.nr : g.nc;
+  evals.alloc(std::max<size_t>(etot, 1), c.stream);
+  int lwork = 0;
+  solver_check(cusolverDnDsyevd_bufferSize(c.solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, maxd, Gram.p,
+                                           maxd, evals.p, &lwork),
+               "syevd_bufferSize");
+  DArr<double> work;
+  work.alloc(std::max(lwork, 1), c.stream);
+  DArr<int> info;
+  info.alloc(groups.size() + 1, c.stream);
+  size_t eo = 0;
+  std::vector<size_t> eoff(groups.size());
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    auto& g = groups[gi];
+    int d = direction == 0 ? g.nr : g.nc;
+    eoff[gi] = eo;
+    solver_check(cusolverDnDsyevd(c.solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, d, Gram.p + g.goff, d,
+                                  evals.p + eo, work.p, lwork, info.p + gi),
+                 "syevd");
+    eo += d;
+  }
+  std::vector<double> ev(etot);
+  std::vector<int> hinfo(groups.size());
+  cuda_check(cudaMemcpyAsync(ev.data(), evals.p, etot * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "d2h");
+  if (!groups.empty())
+    cuda_check(cudaMemcpyAsync(hinfo.data(), info.p, groups.size() * sizeof(int), cudaMemcpyDeviceToHost, c.stream),
+               "d2h");
+  cuda_check(cudaStreamSynchronize(c.stream), "sync");
+  for (int v : hinfo)
+    if (v != 0) throw Error(ST_ENOCONV, "syevd failed in decimation");
+  // selection: weights >= 1e-14, sorted by (-w, group, index-from-top); keep M, never split a multiplet
+  struct Cand { double w; int g, i; };
+  std::vector<Cand> cand;
+  double total = 0;
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    int d = direction == 0 ? groups[gi].nr : groups[gi].nc;
+    for (int i = 0; i < d; ++i) {
+      double w = ev[eoff[gi] + d - 1 - i];
+      total += std::max(w, 0.0);
+      if (w >= 1e-14) cand.push_back({w, (int)gi, i});
+    }
+  }
+  std::sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) {
+    if (a.w != b.w) return a.w > b.w;
+    if (a.g != b.g) return a.g < b.g;
+    return a.i < b.i;
+  });
+  size_t keep = cand.size();
+  if ((long)cand.size() > M) {
+    double t = cand[M].w;
+    keep = 0;
+    for (int i = 0; i < M; ++i)
+      if (cand[i].w > t * (1.0 + 1e-8)) keep = i + 1;
+  }
+  std::vector<int> nk(groups.size(), 0);
+  double kept = 0;
+  for (size_t i = 0; i < keep; ++i) {
+    nk[cand[i].g]++;
+    kept += cand[i].w;
+  }
+  if (keep == 0) throw Error(ST_ENOCONV, "decimation kept no states");
+  Bond nb;
+  std::vector<int> gsec(groups.size(), -1);
+  for (size_t gi = 0; gi < groups.size(); ++gi)
+    if (nk[gi] > 0) {
+      gsec[gi] = nb.nsec();
+      nb.add(groups[gi].qa, groups[gi].qb, nk[gi]);
+    }
+  left.layout(Lb, nb);
+  right.layout(nb, Rb);
+  left.d.alloc(left.nnz, c.stream);
+  right.d.alloc(right.nnz, c.stream);
+  cuda_check(cudaMemsetAsync(left.d.p, 0, left.nnz * sizeof(double), c.stream), "memset");
+  cuda_check(cudaMemsetAsync(right.d.p, 0, right.nnz * sizeof(double), c.stream), "memset");
+  // product with the kept eigenvectors: kept vectors are the last nk columns of the
+  // column-major eigenvector matrix, i.e. rows [d-nk, d) of its row-major view
+  size_t ctot = 0;
+  std::vector<size_t> coff(groups.size());
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    coff[gi] = ctot;
+    ctot += (size_t)nk[gi] * (direction == 0 ? groups[gi].nc : groups[gi].nr);
+  }
+  DArr<double> Cm;
+  Cm.alloc(std::max<size_t>(ctot, 1), c.stream);
+  GemmBuilder g2;
+  std::vector<CopyJob> out;
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    if (!nk[gi]) continue;
+    auto& g = groups[gi];
+    int d = direction == 0 ? g.nr : g.nc;
+    const double* Uk = Gram.p + g.goff + (size_t)(d - nk[gi]) * d;  // nk x d row-major
+    double* Mg = Mat.p + g.moff;
+    int s = gsec[gi];
+    if (direction == 0) {
+      // C = Uk * Mg  (nk x nc)
+      g2.begin(Cm.p + coff[gi], g.nc, nk[gi], g.nc, 0);
+      g2.term(Uk, d, Mg, g.nc, g.nr, GT_BN, 1.0, nk[gi], g.nc);
+      g2.end();
+      for (auto& rs : g.rows) {  // A^{n1}[ql, a] = Uk[a][rowoff + i]
+        int b = left.blk(rs.q, rs.n);
+        out.push_back({Uk + rs.off, left.d.p + left.blocks[b].off, Lb.dim[rs.q], nk[gi], d, nk[gi], 1, 1.0});
+      }
+      for (auto& cs : g.cols) {  // center[a, n2, qr] = C[a][coloff + j]
+        int b = right.blk(s, cs.n);
+        if (b < 0 || right.blocks[b].cs != cs.q) continue;
+        out.push_back({Cm.p + coff[gi] + cs.off, right.d.p + right.blocks[b].off, nk[gi], Rb.dim[cs.q], g.nc,
+                       Rb.dim[cs.q], 0, 1.0});
+      }
+    } else {
+      // C = Mg * Vk^T  (nr x nk)
+      g2.begin(Cm.p + coff[gi], nk[gi], g.nr, nk[gi], 0);
+      g2.term(Mg, g.nc, Uk, d, g.nc, 0, 1.0, g.nr, nk[gi]);
+      g2.end();
+      for (auto& cs : g.cols) {  // B^{n2}[a, qr] = Vk[a][coloff + j]
+        int b = right.blk(s, cs.n);
+        if (b < 0 || right.blocks[b].cs != cs.q) continue;
+        out.push_back({Uk + cs.off, right.d.p + right.blocks[b].off, nk[gi], Rb.dim[cs.q], d, Rb.dim[cs.q], 0, 1.0});
+      }
+      for (auto& rs : g.rows) {  // center[ql, n1, a] = C[rowoff + i][a]
+        int b = left.blk(rs.q, rs.n);
+        out.push_back({Cm.p + coff[gi] + (size_t)rs.off * nk[gi], left.d.p + left.blocks[b].off, Lb.dim[rs.q], nk[gi],
+                       nk[gi], nk[gi], 0, 1.0});
+      }
+    }
+  }
+  run_builder(c, g2);
+  run_copies(c, out);
+  return std::max(0.0, total - kept);
+}
+
+// ---------------------------------------------------------------- canonical form
+
+// rows of X (r x cols, row-major) = L * Q with orthonormal rows Q (MGS, twice)
+static void lq_rows(int r, int cols, std::vector<double>& X, std::vector<double>& L) {
+  L.assign((size_t)r * r, 0.0);
+  for (int i = 0; i < r; ++i) {
+    double* xi = &X[(size_t)i * cols];
+    for (int pass = 0; pass < 2; ++pass)
+      for (int j = 0; j < i; ++j) {
+        const double* qj = &X[(size_t)j * cols];
+        double d = 0;
+        for (int e = 0; e < cols; ++e) d += qj[e] * xi[e];
+        for (int e = 0; e < cols; ++e) xi[e] -= d * qj[e];
+        L[(size_t)i * r + j] += d;
+      }
+    double nr = 0;
+    for (int e = 0; e < cols; ++e) nr += xi[e] * xi[e];
+    nr = std::sqrt(nr);
+    if (!(nr > 1e-300)) throw Error(ST_EINVAL, "initial MPS tensor is rank deficient");
+    for (int e = 0; e < cols; ++e) xi[e] /= nr;
+    L[(size_t)i * r + i] = nr;
+  }
+}
+
+void right_canonicalize(Context& c) {
+  std::vector<std::vector<double>> H(c.K);
+  for (int k = 0; k < c.K; ++k) {
+    H[k].resize(c.sites[k].nnz);
+    if (c.sites[k].nnz)
+      cuda_check(cudaMemcpy(H[k].data(), c.sites[k].d.p, c.sites[k].nnz * sizeof(double), cudaMemcpyDeviceToHost),
+                 "d2h");
+  }
+  for (int k = c.K - 1; k >= 2; --k) {
+    SiteT& A = c.sites[k];
+    SiteT& P = c.sites[k - 1];
+    for (int q = 0; q < A.L.nsec(); ++q) {
+      int r = A.L.dim[q];
+      int cols = 0;
+      std::vector<int> bl;
+      for (int n = 0; n < 4; ++n) {
+        int b = A.blk(q, n);
+        if (b >= 0) { bl.push_back(b); cols += A.blocks[b].cols; }
+      }
+      if (cols < r) throw Error(ST_EINVAL, "initial MPS bond larger than what the next site supplies");
+      std::vector<double> X((size_t)r * cols), L;
+      int co = 0;
+      for (int b : bl) {
+        const Block& B = A.blocks[b];
+        for (int i = 0; i < r; ++i)
+          for (int j = 0; j < B.cols; ++j) X[(size_t)i * cols + co + j] = H[k][B.off + (long)i * B.cols + j];
+        co += B.cols;
+      }
+      lq_rows(r, cols, X, L);
+      co = 0;
+      for (int b : bl) {
+        const Block& B = A.blocks[b];
+        for (int i = 0; i < r; ++i)
+          for (int j = 0; j < B.cols; ++j) H[k][B.off + (long)i * B.cols + j] = X[(size_t)i * cols + co + j];
+        co += B.cols;
+      }
+      // previous site blocks (., ., q) <- block * L
+      for (size_t b = 0; b < P.blocks.size(); ++b) {
+        const Block& B = P.blocks[b];
+        if (B.cs != q) continue;
+        std::vector<double> tmp((size_t)B.rows * r, 0.0);
+        for (int i = 0; i < B.rows; ++i)
+          for (int j = 0; j < r; ++j) {
+            double s = 0;
+            for (int l = 0; l < r; ++l) s += H[k - 1][B.off + (long)i * r + l] * L[(size_t)l * r + j];
+            tmp[(size_t)i * r + j] = s;
+          }
+        std::copy(tmp.begin(), tmp.end(), H[k - 1].begin() + B.off);
+      }
+    }
+  }
+  for (int k = 0; k < c.K; ++k)
+    if (c.sites[k].nnz)
+      cuda_check(cudaMemcpy(c.sites[k].d.p, H[k].data(), c.sites[k].nnz * sizeof(double), cudaMemcpyHostToDevice),
+                 "h2d");
+}
+
+// ---------------------------------------------------------------- sweeps
+
+void run_sweeps(Context& c, int nsweeps, const int* M, const double* tol, int max_iter, SweepStats& st) {
+  if (c.K < 3) throw Error(ST_EINVAL, "sweeps need K >= 3");
+  for (int j = 0; j < c.K; ++j)
+    if (!c.site_set[j]) throw Error(ST_ESTATE, "MPS tensor of site " + std::to_string(j) + " not set");
+  c.prepared = -1;
+  c.have_plan = false;
+  right_canonicalize(c);
+  env_boundary_left(c, c.left[0]);
+  env_boundary_right(c, c.right[c.K]);
+  for (int j = c.K - 1; j >= 2; --j) {
+    Tilde t;
+    build_tilde_right(c, c.right[j + 1], j, t);
+    env_update_right(c, t, c.sites[j], j, c.right[j]);
+  }
+  const int K = c.K;
+  for (int s = 0; s < nsweeps; ++s) {
+    auto t0 = std::chrono::steady_clock::now();
+    double f0 = c.sigma_flops_total, s0 = c.sigma_time_total;
+    double dmax = 0, e = 0;
+    int iters = 0;
+    DavidsonOpts o;
+    o.tol = tol[s];
+    o.max_iter = max_iter;
+    auto step = [&](int k, int dir) {
+      Tilde lt, rt;
+      build_tilde_left(c, c.left[k], k, lt);
+      build_tilde_right(c, c.right[k + 2], k + 1, rt);
+      SigmaPlan plan;
+      build_sigma_plan(c, lt, rt, k, plan);
+      DArr<double> psi, diag;
+      psi.alloc(plan.psi.nnz, c.stream);
+      diag.alloc(plan.psi.nnz, c.stream);
+      make_psi(c, c.sites[k], c.sites[k + 1], plan.psi, psi.p);
+      compute_diag(c, lt, rt, k, plan.psi, diag.p);
+      int it = 0;
+      e = davidson(c, plan, diag.p, psi.p, o, &it);
+      iters += it;
+      SiteT A, B;
+      double dw = decimate(c, plan.psi, psi.p, M[s], dir, A, B);
+      dmax = std::max(dmax, dw);
+      c.sites[k] = std::move(A);
+      c.sites[k + 1] = std::move(B);
+      if (dir == 0) {
+        env_update_left(c, lt, c.sites[k], k, c.left[k + 1]);
+        c.right[k + 2] = Env();
+      } else {
+        env_update_right(c, rt, c.sites[k + 1], k + 1, c.right[k + 1]);
+        c.left[k + 1] = Env();
+      }
+    };
+    for (int k = 0; k <= K - 3; ++k) step(k, 0);
+    if (!c.right[K].valid) env_boundary_right(c, c.right[K]);
+    for (int k = K - 2; k >= 1; --k) step(k, 1);
+    cuda_check(cudaStreamSynchronize(c.stream), "sync");
+    auto t1 = std::chrono::steady_clock::now();
+    st.energy.push_back(e + c.ecore);
+    st.discarded.push_back(dmax);
+    st.seconds.push_back(std::chrono::duration<double>(t1 - t0).count());
+    st.sigma_flops.push_back(c.sigma_flops_total - f0);
+    st.sigma_seconds.push_back(c.sigma_time_total - s0);
+    st.davidson_iters.push_back(iters);
+  }
+}
+
+}  // namespace gbdmrg

@@ -1,0 +1,238 @@
+// Two-site DMRG engine: quantum-number block layouts, renormalised operators
+// (environments), the sigma vector H_eff.psi, Davidson, decimation, sweep.
+#pragma once
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <array>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "kernels.hpp"
+#include "mpo.hpp"
+
+namespace gbdmrg {
+
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+enum : int { ST_OK = 0, ST_EINVAL = 1, ST_ENOMEM = 2, ST_ECUDA = 3, ST_ENOCONV = 4, ST_ETIMEOUT = 5,
+             ST_EIO = 6, ST_ESMALL = 7, ST_ESTATE = 8 };
+
+void cuda_check(cudaError_t e, const char* what);
+
+// local basis n = n_alpha + 2 n_beta
+constexpr int LQA[4] = {0, 1, 0, 1};
+constexpr int LQB[4] = {0, 0, 1, 1};
+
+// Sectors of one bond, sorted by (n_alpha, n_beta); labels are particle
+// counts of the block left of the bond.
+struct Bond {
+  std::vector<int> qa, qb, dim, off;
+  int total = 0;
+  int nsec() const { return (int)dim.size(); }
+  int find(int a, int b) const;
+  void add(int a, int b, int d);   // append (must keep sorted order)
+};
+
+struct Block {
+  int rs, cs, rows, cols;
+  long off;
+};
+
+// Block-sparse operator with quantum-number change (da, db): block (row
+// sector, col sector) exists when q_row = q_col + (da, db) and both exist.
+struct OpLayout {
+  int da = 0, db = 0;
+  std::vector<Block> blocks;
+  std::vector<int> blk_of_col;
+  long nnz = 0;
+};
+OpLayout make_op_layout(const Bond& b, int da, int db);
+
+// stream-ordered device allocation
+void* dev_alloc(size_t bytes, cudaStream_t s);
+void dev_free(void* p, cudaStream_t s);
+
+template <class T>
+struct DArr {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaStream_t s = nullptr;
+  DArr() = default;
+  DArr(const DArr&) = delete;
+  DArr& operator=(const DArr&) = delete;
+  DArr(DArr&& o) noexcept { *this = std::move(o); }
+  DArr& operator=(DArr&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; s = o.s; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DArr() { release(); }
+  void release() { if (p) dev_free(p, s); p = nullptr; n = 0; }
+  void alloc(size_t cnt, cudaStream_t st) {
+    release(); s = st; n = cnt;
+    if (cnt) p = (T*)dev_alloc(cnt * sizeof(T), st);
+  }
+  void upload(const std::vector<T>& h, cudaStream_t st) {
+    alloc(h.size(), st);
+    if (n) cuda_check(cudaMemcpyAsync(p, h.data(), n * sizeof(T), cudaMemcpyHostToDevice, st), "upload");
+  }
+};
+
+// Renormalised operators of every MPO state at one bond (Eq. renormop).
+struct Env {
+  Bond bond;
+  std::vector<OpLayout> cls;
+  std::vector<DArr<double>> data;    // per class [nslot * nnz]
+  std::vector<int> nslot;
+  std::vector<int> st_cls, st_slot;  // per MPO state at this bond
+  bool valid = false;
+  double* op(int st) { return data[st_cls[st]].p + (size_t)st_slot[st] * cls[st_cls[st]].nnz; }
+  const OpLayout& lay(int st) const { return cls[st_cls[st]]; }
+  size_t bytes() const;
+};
+
+// MPS site tensor A^{n}_{l r}: blocks (ql, n, qr = ql + q(n)), row-major ql x qr.
+struct SiteT {
+  Bond L, R;
+  std::vector<Block> blocks;
+  std::vector<int> bn;
+  std::vector<int> lookup;  // [ql*4 + n]
+  long nnz = 0;
+  DArr<double> d;
+  void layout(const Bond& l, const Bond& r);
+  int blk(int ql, int n) const { return lookup[ql * 4 + n]; }
+};
+
+// Two-site tensor psi[l, n1, n2, r] with ql + q(n1) + q(n2) + shift = qr.
+struct PsiLayout {
+  Bond L, R;
+  int da = 0, db = 0;
+  std::vector<Block> blocks;
+  std::vector<int> b1, b2;
+  std::vector<int> lookup;  // [(ql*4 + n1)*4 + n2]
+  long nnz = 0;
+  void build(const Bond& l, const Bond& r, int sa = 0, int sb = 0);
+  int blk(int ql, int n1, int n2) const { return lookup[(ql * 4 + n1) * 4 + n2]; }
+};
+
+// W-contracted operators of one side of a two-site problem:
+//   left : Lt[beta][n n'] = sum_alpha W[k]_{alpha beta}[n, n'] L_k[alpha]
+//   right: Rt[beta][n n'] = sum_gamma W[k]_{beta gamma}[n, n'] R_{k+1}[gamma]
+// Single-term sums reference the environment directly (pointer + coefficient);
+// longer sums are materialised once per site (the element-wise blocking with
+// integral coefficients, e.g. the a_k (x) a_s sum of Eq. prenormrule).
+struct TRef {
+  const double* p = nullptr;
+  double coef = 0.0;
+  int cls = -1;
+};
+struct Tilde {
+  Env* env = nullptr;
+  int nmid = 0;
+  std::vector<std::array<TRef, 16>> ref;
+  DArr<double> combo;
+  long combo_flops = 0;
+};
+
+// Device-side work list of one grouped GEMM launch.
+struct GemmPlan {
+  DArr<GemmTile> tiles;
+  DArr<GemmTask> tasks;
+  DArr<GemmTerm> terms;
+  int ntiles = 0;
+  double flops = 0;
+  void upload(const std::vector<GemmTile>& ti, const std::vector<GemmTask>& ta,
+              const std::vector<GemmTerm>& te, cudaStream_t s);
+  void run(cudaStream_t s) const;
+};
+struct GemmBuilder {
+  std::vector<GemmTile> tiles;
+  std::vector<GemmTask> tasks;
+  std::vector<GemmTerm> terms;
+  double flops = 0;
+  int begin(double* C, int ldc, int m, int n, int beta);  // returns task index
+  void term(const double* A, int lda, const double* B, int ldb, int k, int flags, double alpha, int m, int n);
+  void end();  // emits tiles of the last task if it has terms (or beta == 0)
+  bool empty() const { return tasks.empty(); }
+  void clear() { tiles.clear(); tasks.clear(); terms.clear(); flops = 0; }
+};
+
+struct SigmaPlan {
+  PsiLayout psi;
+  DArr<double> in, out, X;
+  std::vector<GemmPlan> stage1, stage2;
+  double flops = 0;
+};
+
+struct Context;
+
+struct SweepStats {
+  std::vector<double> energy, discarded, seconds, sigma_flops, sigma_seconds;
+  std::vector<int> davidson_iters;
+};
+
+struct Context {
+  int K = 0, N = 0, two_sz = 0, Na = 0, Nb = 0;
+  double ecore = 0.0;
+  std::vector<double> h1, eri;
+  MPO mpo;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cusolverDnHandle_t solver = nullptr;
+  std::string last_error;
+
+  std::vector<SiteT> sites;        // MPS tensors (device)
+  std::vector<bool> site_set;
+  std::vector<Env> left, right;    // left[b]: bond b (sites < b); right[b]: sites >= b
+
+  // state of an explicitly prepared two-site problem (for gbdmrg_sigma / diag)
+  int prepared = -1;
+  Tilde lt, rt;
+  SigmaPlan plan;
+  bool have_plan = false;
+
+  // counters
+  double sigma_flops_total = 0, sigma_time_total = 0;
+  long sigma_calls = 0;
+  int chunk_budget_mb = 2048;
+
+  ~Context();
+};
+
+void ctx_init(Context& c);
+void set_site_dense(Context& c, int k, int Dl, int Dr, const int* qn_l, const int* qn_r, const double* A);
+void get_site_dense(Context& c, int k, std::vector<double>& A);
+
+void env_boundary_left(Context& c, Env& e);
+void env_boundary_right(Context& c, Env& e);
+void build_tilde_left(Context& c, Env& L, int site, Tilde& t);
+void build_tilde_right(Context& c, Env& R, int site, Tilde& t);
+void env_update_left(Context& c, Tilde& lt, const SiteT& A, int site, Env& out);
+void env_update_right(Context& c, Tilde& rt, const SiteT& B, int site, Env& out);
+
+void build_sigma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan);
+void run_sigma(Context& c, SigmaPlan& plan, const double* x, double* y);
+void compute_diag(Context& c, Tilde& lt, Tilde& rt, int k, const PsiLayout& P, double* diag);
+
+void prepare_two_site(Context& c, int k);
+void make_psi(Context& c, const SiteT& TL, const SiteT& TR, const PsiLayout& P, double* psi);
+
+struct DavidsonOpts {
+  double tol = 1e-9;
+  int max_iter = 200, max_sub = 24;
+};
+double davidson(Context& c, SigmaPlan& plan, const double* diag, double* psi, const DavidsonOpts& o,
+                int* iters);
+
+// decimation of psi at sites (k, k+1); direction 0 = left-move (A[k] = U, A[k+1] = S V^T),
+// 1 = right-move (A[k] = U S, A[k+1] = V^T).  Returns discarded weight.
+double decimate(Context& c, const PsiLayout& P, const double* psi, int M, int direction, SiteT& left,
+                SiteT& right);
+
+void right_canonicalize(Context& c);
+void run_sweeps(Context& c, int nsweeps, const int* M, const double* tol, int max_iter, SweepStats& st);
+
+}  // namespace gbdmrg

@@ -1,0 +1,337 @@
+// MPO builder: see mpo.hpp for the construction and its correspondence to
+// Eqs. (Hdecomp), (renormrule), (prenormrule) of the paper.
+#include "mpo.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <stdexcept>
+
+namespace gbdmrg {
+
+uint64_t StateKey::pack() const {
+  uint64_t v = (uint64_t)kind | ((uint64_t)n << 2);
+  for (int i = 0; i < n; ++i)
+    v |= (uint64_t)((uint64_t)ops[i].cre | ((uint64_t)ops[i].x << 1)) << (4 + 13 * i);
+  return v;
+}
+
+static StateKey unpack_key(uint64_t v) {
+  StateKey k;
+  k.kind = v & 3;
+  k.n = (v >> 2) & 3;
+  for (int i = 0; i < k.n; ++i) {
+    uint64_t o = (v >> (4 + 13 * i)) & 0x1fff;
+    k.ops[i].cre = o & 1;
+    k.ops[i].x = (int16_t)(o >> 1);
+  }
+  return k;
+}
+
+int MPO::state_I(int b) const {
+  for (size_t i = 0; i < bonds[b].size(); ++i)
+    if (bonds[b][i].key.kind == 0) return (int)i;
+  return -1;
+}
+int MPO::state_H(int b) const {
+  for (size_t i = 0; i < bonds[b].size(); ++i)
+    if (bonds[b][i].key.kind == 1) return (int)i;
+  return -1;
+}
+
+namespace {
+
+struct Term {
+  int n;
+  FOp o[4];
+};
+
+inline uint64_t term_pack(const FOp* o, int n) {
+  uint64_t v = (uint64_t)n;
+  for (int i = 0; i < n; ++i)
+    v |= (uint64_t)((uint64_t)o[i].cre | ((uint64_t)o[i].x << 1)) << (3 + 13 * i);
+  return v;
+}
+
+inline void term_unpack(uint64_t v, Term& t) {
+  t.n = v & 7;
+  for (int i = 0; i < t.n; ++i) {
+    uint64_t o = (v >> (3 + 13 * i)) & 0x1fff;
+    t.o[i].cre = o & 1;
+    t.o[i].x = (int16_t)(o >> 1);
+  }
+}
+
+// stable sort by spin-orbital, returns permutation sign (swaps of distinct x only)
+inline int stable_sort_sign(FOp* o, int n) {
+  int sign = 1;
+  for (int i = 1; i < n; ++i) {
+    FOp cur = o[i];
+    int j = i - 1;
+    while (j >= 0 && o[j].x > cur.x) {
+      o[j + 1] = o[j];
+      sign = -sign;
+      --j;
+    }
+    o[j + 1] = cur;
+  }
+  return sign;
+}
+
+// 2x2 single spin-orbital matrices, index [n][n']
+struct M2 {
+  double a[2][2];
+};
+inline M2 m2_id() { return {{{1, 0}, {0, 1}}}; }
+inline M2 m2_mul(const M2& x, const M2& y) {
+  M2 r{};
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) r.a[i][j] = x.a[i][0] * y.a[0][j] + x.a[i][1] * y.a[1][j];
+  return r;
+}
+inline M2 m2_sigma(int cre) {
+  M2 r{};
+  if (cre) r.a[1][0] = 1.0; else r.a[0][1] = 1.0;
+  return r;
+}
+inline M2 m2_z() { return {{{1, 0}, {0, -1}}}; }
+
+// Local 4x4 operator on site s for the term operators located there (sorted,
+// given in order) with 'pend' operators of the term on later sites.
+void local_op(const FOp* ops, int nops, int site, int pend, double* m) {
+  M2 la = m2_id(), lb = m2_id();
+  int nb_ops = 0;
+  for (int i = 0; i < nops; ++i)
+    if (ops[i].x == 2 * site + 1) ++nb_ops;
+  for (int i = 0; i < nops; ++i) {
+    if (ops[i].x == 2 * site) la = m2_mul(la, m2_sigma(ops[i].cre));
+    else lb = m2_mul(lb, m2_sigma(ops[i].cre));
+  }
+  if ((nb_ops + pend) & 1) la = m2_mul(la, m2_z());
+  if (pend & 1) lb = m2_mul(lb, m2_z());
+  for (int n = 0; n < 4; ++n)
+    for (int np = 0; np < 4; ++np)
+      m[n * 4 + np] = la.a[n & 1][np & 1] * lb.a[n >> 1][np >> 1];
+}
+
+struct PairHash {
+  size_t operator()(const std::pair<uint64_t, uint64_t>& p) const {
+    return std::hash<uint64_t>()(p.first * 0x9E3779B97F4A7C15ull ^ p.second);
+  }
+};
+
+struct EntryAcc {
+  double m[16];
+  bool structural;
+};
+
+}  // namespace
+
+MPO build_mpo(int K, const double* h, const double* eri, double drop_tol) {
+  if (K < 1 || K > 200) throw std::runtime_error("K out of range");
+  // 1) unique sorted terms with accumulated coefficients
+  std::unordered_map<uint64_t, double> terms;
+  terms.reserve((size_t)K * K * K * K);
+  auto add = [&](FOp* o, int n, double c) {
+    // zero operator: repeated creator or annihilator on the same spin-orbital
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j)
+        if (o[i].cre == o[j].cre && o[i].x == o[j].x) return;
+    int sg = stable_sort_sign(o, n);
+    terms[term_pack(o, n)] += sg * c;
+  };
+  for (int p = 0; p < K; ++p)
+    for (int q = 0; q < K; ++q) {
+      double c = h[p * K + q];
+      if (std::fabs(c) <= drop_tol) continue;
+      for (int s = 0; s < 2; ++s) {
+        FOp o[2] = {{1, (int16_t)(2 * p + s)}, {0, (int16_t)(2 * q + s)}};
+        add(o, 2, c);
+      }
+    }
+  for (int p = 0; p < K; ++p)
+    for (int q = 0; q < K; ++q)
+      for (int r = 0; r < K; ++r)
+        for (int s_ = 0; s_ < K; ++s_) {
+          double g = eri[((size_t)(p * K + q) * K + r) * K + s_];
+          if (std::fabs(g) <= drop_tol) continue;
+          for (int s = 0; s < 2; ++s)
+            for (int t = 0; t < 2; ++t) {
+              // 1/2 (pq|rs) a+_{ps} a+_{rt} a_{st} a_{qs}
+              FOp o[4] = {{1, (int16_t)(2 * p + s)}, {1, (int16_t)(2 * r + t)},
+                          {0, (int16_t)(2 * s_ + t)}, {0, (int16_t)(2 * q + s)}};
+              add(o, 4, 0.5 * g);
+            }
+        }
+
+  const int half = K / 2;
+  // 2) route every term
+  std::unordered_map<uint64_t, std::pair<int, int>> alive;  // key -> [first bond, last bond]
+  std::vector<std::unordered_map<std::pair<uint64_t, uint64_t>, EntryAcc, PairHash>> acc(K);
+  auto state_at = [&](const Term& t, int b) -> StateKey {
+    int e = 0;
+    for (int i = 0; i < t.n; ++i)
+      if (t.o[i].x / 2 < b) ++e;
+    StateKey k;
+    if (e == 0) { k.kind = 0; return k; }
+    if (e == t.n) { k.kind = 1; return k; }
+    if (t.n == 2 || e == 1) {
+      k.kind = 2; k.n = 1; k.ops[0] = t.o[0];
+      if (t.n == 2 && e != 1) throw std::logic_error("bad state");
+      return k;
+    }
+    if (e == 3) { k.kind = 3; k.n = 1; k.ops[0] = t.o[3]; return k; }
+    // e == 2 of 4
+    if (b <= half) { k.kind = 2; k.n = 2; k.ops[0] = t.o[0]; k.ops[1] = t.o[1]; }
+    else { k.kind = 3; k.n = 2; k.ops[0] = t.o[2]; k.ops[1] = t.o[3]; }
+    return k;
+  };
+  auto note_alive = [&](uint64_t key, int b) {
+    auto it = alive.find(key);
+    if (it == alive.end()) alive.emplace(key, std::make_pair(b, b));
+    else { it->second.first = std::min(it->second.first, b); it->second.second = std::max(it->second.second, b); }
+  };
+  Term t;
+  for (const auto& kv : terms) {
+    double c = kv.second;
+    if (std::fabs(c) <= drop_tol) continue;
+    term_unpack(kv.first, t);
+    StateKey prev = state_at(t, 0);
+    uint64_t pk = prev.pack();
+    note_alive(pk, 0);
+    for (int s = 0; s < K; ++s) {
+      StateKey nxt = state_at(t, s + 1);
+      uint64_t nk = nxt.pack();
+      FOp site_ops[4];
+      int ns = 0, later = 0;
+      for (int i = 0; i < t.n; ++i) {
+        int si = t.o[i].x / 2;
+        if (si == s) site_ops[ns++] = t.o[i];
+        else if (si > s) ++later;
+      }
+      if (nk != pk || ns > 0) {
+        note_alive(pk, s);
+        note_alive(nk, s + 1);
+        bool coef = (prev.kind == 0 || prev.kind == 2) && (nxt.kind == 1 || nxt.kind == 3);
+        double m[16];
+        local_op(site_ops, ns, s, later, m);
+        auto& slot = acc[s][std::make_pair(pk, nk)];
+        bool fresh = false;
+        if (slot.m[0] == 0 && slot.m[5] == 0 && slot.m[10] == 0 && slot.m[15] == 0) {
+          bool allz = true;
+          for (int i = 0; i < 16; ++i) if (slot.m[i] != 0) { allz = false; break; }
+          fresh = allz;
+        }
+        if (coef) {
+          for (int i = 0; i < 16; ++i) slot.m[i] += c * m[i];
+          slot.structural = false;
+        } else if (fresh) {
+          for (int i = 0; i < 16; ++i) slot.m[i] = m[i];
+          slot.structural = true;
+        }
+      }
+      prev = nxt;
+      pk = nk;
+    }
+    note_alive(pk, K);
+  }
+  // 3) bond state lists (deterministic order)
+  MPO mpo;
+  mpo.K = K;
+  mpo.bonds.resize(K + 1);
+  std::vector<std::unordered_map<uint64_t, int>> index(K + 1);
+  {
+    std::vector<std::vector<uint64_t>> keys(K + 1);
+    for (const auto& kv : alive)
+      for (int b = kv.second.first; b <= kv.second.second; ++b) keys[b].push_back(kv.first);
+    for (int b = 0; b <= K; ++b) {
+      auto& v = keys[b];
+      std::vector<BondState> st;
+      for (uint64_t kk : v) {
+        BondState bs;
+        bs.key = unpack_key(kk);
+        int da = 0, db = 0;
+        for (int i = 0; i < bs.key.n; ++i) {
+          int d = bs.key.ops[i].cre ? 1 : -1;
+          if (bs.key.ops[i].x & 1) db += d; else da += d;
+        }
+        if (bs.key.kind == 3) { da = -da; db = -db; }
+        bs.dna = da; bs.dnb = db;
+        bs.parity = bs.key.n & 1;
+        st.push_back(bs);
+      }
+      std::sort(st.begin(), st.end(), [](const BondState& a, const BondState& b2) {
+        if (a.dna != b2.dna) return a.dna < b2.dna;
+        if (a.dnb != b2.dnb) return a.dnb < b2.dnb;
+        return a.key.pack() < b2.key.pack();
+      });
+      for (size_t i = 0; i < st.size(); ++i) index[b][st[i].key.pack()] = (int)i;
+      mpo.bonds[b] = std::move(st);
+    }
+  }
+  // 4) entries: routed transitions + pass-throughs
+  mpo.W.resize(K);
+  for (int s = 0; s < K; ++s) {
+    auto& out = mpo.W[s];
+    for (const auto& kv : acc[s]) {
+      WEntry e;
+      e.row = index[s].at(kv.first.first);
+      e.col = index[s + 1].at(kv.first.second);
+      bool nz = false;
+      for (int i = 0; i < 16; ++i) { e.m[i] = kv.second.m[i]; if (std::fabs(e.m[i]) > 0) nz = true; }
+      if (nz) out.push_back(e);
+    }
+    for (const auto& kv : index[s]) {
+      auto it = index[s + 1].find(kv.first);
+      if (it == index[s + 1].end()) continue;
+      WEntry e;
+      e.row = kv.second;
+      e.col = it->second;
+      int par = mpo.bonds[s][kv.second].parity;
+      for (int i = 0; i < 16; ++i) e.m[i] = 0;
+      const double pz[4] = {1, -1, -1, 1};
+      for (int n = 0; n < 4; ++n) e.m[n * 5] = par ? pz[n] : 1.0;
+      out.push_back(e);
+    }
+    std::sort(out.begin(), out.end(), [](const WEntry& a, const WEntry& b) {
+      return a.col != b.col ? a.col < b.col : a.row < b.row;
+    });
+  }
+  return mpo;
+}
+
+void mpo_to_dense(const MPO& mpo, std::vector<double>& out) {
+  const int K = mpo.K;
+  if (K > 6) throw std::runtime_error("mpo_to_dense: K too large");
+  // T[state] is a (4^b x 4^b) matrix
+  std::vector<std::vector<double>> T(mpo.bonds[0].size());
+  int I0 = mpo.state_I(0);
+  T[I0] = {1.0};
+  size_t dim = 1;
+  for (int s = 0; s < K; ++s) {
+    size_t nd = dim * 4;
+    std::vector<std::vector<double>> Tn(mpo.bonds[s + 1].size());
+    for (const auto& e : mpo.W[s]) {
+      const auto& src = T[e.row];
+      if (src.empty()) continue;
+      auto& dst = Tn[e.col];
+      if (dst.empty()) dst.assign(nd * nd, 0.0);
+      for (size_t i = 0; i < dim; ++i)
+        for (size_t j = 0; j < dim; ++j) {
+          double v = src[i * dim + j];
+          if (v == 0) continue;
+          for (int n = 0; n < 4; ++n)
+            for (int np = 0; np < 4; ++np) {
+              double w = e.m[n * 4 + np];
+              if (w != 0) dst[(i * 4 + n) * nd + (j * 4 + np)] += v * w;
+            }
+        }
+    }
+    T.swap(Tn);
+    dim = nd;
+  }
+  int H = mpo.state_H(K);
+  out = T[H];
+}
+
+}  // namespace gbdmrg
