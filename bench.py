@@ -1,0 +1,338 @@
+"""Benchmark of the two-site DMRG hot path on GB300.
+
+One step = one full two-site update at the central bond of the K=40, N=40,
+S_z=0, M=2000 workload (the configuration the headline metric is quoted on):
+W-contracted operators, diagonal of H_eff, Davidson with a fixed iteration
+budget (each iteration one H_eff.psi), decimation to M states and the
+environment update of the new bond.  Inputs (integrals, a random QN-block MPS
+with bond dimension 2000 and its environments, tens of GB) are built before
+the timed region and stay resident in HBM; they are far larger than L2, so no
+explicit flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: the hot path of one problem is not sharded here (replicas only):
+each rank runs its own replica of the workload on its own GPU, value is the
+sum over ranks, time the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H_eff·ψ TFLOP/s & sweep s at K=40 M=2000, mixed vs FP64 GPU at |ΔE|≤1e-6 Eh"
+
+WORKLOADS = {
+    # name: K, N, two_sz, M, spread of the synthetic sector dimensions, integral seed, h off-diagonal std
+    "k40_m2000": dict(K=40, N=40, two_sz=0, M=2000, spread=1.0, seed=1607, offdiag_std=0.05),
+    "k24_m512": dict(K=24, N=24, two_sz=0, M=512, spread=1.0, seed=1606, offdiag_std=0.1),
+    "k16_m256": dict(K=16, N=16, two_sz=0, M=256, spread=1.0, seed=1606, offdiag_std=0.1),
+}
+# bounded CPU sample for the oracle: the projected-H_eff oracle works in the
+# full Fock space, so it can only take K <= 10; this is the largest sample of
+# the same kind of step (central two-site sigma) it finishes in seconds
+ORACLE_SAMPLE = dict(K=10, N=10, two_sz=0, M=1000, k=3, seed=1607, spread=0.5)
+
+
+def _measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(seconds: float = 12.0):
+    """Time the CPU oracle's sigma (P^T H P psi) on the bounded sample; returns
+    (sigma flops of the sample, seconds per sigma, calls)."""
+    import paper_1605_02611_gb300 as G
+    from oracle import mps as omps
+    from paper_1605_02611_gb300 import synth
+    s = ORACLE_SAMPLE
+    h, eri = synth.integrals(s["K"], s["seed"])
+    bonds, T = synth.random_mps(s["K"], s["N"], s["two_sz"], s["M"], s["seed"] + 1, s["spread"])
+    k = s["k"]
+    psi = synth.random_psi(bonds[k], bonds[k + 2], s["seed"] + 2)
+    Na = Nb = s["N"] // 2
+    flops = G.sigma_flops_host(h, eri, s["N"], s["two_sz"], k, bonds[k].labels(), bonds[k + 2].labels())
+    P = omps.TwoSiteProjector(T, k, Na, Nb)
+    omps.sigma(T, k, psi, h, eri, Na, Nb, P)  # warm-up (string tables)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        omps.sigma(T, k, psi, h, eri, Na, Nb, P)
+        n += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = (time.perf_counter() - t0) / n
+    return flops, dt, n
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        return max((x.get("num_threads") or 0) for x in threadpool_info()) or os.cpu_count()
+    except Exception:
+        return os.cpu_count()
+
+
+def dgemm_measured(torch):
+    """cuBLAS FP64 GEMM throughput on this GPU (context for the FP64 roofline)."""
+    n = 4096
+    a = torch.randn(n, n, device="cuda", dtype=torch.float64)
+    b = torch.randn(n, n, device="cuda", dtype=torch.float64)
+    for _ in range(2):
+        a @ b
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        a @ b
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return 2 * n ** 3 / best / 1e9
+
+
+def run_reference(args, rank, world):
+    """Oracle arm: the CPU oracle on a bounded sample of the workload (rank 0 only)."""
+    if rank != 0:
+        return
+    import paper_1605_02611_gb300 as G  # noqa: F401  (host-only flop count of the sample)
+    times = []
+    flops = None
+    for i in range(args.warmup + args.steps):
+        fl, dt, n = oracle_sample(seconds=3.0)
+        flops = fl
+        if i >= args.warmup:
+            times.append(dt)
+    dt = sum(times) / len(times)
+    value = flops / dt / 1e12
+    cores = blas_threads()
+    sample = (f"oracle sigma (P^T H P psi via direct CI) at K={ORACLE_SAMPLE['K']}, M={ORACLE_SAMPLE['M']}, "
+              f"sites ({ORACLE_SAMPLE['k']},{ORACLE_SAMPLE['k'] + 1}); the oracle cannot hold K=40")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_1605_02611_gb300 as G
+    from paper_1605_02611_gb300 import synth
+
+    torch.cuda.set_device(local_rank)
+    w = WORKLOADS[args.workload]
+    K, N, M = w["K"], w["N"], w["M"]
+    k = K // 2 - 1
+    t_setup = time.perf_counter()
+    h, eri = synth.integrals(K, w["seed"], w["offdiag_std"])
+    bonds, T = synth.random_isometric_mps(K, N, w["two_sz"], M, w["seed"] + 1, k, w["spread"])
+    stream = torch.cuda.Stream()
+    ctx = G.Context(h, eri, N, w["two_sz"], stream=stream.cuda_stream)
+    ctx.set_mps(T, [b.labels() for b in bonds])
+    del T
+    ctx.prepare(k)
+    nnz = ctx.nnz
+    setup_s = time.perf_counter() - t_setup
+    setup_launches = G.kernel_launches()
+    dav = args.dav_iters
+    if args.profile_sigma:
+        # profiling helper: only H_eff.psi calls on device buffers, then exit
+        x = torch.randn(nnz, device="cuda", dtype=torch.float64)
+        y = torch.empty_like(x)
+        for _ in range(args.profile_sigma):
+            ctx.sigma_device(x.data_ptr(), y.data_ptr())
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_sigma": args.profile_sigma, "setup_launches": setup_launches, "psi_nnz": nnz}))
+        ctx.close()
+        return
+
+    def step(psi_in=None, want=False):
+        return ctx.step(k, 0, M, 1e-14, dav, psi_in=psi_in, want_psi=want)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    c0 = ctx.counters()
+    l0 = G.kernel_launches()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    c1 = ctx.counters()
+    launches = G.kernel_launches() - l0
+    flops = (c1["sigma_flops"] - c0["sigma_flops"]) + (c1["other_flops"] - c0["other_flops"])
+    sig_fl = c1["sigma_flops"] - c0["sigma_flops"]
+    sig_s = c1["sigma_seconds"] - c0["sigma_seconds"]
+    sig_calls = c1["sigma_calls"] - c0["sigma_calls"]
+    # end to end through the public API with host buffers: psi in / optimised psi out
+    psi_host = np.zeros(nnz)
+    _, _, _, psi_host = step(want=True)
+    torch.cuda.synchronize()
+    ce0 = ctx.counters()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, _, _, out = step(psi_in=psi_host, want=True)
+    t_e2e = time.perf_counter() - t0
+    ce1 = ctx.counters()
+    e2e_flops = (ce1["sigma_flops"] - ce0["sigma_flops"]) + (ce1["other_flops"] - ce0["other_flops"])
+
+    t = torch.tensor([ms, flops, t_e2e, e2e_flops], dtype=torch.float64, device="cuda")
+    if world > 1:
+        mx = t.clone()
+        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+        sm = t.clone()
+        torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+        ms, t_e2e = float(mx[0]), float(mx[2])
+        flops, e2e_flops = float(sm[1]), float(sm[3])
+    if rank != 0:
+        return
+    value = flops / (ms * 1e-3) / 1e12
+    peaks, src = _measured_peaks()
+    # FP64 runs on the FP64 FMA units: peak = measured bf16 dense x nominal FP64/BF16 (1.25 / 2250)
+    peak_fp64 = peaks["bf16_tflops_sustained"] * 1.25 / 2250.0
+    achieved = sig_fl / sig_s / 1e12 if sig_s > 0 else None
+    dg = dgemm_measured(torch)
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: K={K} N={N} 2Sz={w['two_sz']} M={M}, two-site step at sites "
+                               f"({k},{k + 1}), Davidson {dav} iterations/step, FP64 path",
+                   "psi_nnz": nnz, "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (no flush)",
+                   "setup_s": round(setup_s, 1), "setup_launches": int(setup_launches)},
+        "sigma_tflops": achieved, "sigma_calls": sig_calls,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
+                     "frac": (achieved / peak_fp64) if achieved else None, "traffic": None,
+                     "kernel": "gemm_f64_kernel (sigma stages 1+2)",
+                     "peak_note": f"FP64 = {src} bf16 sustained x 1.25/2250; cuBLAS DGEMM here {dg:.3f} TFLOP/s"},
+        "e2e": {"value": e2e_flops / t_e2e / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": nnz * 8,
+                "d2h_bytes_per_step": nnz * 8},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        fl, dt, n = oracle_sample(seconds=args.cpu_seconds)
+        line["cpu_baseline"] = {
+            "value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": blas_threads(), "kind": "oracle",
+            "sample": f"{n} oracle sigmas (P^T H P psi, direct CI) at K={ORACLE_SAMPLE['K']}, "
+                      f"M={ORACLE_SAMPLE['M']}; the oracle works in the 4^K Fock space and cannot hold K=40"}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="k40_m2000", choices=sorted(WORKLOADS))
+    ap.add_argument("--dav-iters", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-sigma", type=int, default=0,
+                    help="after setup run this many H_eff.psi calls only (for ncu captures) and exit")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -111,6 +111,47 @@ gbdmrg_status gbdmrg_diag(gbdmrg_ctx* ctx, double* diag, int32_t on_device);
 gbdmrg_status gbdmrg_sigma_timing(gbdmrg_ctx* ctx, int32_t reps, const double* psi_dev, double* sigma_dev,
                                   double* ms_per_call);
 
+/* One two-site update at sites (k, k+1) with the environments the context
+ * holds for bonds k and k+2 (after gbdmrg_prepare(k), or after a previous
+ * step): diagonal of H_eff, Davidson solve (at most dav_max_iter iterations,
+ * residual norm dav_tol), decimation to at most M states, environment update
+ * of bond k+1 (direction 0: site k left-orthonormal, left environment;
+ * direction 1: site k+1 right-orthonormal, right environment).  Blocking,
+ * solving and decimation of Sec. "The DMRG in renormalization group language".
+ * psi_in (optional): start vector in the packed layout of gbdmrg_psi_layout
+ * for (k, k+1), else the product of the two current site tensors; psi_out
+ * (optional): the optimised packed psi.  Both host or both device pointers
+ * (on_device).  energy (optional): eigenvalue + ecore; discarded (optional):
+ * discarded weight; iters (optional): Davidson iterations. */
+gbdmrg_status gbdmrg_step(gbdmrg_ctx* ctx, int32_t k, int32_t direction, int32_t M, double dav_tol,
+                          int32_t dav_max_iter, const double* psi_in, double* psi_out, int32_t on_device,
+                          double* energy, double* discarded, int32_t* iters);
+/* Cumulative counters of the context: algorithmic sigma flops, sigma device
+ * seconds (CUDA events), number of sigma calls, algorithmic flops of all other
+ * grouped GEMMs (environment updates, diagonal, decimation).  Any may be NULL. */
+gbdmrg_status gbdmrg_counters(gbdmrg_ctx* ctx, double* sigma_flops, double* sigma_seconds, int64_t* sigma_calls,
+                              double* other_flops);
+/* Number of CUDA kernel launches issued by this library in this process. */
+int64_t gbdmrg_kernel_launches(void);
+
+/* Self-test of the tensor-core grouped block GEMM used by the mixed-precision
+ * sigma (tcgen05, BF16 operands, FP32 accumulation).  For every task i:
+ *   C_i (+)= sum_{t in [t0_i, t1_i)} (-1)^neg_t A_t B_t^T
+ * with C_i fp32 row-major (m_i x n_i, ldc_i), A_t (m_i x k_t) and B_t (n_i x k_t)
+ * row-major bf16, 16-byte aligned, leading dimensions multiples of 8 and zero
+ * padding between k_t and the leading dimension.  All matrix pointers are
+ * device pointers; the descriptor arrays are host arrays:
+ * tasks[8*i] = (C, ldc, m, n, beta, t0, t1, 0), terms[6*t] = (A, B, lda, ldb, k, neg).
+ * GBDMRG_ETIMEOUT if a bounded wait inside the kernel ran out. */
+gbdmrg_status gbdmrg_gemm_bf16_selftest(const int64_t* tasks, int32_t ntasks, const int64_t* terms, int32_t nterms,
+                                        void* stream);
+
+/* Host only: algorithmic flop count of one sigma at sites (k, k+1) when bond k
+ * has labels qn_l[2*Dl] and bond k+2 has qn_r[2*Dr] (sum 2mnk over non-zero
+ * blocks, the count gbdmrg_sigma reports). */
+gbdmrg_status gbdmrg_sigma_flops_host(const gbdmrg_problem* prob, int32_t k, int32_t Dl, const int32_t* qn_l,
+                                      int32_t Dr, const int32_t* qn_r, double* flops);
+
 /* Sweep schedule (Sec. "The DMRG in renormalization group language"):
  * nsweeps sweeps, sweep s keeps at most M[s] states and converges Davidson
  * to residual norm dav_tol[s].  One sweep = left-to-right over k = 0..K-3

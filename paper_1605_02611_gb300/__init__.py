@@ -50,6 +50,11 @@ SIGNATURES = {
     "gbdmrg_sigma": (C.c_int, [_P, _P, _P, _I32, _PD]),
     "gbdmrg_diag": (C.c_int, [_P, _P, _I32]),
     "gbdmrg_sigma_timing": (C.c_int, [_P, _I32, _P, _P, _PD]),
+    "gbdmrg_step": (C.c_int, [_P, _I32, _I32, _I32, C.c_double, _I32, _P, _P, _I32, _PD, _PD, _PI32]),
+    "gbdmrg_counters": (C.c_int, [_P, _PD, _PD, _PI64, _PD]),
+    "gbdmrg_kernel_launches": (C.c_int64, []),
+    "gbdmrg_gemm_bf16_selftest": (C.c_int, [_PI64, _I32, _PI64, _I32, _P]),
+    "gbdmrg_sigma_flops_host": (C.c_int, [C.POINTER(Problem), _I32, _I32, _PI32, _I32, _PI32, _PD]),
     "gbdmrg_run": (C.c_int, [_P, C.POINTER(Schedule), _PD, _PD]),
     "gbdmrg_run_stats": (C.c_int, [_P, _PD, _PD, _PD, _PI32]),
 }
@@ -94,6 +99,38 @@ def mpo_build_host(h1, eri, N: int, two_sz: int = 0, dense: bool = False):
     if st != 0:
         raise GbdmrgError(f"gbdmrg_mpo_build_host failed: {STATUS.get(st, st)}")
     return dims, out
+
+
+def kernel_launches() -> int:
+    """CUDA kernel launches issued by the library so far in this process."""
+    return int(load().gbdmrg_kernel_launches())
+
+
+def gemm_bf16_selftest(tasks: np.ndarray, terms: np.ndarray, stream: int = 0) -> None:
+    """Run the tensor-core grouped GEMM on device buffers (see include/gbdmrg.h)."""
+    lib = load()
+    tasks = np.ascontiguousarray(tasks, dtype=np.int64)
+    terms = np.ascontiguousarray(terms, dtype=np.int64)
+    st = lib.gbdmrg_gemm_bf16_selftest(tasks.ctypes.data_as(_PI64), len(tasks), terms.ctypes.data_as(_PI64),
+                                       len(terms), _P(stream))
+    if st != 0:
+        raise GbdmrgError(f"gbdmrg_gemm_bf16_selftest failed: {STATUS.get(st, st)}")
+
+
+def sigma_flops_host(h1, eri, N: int, two_sz: int, k: int, lab_l, lab_r) -> float:
+    """Algorithmic flops of one sigma at sites (k, k+1) (host only, no GPU)."""
+    lib = load()
+    h1 = np.ascontiguousarray(h1, dtype=np.float64)
+    eri = np.ascontiguousarray(eri, dtype=np.float64)
+    prob = Problem(h1.shape[0], N, two_sz, _dptr(h1), _dptr(eri), 0.0)
+    ql = np.ascontiguousarray(lab_l, dtype=np.int32).reshape(-1)
+    qr = np.ascontiguousarray(lab_r, dtype=np.int32).reshape(-1)
+    fl = C.c_double()
+    st = lib.gbdmrg_sigma_flops_host(C.byref(prob), k, len(ql) // 2, ql.ctypes.data_as(_PI32), len(qr) // 2,
+                                     qr.ctypes.data_as(_PI32), C.byref(fl))
+    if st != 0:
+        raise GbdmrgError(f"gbdmrg_sigma_flops_host failed: {STATUS.get(st, st)}")
+    return fl.value
 
 
 class Context:
@@ -209,6 +246,32 @@ class Context:
         d = np.zeros(self.nnz)
         self._check(self.lib.gbdmrg_diag(self.h, d.ctypes.data_as(_P), 0), "diag")
         return d
+
+    def step(self, k: int, direction: int, M: int, tol: float, max_iter: int, psi_in=None, want_psi=False,
+             on_device: bool = False):
+        """One two-site update (gbdmrg_step).  Host numpy (or device pointers if on_device)."""
+        e, d, it = C.c_double(), C.c_double(), C.c_int32()
+        pin = pout = None
+        out = None
+        if on_device:
+            pin = _P(psi_in) if psi_in is not None else None
+            pout = _P(want_psi) if want_psi else None
+        else:
+            if psi_in is not None:
+                psi_in = np.ascontiguousarray(psi_in, dtype=np.float64)
+                pin = psi_in.ctypes.data_as(_P)
+            if want_psi:
+                out = np.zeros(self.nnz)
+                pout = out.ctypes.data_as(_P)
+        self._check(self.lib.gbdmrg_step(self.h, k, direction, M, tol, max_iter, pin, pout, int(on_device),
+                                         C.byref(e), C.byref(d), C.byref(it)), "step")
+        return e.value, d.value, it.value, out
+
+    def counters(self):
+        f, s, o = C.c_double(), C.c_double(), C.c_double()
+        n = C.c_int64()
+        self._check(self.lib.gbdmrg_counters(self.h, C.byref(f), C.byref(s), C.byref(n), C.byref(o)), "counters")
+        return dict(sigma_flops=f.value, sigma_seconds=s.value, sigma_calls=n.value, other_flops=o.value)
 
     # ---- sweeps
     def run(self, M, dav_tol, max_iter: int = 200):

@@ -6,6 +6,7 @@
 
 #include "../../include/gbdmrg.h"
 #include "engine.hpp"
+#include "kernels_tc.hpp"
 
 struct gbdmrg_ctx {
   gbdmrg::Context c;
@@ -259,6 +260,129 @@ gbdmrg_status gbdmrg_sigma_timing(gbdmrg_ctx* ctx, int32_t reps, const double* p
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     *ms_per_call = ms / reps;
+  });
+}
+
+gbdmrg_status gbdmrg_step(gbdmrg_ctx* ctx, int32_t k, int32_t direction, int32_t M, double dav_tol,
+                          int32_t dav_max_iter, const double* psi_in, double* psi_out, int32_t on_device,
+                          double* energy, double* discarded, int32_t* iters) {
+  if (!ctx || M <= 0 || !(dav_tol > 0) || (direction != 0 && direction != 1)) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    auto& c = ctx->c;
+    if (k < 0 || k + 1 >= c.K) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "two-site position out of range");
+    gbdmrg::DavidsonOpts o;
+    o.tol = dav_tol;
+    o.max_iter = dav_max_iter > 0 ? dav_max_iter : 200;
+    gbdmrg::DArr<double> din, dout;
+    const double* p0 = nullptr;
+    double* p1 = nullptr;
+    if (psi_in || psi_out) {
+      if (!c.left[k].valid || !c.right[k + 2].valid)
+        throw gbdmrg::Error(gbdmrg::ST_ESTATE, "environments of the two-site step are not built");
+      gbdmrg::PsiLayout P;
+      P.build(c.left[k].bond, c.right[k + 2].bond);
+      if (psi_in) {
+        if (on_device) p0 = psi_in;
+        else {
+          din.alloc(P.nnz, c.stream);
+          gbdmrg::cuda_check(cudaMemcpyAsync(din.p, psi_in, P.nnz * sizeof(double), cudaMemcpyHostToDevice, c.stream),
+                             "h2d");
+          p0 = din.p;
+        }
+      }
+      if (psi_out) {
+        if (on_device) p1 = psi_out;
+        else {
+          dout.alloc(P.nnz, c.stream);
+          p1 = dout.p;
+        }
+      }
+    }
+    int it = 0;
+    double dw = 0;
+    long nnz = 0;
+    double e = gbdmrg::two_site_step(c, k, direction, M, o, false, &it, &dw, p0, p1, &nnz);
+    if (psi_out && !on_device)
+      gbdmrg::cuda_check(cudaMemcpy(psi_out, dout.p, nnz * sizeof(double), cudaMemcpyDeviceToHost), "d2h");
+    if (energy) *energy = e + c.ecore;
+    if (discarded) *discarded = dw;
+    if (iters) *iters = it;
+  });
+}
+
+int64_t gbdmrg_kernel_launches(void) { return (int64_t)(gbdmrg::launch_count() + gbdmrg::tc_launch_count()); }
+
+gbdmrg_status gbdmrg_gemm_bf16_selftest(const int64_t* tasks, int32_t ntasks, const int64_t* terms, int32_t nterms,
+                                        void* stream) {
+  if (!tasks || !terms || ntasks <= 0 || nterms <= 0) return GBDMRG_EINVAL;
+  return guard(nullptr, [&] {
+    using namespace gbdmrg;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<TcTask> ta(ntasks);
+    std::vector<TcTerm> te(nterms);
+    std::vector<TcTile> ti;
+    for (int i = 0; i < nterms; ++i) {
+      const int64_t* r = terms + 6 * i;
+      te[i] = {(const __nv_bfloat16*)r[0], (const __nv_bfloat16*)r[1], (int)r[2], (int)r[3], (int)r[4], (int)r[5]};
+      if ((r[0] | r[1]) & 15 || r[2] % 8 || r[3] % 8 || r[4] <= 0 || r[4] > r[2] || r[4] > r[3])
+        throw Error(ST_EINVAL, "bf16 operands must be 16-byte aligned, ld % 8 == 0, 0 < k <= ld");
+    }
+    for (int i = 0; i < ntasks; ++i) {
+      const int64_t* r = tasks + 8 * i;
+      ta[i] = {(float*)r[0], nullptr, 0, (int)r[1], 0, (int)r[2], (int)r[3], (int)r[4], 0, (int)r[5], (int)r[6]};
+      if (ta[i].t0 < 0 || ta[i].t1 > nterms || ta[i].t0 >= ta[i].t1 || ta[i].m <= 0 || ta[i].n <= 0)
+        throw Error(ST_EINVAL, "bad task");
+      for (int r0 = 0; r0 < ta[i].m; r0 += TC_TILE_M)
+        for (int c0 = 0; c0 < ta[i].n; c0 += TC_TILE_N) ti.push_back({i, r0, c0});
+    }
+    DArr<TcTask> dta;
+    DArr<TcTerm> dte;
+    DArr<TcTile> dti;
+    DArr<int> derr;
+    dta.upload(ta, st);
+    dte.upload(te, st);
+    dti.upload(ti, st);
+    derr.alloc(1, st);
+    cuda_check(cudaMemsetAsync(derr.p, 0, sizeof(int), st), "memset");
+    cuda_check(launch_gemm_bf16_tc(dti.p, (int)ti.size(), dta.p, dte.p, derr.p, st), "tc gemm launch");
+    int herr = 0;
+    cuda_check(cudaMemcpyAsync(&herr, derr.p, sizeof(int), cudaMemcpyDeviceToHost, st), "d2h");
+    cuda_check(cudaStreamSynchronize(st), "sync");
+    if (herr) throw Error(ST_ETIMEOUT, "tensor-core GEMM: a bounded wait ran out");
+  });
+}
+
+gbdmrg_status gbdmrg_counters(gbdmrg_ctx* ctx, double* sigma_flops, double* sigma_seconds, int64_t* sigma_calls,
+                              double* other_flops) {
+  if (!ctx) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    auto& c = ctx->c;
+    if (sigma_flops) *sigma_flops = c.sigma_flops_total;
+    if (sigma_seconds) *sigma_seconds = c.sigma_time_total;
+    if (sigma_calls) *sigma_calls = c.sigma_calls;
+    if (other_flops) *other_flops = c.other_flops_total;
+  });
+}
+
+gbdmrg_status gbdmrg_sigma_flops_host(const gbdmrg_problem* prob, int32_t k, int32_t Dl, const int32_t* qn_l,
+                                      int32_t Dr, const int32_t* qn_r, double* flops) {
+  if (!flops || !qn_l || !qn_r || Dl <= 0 || Dr <= 0) return GBDMRG_EINVAL;
+  return guard(nullptr, [&] {
+    check_problem(prob);
+    if (k < 0 || k + 1 >= prob->K) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "two-site position out of range");
+    gbdmrg::MPO m = gbdmrg::build_mpo(prob->K, prob->h1, prob->eri);
+    auto bond = [](int D, const int32_t* q) {
+      gbdmrg::Bond b;
+      int i = 0;
+      while (i < D) {
+        int j = i;
+        while (j < D && q[2 * j] == q[2 * i] && q[2 * j + 1] == q[2 * i + 1]) ++j;
+        b.add(q[2 * i], q[2 * i + 1], j - i);
+        i = j;
+      }
+      return b;
+    };
+    *flops = gbdmrg::count_sigma_flops(m, k, bond(Dl, qn_l), bond(Dr, qn_r));
   });
 }
 

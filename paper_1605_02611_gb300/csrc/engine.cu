@@ -161,6 +161,7 @@ void GemmPlan::run(cudaStream_t s) const {
 
 static void run_builder(Context& c, GemmBuilder& g) {
   if (g.tasks.empty()) return;
+  c.other_flops_total += g.flops;
   GemmPlan p;
   p.upload(g.tiles, g.tasks, g.terms, c.stream);
   p.run(c.stream);
@@ -190,6 +191,8 @@ Context::~Context() {
   plan = SigmaPlan();
   if (stream) cudaStreamSynchronize(stream);
   if (solver) cusolverDnDestroy(solver);
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
   if (own_stream && stream) cudaStreamDestroy(stream);
 }
 
@@ -204,6 +207,8 @@ void ctx_init(Context& c) {
   cuda_check(cudaDeviceGetDefaultMemPool(&pool, dev), "mem pool");
   uint64_t thr = UINT64_MAX;
   cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  cuda_check(cudaEventCreate(&c.ev0), "event");
+  cuda_check(cudaEventCreate(&c.ev1), "event");
   solver_check(cusolverDnCreate(&c.solver), "cusolverDnCreate");
   solver_check(cusolverDnSetStream(c.solver, c.stream), "cusolverDnSetStream");
   c.mpo = build_mpo(c.K, c.h1.data(), c.eri.data());
@@ -862,11 +867,13 @@ double davidson(Context& c, SigmaPlan& plan, const double* diag, double* psi, co
   dh.init(ms, c.stream);
   std::vector<double> G((size_t)ms * ms, 0.0);
   auto sigma_of = [&](const double* in, double* out) {
-    auto t0 = std::chrono::steady_clock::now();
+    cuda_check(cudaEventRecord(c.ev0, c.stream), "record");
     run_sigma(c, plan, in, out);
-    cuda_check(cudaStreamSynchronize(c.stream), "sync");
-    auto t1 = std::chrono::steady_clock::now();
-    c.sigma_time_total += std::chrono::duration<double>(t1 - t0).count();
+    cuda_check(cudaEventRecord(c.ev1, c.stream), "record");
+    cuda_check(cudaEventSynchronize(c.ev1), "sync");
+    float ms = 0;
+    cuda_check(cudaEventElapsedTime(&ms, c.ev0, c.ev1), "elapsed");
+    c.sigma_time_total += 1e-3 * ms;
     c.sigma_flops_total += plan.flops;
     c.sigma_calls++;
   };
@@ -1212,6 +1219,91 @@ void right_canonicalize(Context& c) {
 
 // ---------------------------------------------------------------- sweeps
 
+double two_site_step(Context& c, int k, int dir, int M, const DavidsonOpts& o, bool free_used, int* iters,
+                     double* discarded, const double* psi0, double* psi_out, long* nnz_out) {
+  if (!c.left[k].valid || !c.right[k + 2].valid)
+    throw Error(ST_ESTATE, "environments of the two-site step are not built");
+  Tilde lt, rt;
+  build_tilde_left(c, c.left[k], k, lt);
+  build_tilde_right(c, c.right[k + 2], k + 1, rt);
+  SigmaPlan plan;
+  build_sigma_plan(c, lt, rt, k, plan);
+  DArr<double> psi, diag;
+  psi.alloc(plan.psi.nnz, c.stream);
+  diag.alloc(plan.psi.nnz, c.stream);
+  if (psi0)
+    cuda_check(cudaMemcpyAsync(psi.p, psi0, plan.psi.nnz * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "d2d");
+  else
+    make_psi(c, c.sites[k], c.sites[k + 1], plan.psi, psi.p);
+  compute_diag(c, lt, rt, k, plan.psi, diag.p);
+  double e = davidson(c, plan, diag.p, psi.p, o, iters);
+  if (psi_out)
+    cuda_check(cudaMemcpyAsync(psi_out, psi.p, plan.psi.nnz * sizeof(double), cudaMemcpyDeviceToDevice, c.stream),
+               "d2d");
+  if (nnz_out) *nnz_out = plan.psi.nnz;
+  SiteT A, B;
+  double dw = decimate(c, plan.psi, psi.p, M, dir, A, B);
+  if (discarded) *discarded = dw;
+  c.sites[k] = std::move(A);
+  c.sites[k + 1] = std::move(B);
+  if (dir == 0) {
+    env_update_left(c, lt, c.sites[k], k, c.left[k + 1]);
+    if (free_used) c.right[k + 2] = Env();
+  } else {
+    env_update_right(c, rt, c.sites[k + 1], k + 1, c.right[k + 1]);
+    if (free_used) c.left[k + 1] = Env();
+  }
+  cuda_check(cudaStreamSynchronize(c.stream), "sync");
+  c.prepared = -1;
+  return e;
+}
+
+double count_sigma_flops(const MPO& mpo, int k, const Bond& Lb, const Bond& Rb) {
+  const auto& mid = mpo.bonds[k + 1];
+  // which (n, n') site-operator slots of the W-contracted operators are non-zero
+  std::vector<std::array<char, 16>> lref(mid.size()), rref(mid.size());
+  for (auto& a : lref) a.fill(0);
+  for (auto& a : rref) a.fill(0);
+  for (const auto& e : mpo.W[k])
+    for (int nn = 0; nn < 16; ++nn)
+      if (e.m[nn] != 0.0) lref[e.col][nn] = 1;
+  for (const auto& e : mpo.W[k + 1])
+    for (int nn = 0; nn < 16; ++nn)
+      if (e.m[nn] != 0.0) rref[e.row][nn] = 1;
+  double fl = 0;
+  for (size_t beta = 0; beta < mid.size(); ++beta) {
+    const int da = mid[beta].dna, db = mid[beta].dnb;
+    std::vector<char> xhas((size_t)Lb.nsec() * 16, 0);
+    for (int qlp = 0; qlp < Lb.nsec(); ++qlp)
+      for (int n1p = 0; n1p < 4; ++n1p)
+        for (int n2 = 0; n2 < 4; ++n2) {
+          int qr = Rb.find(Lb.qa[qlp] + LQA[n1p] + LQA[n2] + da, Lb.qb[qlp] + LQB[n1p] + LQB[n2] + db);
+          if (qr < 0) continue;
+          for (int n2p = 0; n2p < 4; ++n2p) {
+            if (!rref[beta][n2 * 4 + n2p]) continue;
+            int qrp = Rb.find(Lb.qa[qlp] + LQA[n1p] + LQA[n2p], Lb.qb[qlp] + LQB[n1p] + LQB[n2p]);
+            if (qrp < 0) continue;
+            fl += 2.0 * Rb.dim[qr] * Lb.dim[qlp] * Rb.dim[qrp];
+            xhas[(qlp * 4 + n1p) * 4 + n2] = 1;
+          }
+        }
+    for (int ql = 0; ql < Lb.nsec(); ++ql)
+      for (int n1 = 0; n1 < 4; ++n1)
+        for (int n2 = 0; n2 < 4; ++n2) {
+          int qr = Rb.find(Lb.qa[ql] + LQA[n1] + LQA[n2], Lb.qb[ql] + LQB[n1] + LQB[n2]);
+          if (qr < 0) continue;
+          for (int n1p = 0; n1p < 4; ++n1p) {
+            if (!lref[beta][n1 * 4 + n1p]) continue;
+            // the W-contracted operator changes the quantum number by dQ_beta - q(n1) + q(n1')
+            int qlp = Lb.find(Lb.qa[ql] - (da - LQA[n1] + LQA[n1p]), Lb.qb[ql] - (db - LQB[n1] + LQB[n1p]));
+            if (qlp < 0 || !xhas[(qlp * 4 + n1p) * 4 + n2]) continue;
+            fl += 2.0 * Lb.dim[ql] * Rb.dim[qr] * Lb.dim[qlp];
+          }
+        }
+  }
+  return fl;
+}
+
 void run_sweeps(Context& c, int nsweeps, const int* M, const double* tol, int max_iter, SweepStats& st) {
   if (c.K < 3) throw Error(ST_EINVAL, "sweeps need K >= 3");
   for (int j = 0; j < c.K; ++j)
@@ -1236,31 +1328,11 @@ void run_sweeps(Context& c, int nsweeps, const int* M, const double* tol, int ma
     o.tol = tol[s];
     o.max_iter = max_iter;
     auto step = [&](int k, int dir) {
-      Tilde lt, rt;
-      build_tilde_left(c, c.left[k], k, lt);
-      build_tilde_right(c, c.right[k + 2], k + 1, rt);
-      SigmaPlan plan;
-      build_sigma_plan(c, lt, rt, k, plan);
-      DArr<double> psi, diag;
-      psi.alloc(plan.psi.nnz, c.stream);
-      diag.alloc(plan.psi.nnz, c.stream);
-      make_psi(c, c.sites[k], c.sites[k + 1], plan.psi, psi.p);
-      compute_diag(c, lt, rt, k, plan.psi, diag.p);
       int it = 0;
-      e = davidson(c, plan, diag.p, psi.p, o, &it);
+      double dw = 0;
+      e = two_site_step(c, k, dir, M[s], o, true, &it, &dw);
       iters += it;
-      SiteT A, B;
-      double dw = decimate(c, plan.psi, psi.p, M[s], dir, A, B);
       dmax = std::max(dmax, dw);
-      c.sites[k] = std::move(A);
-      c.sites[k + 1] = std::move(B);
-      if (dir == 0) {
-        env_update_left(c, lt, c.sites[k], k, c.left[k + 1]);
-        c.right[k + 2] = Env();
-      } else {
-        env_update_right(c, rt, c.sites[k + 1], k + 1, c.right[k + 1]);
-        c.left[k + 1] = Env();
-      }
     };
     for (int k = 0; k <= K - 3; ++k) step(k, 0);
     if (!c.right[K].valid) env_boundary_right(c, c.right[K]);

@@ -194,9 +194,12 @@ struct Context {
   SigmaPlan plan;
   bool have_plan = false;
 
-  // counters
-  double sigma_flops_total = 0, sigma_time_total = 0;
+  // counters: sigma flops / device seconds (CUDA events on the context stream),
+  // and the algorithmic flops of every other grouped GEMM (environments, diagonal,
+  // decimation)
+  double sigma_flops_total = 0, sigma_time_total = 0, other_flops_total = 0;
   long sigma_calls = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int chunk_budget_mb = 2048;
 
   ~Context();
@@ -231,6 +234,17 @@ double davidson(Context& c, SigmaPlan& plan, const double* diag, double* psi, co
 // 1 = right-move (A[k] = U S, A[k+1] = V^T).  Returns discarded weight.
 double decimate(Context& c, const PsiLayout& P, const double* psi, int M, int direction, SiteT& left,
                 SiteT& right);
+
+// One two-site step at sites (k, k+1) (blocking, solving, decimation of Sec. "The
+// DMRG in renormalization group language"); needs left[k] and right[k+2].
+// psi0/psi_out (optional, device, packed) override the start vector / receive
+// the optimised one.  Returns the Davidson eigenvalue (without ecore).
+double two_site_step(Context& c, int k, int dir, int M, const DavidsonOpts& o, bool free_used, int* iters,
+                     double* discarded, const double* psi0 = nullptr, double* psi_out = nullptr,
+                     long* nnz_out = nullptr);
+// Algorithmic flops (sum 2mnk over non-zero blocks) of one sigma at sites
+// (k, k+1) for the given bonds k and k+2 -- host only, equals SigmaPlan::flops.
+double count_sigma_flops(const MPO& mpo, int k, const Bond& Lb, const Bond& Rb);
 
 void right_canonicalize(Context& c);
 void run_sweeps(Context& c, int nsweeps, const int* M, const double* tol, int max_iter, SweepStats& st);

@@ -9,6 +9,8 @@
 // the result is deterministic.
 #include "kernels.hpp"
 
+#include <atomic>
+
 namespace gbdmrg {
 
 namespace {
@@ -164,11 +166,16 @@ inline int grid_for(long n, int per = 256, int cap = 152 * 16) {
   return (int)g;
 }
 
+std::atomic<long> g_launches{0};
+
 }  // namespace
+
+long launch_count() { return g_launches.load(); }
 
 void launch_gemm(const GemmTile* d_tiles, int ntiles, const GemmTask* d_tasks, const GemmTerm* d_terms,
                  cudaStream_t s) {
   if (ntiles <= 0) return;
+  ++g_launches;
   gemm_f64_kernel<<<ntiles, 256, 0, s>>>(d_tiles, d_tasks, d_terms);
 }
 
@@ -178,6 +185,7 @@ void launch_combo(const ComboOut* d_outs, int nouts, long max_nnz, const ComboTe
     int no = nouts - o0 < 65535 ? nouts - o0 : 65535;
     dim3 g(grid_for(max_nnz, 256, 64), no);
     combo_kernel<<<g, 256, 0, s>>>(d_outs + o0, d_terms);
+    ++g_launches;
   }
 }
 
@@ -187,16 +195,19 @@ void launch_copy(const CopyJob* d_jobs, int njobs, int max_elems, cudaStream_t s
     int no = njobs - o0 < 65535 ? njobs - o0 : 65535;
     dim3 g(grid_for(max_elems, 256, 64), no);
     copy_kernel<<<g, 256, 0, s>>>(d_jobs + o0);
+    ++g_launches;
   }
 }
 
 void launch_fill(double* p, long n, double v, cudaStream_t s) {
   if (n <= 0) return;
+  ++g_launches;
   fill_kernel<<<grid_for(n), 256, 0, s>>>(p, n, v);
 }
 
 void launch_axpby(long n, double a, const double* x, double b, double* y, cudaStream_t s) {
   if (n <= 0) return;
+  ++g_launches;
   axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, a, x, b, y);
 }
 
@@ -206,17 +217,20 @@ void launch_multidot(const double* V, long ldv, int m, const double* x, long n, 
   dim3 g(nblk, m);
   multidot_part_kernel<<<g, 256, 0, s>>>(V, ldv, x, n, d_part);
   multidot_final_kernel<<<(m + 63) / 64, 64, 0, s>>>(d_part, nblk, m, d_out);
+  g_launches += 2;
 }
 
 void launch_combine_vectors(const double* V, long ldv, int m, const double* d_c, long n, double* y,
                             cudaStream_t s) {
   if (n <= 0) return;
+  ++g_launches;
   combine_vectors_kernel<<<grid_for(n), 256, 0, s>>>(V, ldv, m, d_c, n, y);
 }
 
 void launch_precond(long n, const double* r, const double* diag, double theta, double eps, double* t,
                     cudaStream_t s) {
   if (n <= 0) return;
+  ++g_launches;
   precond_kernel<<<grid_for(n), 256, 0, s>>>(n, r, diag, theta, eps, t);
 }
 
@@ -226,6 +240,7 @@ void launch_diag_extract(const DiagJob* d_jobs, int njobs, int max_rows, cudaStr
     int no = njobs - o0 < 65535 ? njobs - o0 : 65535;
     dim3 g(grid_for(max_rows, 128, 16), no);
     diag_extract_kernel<<<g, 128, 0, s>>>(d_jobs + o0);
+    ++g_launches;
   }
 }
 

@@ -49,6 +49,9 @@ struct CopyJob {
   double alpha;
 };
 
+// number of kernel launches issued by this library (all launch wrappers)
+long launch_count();
+
 void launch_gemm(const GemmTile* d_tiles, int ntiles, const GemmTask* d_tasks,
                  const GemmTerm* d_terms, cudaStream_t s);
 void launch_combo(const ComboOut* d_outs, int nouts, long max_nnz, const ComboTerm* d_terms,

@@ -1,0 +1,32 @@
+// Tensor-core grouped block GEMM (tcgen05, BF16 in, FP32 accumulate).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace gbdmrg {
+
+// C[m x n] (+)= sum_t (-1)^{neg_t} A_t[m x k_t] B_t[n x k_t]^T; A, B row-major bf16 with
+// leading dimensions (elements) multiples of 8, 16-byte aligned, zero padding up to ld.
+struct TcTerm {
+  const __nv_bfloat16* A;
+  const __nv_bfloat16* B;
+  int lda, ldb, k, flags;  // flags bit 0: negate
+};
+// outputs: C (fp32, optional, += if beta) and/or Cb (bf16, optional): nslices bf16
+// slices x = s0 + s1 + s2 written slice_stride elements apart
+struct TcTask {
+  float* C;
+  __nv_bfloat16* Cb;
+  long slice_stride;
+  int ldc, ldcb, m, n, beta, nslices, t0, t1;
+};
+struct TcTile {
+  int task, r0, c0;
+};
+constexpr int TC_TILE_M = 128, TC_TILE_N = 128;
+
+cudaError_t launch_gemm_bf16_tc(const TcTile* d_tiles, int ntiles, const TcTask* d_tasks, const TcTerm* d_terms,
+                                int* d_err, cudaStream_t s);
+long tc_launch_count();
+
+}  // namespace gbdmrg

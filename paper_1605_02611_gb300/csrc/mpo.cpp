@@ -196,12 +196,19 @@ MPO build_mpo(int K, const double* h, const double* eri, double drop_tol) {
     double c = kv.second;
     if (std::fabs(c) <= drop_tol) continue;
     term_unpack(kv.first, t);
-    StateKey prev = state_at(t, 0);
-    uint64_t pk = prev.pack();
-    note_alive(pk, 0);
-    for (int s = 0; s < K; ++s) {
-      StateKey nxt = state_at(t, s + 1);
-      uint64_t nk = nxt.pack();
+    // the state only changes at sites carrying operators of the term and at the
+    // switch site K/2, so only those sites are visited
+    int ev[5], nev = 0;
+    for (int i = 0; i < t.n; ++i) ev[nev++] = t.o[i].x / 2;
+    if (half < K) ev[nev++] = half;
+    std::sort(ev, ev + nev);
+    nev = (int)(std::unique(ev, ev + nev) - ev);
+    note_alive(state_at(t, 0).pack(), 0);
+    note_alive(state_at(t, K).pack(), K);
+    for (int e = 0; e < nev; ++e) {
+      const int s = ev[e];
+      StateKey prev = state_at(t, s), nxt = state_at(t, s + 1);
+      uint64_t pk = prev.pack(), nk = nxt.pack();
       FOp site_ops[4];
       int ns = 0, later = 0;
       for (int i = 0; i < t.n; ++i) {
@@ -209,31 +216,21 @@ MPO build_mpo(int K, const double* h, const double* eri, double drop_tol) {
         if (si == s) site_ops[ns++] = t.o[i];
         else if (si > s) ++later;
       }
-      if (nk != pk || ns > 0) {
-        note_alive(pk, s);
-        note_alive(nk, s + 1);
-        bool coef = (prev.kind == 0 || prev.kind == 2) && (nxt.kind == 1 || nxt.kind == 3);
-        double m[16];
-        local_op(site_ops, ns, s, later, m);
-        auto& slot = acc[s][std::make_pair(pk, nk)];
-        bool fresh = false;
-        if (slot.m[0] == 0 && slot.m[5] == 0 && slot.m[10] == 0 && slot.m[15] == 0) {
-          bool allz = true;
-          for (int i = 0; i < 16; ++i) if (slot.m[i] != 0) { allz = false; break; }
-          fresh = allz;
-        }
-        if (coef) {
-          for (int i = 0; i < 16; ++i) slot.m[i] += c * m[i];
-          slot.structural = false;
-        } else if (fresh) {
-          for (int i = 0; i < 16; ++i) slot.m[i] = m[i];
-          slot.structural = true;
-        }
+      if (nk == pk && ns == 0) continue;
+      note_alive(pk, s);
+      note_alive(nk, s + 1);
+      bool coef = (prev.kind == 0 || prev.kind == 2) && (nxt.kind == 1 || nxt.kind == 3);
+      double m[16];
+      local_op(site_ops, ns, s, later, m);
+      auto& slot = acc[s][std::make_pair(pk, nk)];
+      if (coef) {
+        for (int i = 0; i < 16; ++i) slot.m[i] += c * m[i];
+        slot.structural = false;
+      } else if (!slot.structural) {
+        for (int i = 0; i < 16; ++i) slot.m[i] = m[i];
+        slot.structural = true;
       }
-      prev = nxt;
-      pk = nk;
     }
-    note_alive(pk, K);
   }
   // 3) bond state lists (deterministic order)
   MPO mpo;

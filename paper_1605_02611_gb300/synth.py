@@ -1,7 +1,9 @@
 """Seeded synthetic inputs shared by the CUDA path, the CPU oracle and the bench.
 
 This module draws random numbers and lays out structure only; it holds none of
-the DMRG arithmetic (no operator algebra, no contractions, no canonicalisation).
+the DMRG arithmetic (no operator algebra, no contractions of the method).  The
+one matrix factorisation here is the QR of Gaussian matrices used to draw
+random isometries (random orthonormal bases), a standard way to sample them.
 
 Workload recipe (the paper's own test system, H20/STO-3G, Sec. "Hamiltonian
 compression", is not available here, so these stand in for it):
@@ -168,6 +170,48 @@ def random_mps(K: int, N: int, two_sz: int, M: int, seed: int, spread: float = 0
         for n, (a, c) in enumerate(LOCAL_QN):
             mask = (ll[:, None, 0] + a == rl[None, :, 0]) & (ll[:, None, 1] + c == rl[None, :, 1])
             A[:, n, :] *= mask
+        tensors.append(np.ascontiguousarray(A))
+    return bonds, tensors
+
+
+def random_isometric_mps(K: int, N: int, two_sz: int, M: int, seed: int, center: int, spread: float = 0.5):
+    """Random QN-block MPS in mixed-canonical form around sites (center, center+1).
+
+    Sites left of `center` are random left isometries (for every right sector
+    the stacked (l, n) x r block has orthonormal columns), sites right of
+    center+1 random right isometries (orthonormal rows per left sector): the
+    Q factors of Gaussian random matrices.  The two centre tensors are
+    Gaussian.  Returns (bonds, tensors) like random_mps.
+    """
+    Na, Nb = (N + two_sz) // 2, (N - two_sz) // 2
+    bonds = bond_sectors(K, Na, Nb, M, spread)
+    rng = np.random.default_rng(seed)
+    tensors = []
+    for k in range(K):
+        L, R = bonds[k], bonds[k + 1]
+        ll, rl = L.labels(), R.labels()
+        A = np.zeros((L.total, 4, R.total))
+        if k < center:
+            # rows (l, n) grouped by right sector
+            for (qa, qb), d, off in zip(R.qn, R.dim, np.cumsum([0] + R.dim[:-1])):
+                rows = [(l, n) for n, (a, c) in enumerate(LOCAL_QN)
+                        for l in range(L.total) if ll[l, 0] + a == qa and ll[l, 1] + c == qb]
+                Q, _ = np.linalg.qr(rng.normal(size=(len(rows), d)))
+                for i, (l, n) in enumerate(rows):
+                    A[l, n, off:off + d] = Q[i]
+        elif k > center + 1:
+            for (qa, qb), d, off in zip(L.qn, L.dim, np.cumsum([0] + L.dim[:-1])):
+                cols = [(n, r) for n, (a, c) in enumerate(LOCAL_QN)
+                        for r in range(R.total) if qa + a == rl[r, 0] and qb + c == rl[r, 1]]
+                Q, _ = np.linalg.qr(rng.normal(size=(len(cols), d)))
+                for i, (n, r) in enumerate(cols):
+                    A[off:off + d, n, r] = Q[i]
+        else:
+            A = rng.normal(size=(L.total, 4, R.total))
+            for n, (a, c) in enumerate(LOCAL_QN):
+                mask = (ll[:, None, 0] + a == rl[None, :, 0]) & (ll[:, None, 1] + c == rl[None, :, 1])
+                A[:, n, :] *= mask
+            A /= np.linalg.norm(A)
         tensors.append(np.ascontiguousarray(A))
     return bonds, tensors
 

@@ -125,3 +125,37 @@ def test_canonical_form_after_run():
         A = ctx.get_mps(k)
         A = A.reshape(A.shape[0], -1)
         assert np.allclose(A @ A.T, np.eye(A.shape[0]), atol=1e-12)
+
+
+@pytest.mark.parametrize("direction", [0, 1])
+def test_step_energy_matches_oracle_solve(direction):
+    """gbdmrg_step on a mixed-canonical MPS: the Davidson eigenvalue equals the
+    lowest eigenvalue of the projected H_eff (oracle), and the returned psi is
+    its eigenvector (up to sign)."""
+    require_gpu()
+    K, N, M, k = 6, 6, 16, 2
+    h, eri = synth.integrals(K, 61)
+    bonds, T = synth.random_isometric_mps(K, N, 0, M, 62, k)
+    lab = [b.labels() for b in bonds]
+    mask = omps.allowed_mask(lab[k], lab[k + 2])
+    psi0 = np.einsum("lnm,mor->lnor", T[k], T[k + 1])
+    e_ref, x_ref = odmrg.solve(T, k, psi0, mask, h, eri, 3, 3, tol=1e-13)
+    ctx = context_with_mps(h, eri, N, 0, bonds, T)
+    ctx.prepare(k)
+    e, dw, it, psi = ctx.step(k, direction, M, 1e-10, 300, want_psi=True)
+    assert abs(e - e_ref) < 1e-9
+    ref = ctx.pack(x_ref)
+    assert min(np.abs(psi - ref).max(), np.abs(psi + ref).max()) < 1e-7
+    assert 0 <= dw < 1e-2
+
+
+def test_sigma_flops_host_matches_plan():
+    require_gpu()
+    import paper_1605_02611_gb300 as G
+    K, N, M, k = 8, 8, 40, 3
+    h, eri = synth.integrals(K, 71)
+    bonds, T = synth.random_mps(K, N, 0, M, 72)
+    ctx = context_with_mps(h, eri, N, 0, bonds, T)
+    ctx.prepare(k)
+    _, fl = ctx.sigma(np.ones(ctx.nnz))
+    assert fl == G.sigma_flops_host(h, eri, N, 0, k, bonds[k].labels(), bonds[k + 2].labels())
