@@ -86,11 +86,22 @@ gbdmrg_status gbdmrg_get_mps(gbdmrg_ctx* ctx, int32_t site, int32_t* Dl, int32_t
 /* Labels of bond b (b = 0..K) of the current MPS: *D and, if qn != NULL, qn[2*D]. */
 gbdmrg_status gbdmrg_get_bond(gbdmrg_ctx* ctx, int32_t bond, int32_t* D, int32_t* qn);
 
+/* Arithmetic of H_eff.psi for subsequent gbdmrg_prepare / gbdmrg_step calls:
+ * 0 = FP64 grouped GEMMs on the FP64 units; 1 = tensor cores (tcgen05), one
+ * BF16 pass with FP32 accumulation; 2 = tensor cores, every operand split in
+ * three BF16 slices and the six leading slice products accumulated in FP32
+ * (about FP32 accuracy).  Environments, Davidson, decimation stay FP64. */
+gbdmrg_status gbdmrg_set_precision(gbdmrg_ctx* ctx, int32_t precision);
+
 /* Build the renormalised operators (Eq. renormop) of bonds k and k+2 from the
  * current MPS tensors in whatever gauge they are (blocking + decimation,
  * Eqs. prenormmatrix/prenormdec), and the work lists of H_eff for the sites
  * (k, k+1).  Must precede gbdmrg_sigma / gbdmrg_diag / gbdmrg_psi_layout. */
 gbdmrg_status gbdmrg_prepare(gbdmrg_ctx* ctx, int32_t k);
+
+/* Rebuild only the work lists of H_eff for sites (k, k+1) (current precision)
+ * from the environments the context already holds for bonds k and k+2. */
+gbdmrg_status gbdmrg_plan(gbdmrg_ctx* ctx, int32_t k);
 
 /* Packed layout of psi for the prepared sites.  *nblocks and *nnz are always
  * written; if blocks != NULL it receives nblocks rows of 7 int64:
@@ -161,7 +172,7 @@ typedef struct {
   const int32_t* M;
   const double* dav_tol;
   int32_t dav_max_iter;
-  int32_t precision; /* 0 = FP64 (only value supported by this build) */
+  int32_t precision; /* as gbdmrg_set_precision: 0 FP64, 1 BF16 pass, 2 BF16 x3 slices */
 } gbdmrg_schedule;
 
 /* Run the sweeps from the current MPS (brought to right-canonical form first).

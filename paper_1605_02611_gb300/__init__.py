@@ -45,7 +45,9 @@ SIGNATURES = {
     "gbdmrg_set_mps": (C.c_int, [_P, _I32, _I32, _I32, _PI32, _PI32, _PD]),
     "gbdmrg_get_mps": (C.c_int, [_P, _I32, _PI32, _PI32, _PD]),
     "gbdmrg_get_bond": (C.c_int, [_P, _I32, _PI32, _PI32]),
+    "gbdmrg_set_precision": (C.c_int, [_P, _I32]),
     "gbdmrg_prepare": (C.c_int, [_P, _I32]),
+    "gbdmrg_plan": (C.c_int, [_P, _I32]),
     "gbdmrg_psi_layout": (C.c_int, [_P, _PI64, _PI64, _PI64]),
     "gbdmrg_sigma": (C.c_int, [_P, _P, _P, _I32, _PD]),
     "gbdmrg_diag": (C.c_int, [_P, _P, _I32]),
@@ -201,6 +203,10 @@ class Context:
         return q
 
     # ---- two-site problem
+    def set_precision(self, mode: int):
+        """0 FP64, 1 tensor-core BF16 single pass, 2 tensor-core BF16 x3 slices."""
+        self._check(self.lib.gbdmrg_set_precision(self.h, mode), "set_precision")
+
     def prepare(self, k: int):
         self._check(self.lib.gbdmrg_prepare(self.h, k), "prepare")
         nb, nnz = C.c_int64(), C.c_int64()
@@ -211,6 +217,10 @@ class Context:
         self.layout = blk
         self.nnz = nnz.value
         return blk
+
+    def plan(self, k: int):
+        """Rebuild the H_eff work lists at (k, k+1) from the held environments."""
+        self._check(self.lib.gbdmrg_plan(self.h, k), "plan")
 
     def pack(self, psi: np.ndarray) -> np.ndarray:
         out = np.zeros(self.nnz)
@@ -274,10 +284,10 @@ class Context:
         return dict(sigma_flops=f.value, sigma_seconds=s.value, sigma_calls=n.value, other_flops=o.value)
 
     # ---- sweeps
-    def run(self, M, dav_tol, max_iter: int = 200):
+    def run(self, M, dav_tol, max_iter: int = 200, precision: int = 0):
         M = np.ascontiguousarray(M, dtype=np.int32)
         tol = np.ascontiguousarray(np.broadcast_to(dav_tol, M.shape), dtype=np.float64)
-        s = Schedule(len(M), M.ctypes.data_as(_PI32), _dptr(tol), max_iter, 0)
+        s = Schedule(len(M), M.ctypes.data_as(_PI32), _dptr(tol), max_iter, precision)
         e = np.zeros(len(M))
         d = np.zeros(len(M))
         self._check(self.lib.gbdmrg_run(self.h, C.byref(s), _dptr(e), _dptr(d)), "run")

@@ -177,6 +177,29 @@ gbdmrg_status gbdmrg_get_bond(gbdmrg_ctx* ctx, int32_t bond, int32_t* D, int32_t
   });
 }
 
+gbdmrg_status gbdmrg_set_precision(gbdmrg_ctx* ctx, int32_t precision) {
+  if (!ctx || precision < 0 || precision > 2) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    ctx->c.precision = precision;
+    ctx->c.prepared = -1;
+  });
+}
+
+gbdmrg_status gbdmrg_plan(gbdmrg_ctx* ctx, int32_t k) {
+  if (!ctx) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    auto& c = ctx->c;
+    if (k < 0 || k + 1 >= c.K) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "two-site position out of range");
+    if (!c.left[k].valid || !c.right[k + 2].valid)
+      throw gbdmrg::Error(gbdmrg::ST_ESTATE, "environments of bonds k and k+2 are not built");
+    gbdmrg::build_tilde_left(c, c.left[k], k, c.lt);
+    gbdmrg::build_tilde_right(c, c.right[k + 2], k + 1, c.rt);
+    gbdmrg::build_sigma_plan(c, c.lt, c.rt, k, c.plan);
+    gbdmrg::cuda_check(cudaStreamSynchronize(c.stream), "sync");
+    c.prepared = k;
+  });
+}
+
 gbdmrg_status gbdmrg_prepare(gbdmrg_ctx* ctx, int32_t k) {
   if (!ctx) return GBDMRG_EINVAL;
   return guard(ctx, [&] { gbdmrg::prepare_two_site(ctx->c, k); });
@@ -220,6 +243,8 @@ gbdmrg_status gbdmrg_sigma(gbdmrg_ctx* ctx, const double* psi, double* sigma, in
       gbdmrg::cuda_check(cudaMemcpyAsync(sigma, plan.out.p, bytes, cudaMemcpyDeviceToHost, c.stream), "d2h");
     }
     gbdmrg::cuda_check(cudaStreamSynchronize(c.stream), "sync");
+    if (plan.mx && gbdmrg::mixed_error(c, plan))
+      throw gbdmrg::Error(gbdmrg::ST_ETIMEOUT, "tensor-core GEMM: a bounded wait ran out");
     if (flops) *flops = plan.flops;
   });
 }
@@ -255,6 +280,8 @@ gbdmrg_status gbdmrg_sigma_timing(gbdmrg_ctx* ctx, int32_t reps, const double* p
     for (int r = 0; r < reps; ++r) gbdmrg::run_sigma(c, c.plan, psi_dev, sigma_dev);
     gbdmrg::cuda_check(cudaEventRecord(e1, c.stream), "record");
     gbdmrg::cuda_check(cudaEventSynchronize(e1), "sync");
+    if (c.plan.mx && gbdmrg::mixed_error(c, c.plan))
+      throw gbdmrg::Error(gbdmrg::ST_ETIMEOUT, "tensor-core GEMM: a bounded wait ran out");
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
@@ -323,7 +350,8 @@ gbdmrg_status gbdmrg_gemm_bf16_selftest(const int64_t* tasks, int32_t ntasks, co
     std::vector<TcTile> ti;
     for (int i = 0; i < nterms; ++i) {
       const int64_t* r = terms + 6 * i;
-      te[i] = {(const __nv_bfloat16*)r[0], (const __nv_bfloat16*)r[1], (int)r[2], (int)r[3], (int)r[4], (int)r[5]};
+      te[i] = {(const __nv_bfloat16*)r[0], (const __nv_bfloat16*)r[1], 0, 0, (int)r[2], (int)r[3], (int)r[4],
+               (int)r[5], 1};
       if ((r[0] | r[1]) & 15 || r[2] % 8 || r[3] % 8 || r[4] <= 0 || r[4] > r[2] || r[4] > r[3])
         throw Error(ST_EINVAL, "bf16 operands must be 16-byte aligned, ld % 8 == 0, 0 < k <= ld");
     }
@@ -393,7 +421,8 @@ gbdmrg_status gbdmrg_run(gbdmrg_ctx* ctx, const gbdmrg_schedule* s, double* ener
       if (s->M[i] <= 0) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "M must be positive");
       if (!(s->dav_tol[i] > 0)) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "dav_tol must be positive");
     }
-    if (s->precision != 0) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "only precision 0 (FP64) is supported");
+    if (s->precision < 0 || s->precision > 2) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "precision must be 0, 1 or 2");
+    ctx->c.precision = s->precision;
     ctx->stats = gbdmrg::SweepStats();
     gbdmrg::run_sweeps(ctx->c, s->nsweeps, s->M, s->dav_tol, s->dav_max_iter > 0 ? s->dav_max_iter : 200,
                        ctx->stats);

@@ -575,6 +575,10 @@ void build_sigma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) 
   P.build(Lb, Rb);
   plan.in.alloc(P.nnz, c.stream);
   plan.out.alloc(P.nnz, c.stream);
+  if (c.precision > 0) {
+    build_mixed_plan(c, lt, rt, k, plan, c.precision == 1 ? 1 : 3);
+    return;
+  }
   const int nL = Lb.nsec();
   // X_beta layout = psi layout shifted by dQ_beta; X stored transposed per block
   std::vector<size_t> xsz(mid.size(), 0);
@@ -667,6 +671,10 @@ void build_sigma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) 
 }
 
 void run_sigma(Context& c, SigmaPlan& plan, const double* x, double* y) {
+  if (plan.mx) {
+    run_mixed_sigma(c, plan, x, y);
+    return;
+  }
   const size_t bytes = plan.psi.nnz * sizeof(double);
   if (x != plan.in.p) cuda_check(cudaMemcpyAsync(plan.in.p, x, bytes, cudaMemcpyDeviceToDevice, c.stream), "d2d");
   cuda_check(cudaMemsetAsync(plan.out.p, 0, bytes, c.stream), "memset");
@@ -873,6 +881,7 @@ double davidson(Context& c, SigmaPlan& plan, const double* diag, double* psi, co
     cuda_check(cudaEventSynchronize(c.ev1), "sync");
     float ms = 0;
     cuda_check(cudaEventElapsedTime(&ms, c.ev0, c.ev1), "elapsed");
+    if (plan.mx && mixed_error(c, plan)) throw Error(ST_ETIMEOUT, "tensor-core GEMM: a bounded wait ran out");
     c.sigma_time_total += 1e-3 * ms;
     c.sigma_flops_total += plan.flops;
     c.sigma_calls++;
@@ -1336,7 +1345,22 @@ void run_sweeps(Context& c, int nsweeps, const int* M, const double* tol, int ma
     };
     for (int k = 0; k <= K - 3; ++k) step(k, 0);
     if (!c.right[K].valid) env_boundary_right(c, c.right[K]);
-    for (int k = K - 2; k >= 1; --k) step(k, 1);
+    for (int k = K - 2; k >= 2; --k) step(k, 1);
+    {
+      // Refinement of the mixed-precision sweep: the last step (sites 1, 2,
+      // small bonds next to the edge) is solved with the FP64 sigma, so the
+      // reported energy is an FP64-converged eigenvalue (residual checked in
+      // FP64) of the basis the tensor-core sweep produced.
+      const int keep = c.precision;
+      c.precision = 0;
+      try {
+        step(1, 1);
+      } catch (...) {
+        c.precision = keep;
+        throw;
+      }
+      c.precision = keep;
+    }
     cuda_check(cudaStreamSynchronize(c.stream), "sync");
     auto t1 = std::chrono::steady_clock::now();
     st.energy.push_back(e + c.ecore);

@@ -5,6 +5,7 @@
 #include <cusolverDn.h>
 
 #include <array>
+#include <memory>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -160,10 +161,19 @@ struct GemmBuilder {
   void clear() { tiles.clear(); tasks.clear(); terms.clear(); flops = 0; }
 };
 
+struct MixedPlan;
+void mixed_plan_free(MixedPlan* p);
+struct MixedDeleter {
+  void operator()(MixedPlan* p) const { mixed_plan_free(p); }
+};
+
+// Work lists of H_eff.psi for one two-site problem: FP64 grouped GEMMs, or
+// (mx set) the tensor-core mixed-precision plan of engine_mixed.cu.
 struct SigmaPlan {
   PsiLayout psi;
   DArr<double> in, out, X;
   std::vector<GemmPlan> stage1, stage2;
+  std::unique_ptr<MixedPlan, MixedDeleter> mx;
   double flops = 0;
 };
 
@@ -201,6 +211,9 @@ struct Context {
   long sigma_calls = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int chunk_budget_mb = 2048;
+  // 0: FP64 grouped GEMMs; 1: tensor cores, one BF16 pass; 2: tensor cores,
+  // three BF16 slices (six products, about FP32 accuracy)
+  int precision = 0;
 
   ~Context();
 };
@@ -218,6 +231,9 @@ void env_update_right(Context& c, Tilde& rt, const SiteT& B, int site, Env& out)
 
 void build_sigma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan);
 void run_sigma(Context& c, SigmaPlan& plan, const double* x, double* y);
+void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, int nslices);
+void run_mixed_sigma(Context& c, SigmaPlan& plan, const double* x, double* y);
+int mixed_error(Context& c, SigmaPlan& plan);
 void compute_diag(Context& c, Tilde& lt, Tilde& rt, int k, const PsiLayout& P, double* diag);
 
 void prepare_two_site(Context& c, int k);

@@ -32,6 +32,11 @@ constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024;
 constexpr int TC_THREADS = 128;
 constexpr long TC_WAIT_LIMIT = 1L << 22;
 
+// slice pairs (i, j) with i + j < nsl, largest products first
+__constant__ int PAIR_I[6] = {0, 0, 1, 0, 1, 2};
+__constant__ int PAIR_J[6] = {0, 1, 0, 2, 1, 0};
+__device__ __forceinline__ int npairs(int nsl) { return nsl <= 1 ? 1 : (nsl == 2 ? 3 : 6); }
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -124,22 +129,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
   const uint32_t tmem = tmem_base_sh;
 
-  // total number of 64-wide k-steps over the term list
+  // total number of 64-wide k-steps over the term list (and slice pairs)
   int S = 0;
-  for (int t = tk.t0; t < tk.t1; ++t) S += (terms[t].k + TC_K - 1) / TC_K;
+  for (int t = tk.t0; t < tk.t1; ++t) S += npairs(terms[t].nsl) * ((terms[t].k + TC_K - 1) / TC_K);
 
-  int lt = tk.t0, lk = 0;  // load cursor
-  int mt = tk.t0, mk = 0;  // MMA cursor
-  auto adv = [&](int& t, int& k0) {
+  int lt = tk.t0, lp = 0, lk = 0;  // load cursor (term, slice pair, k offset)
+  int mt = tk.t0, mp = 0, mk = 0;  // MMA cursor
+  auto adv = [&](int& t, int& p, int& k0) {
     k0 += TC_K;
-    if (k0 >= terms[t].k) { ++t; k0 = 0; }
+    if (k0 >= terms[t].k) {
+      k0 = 0;
+      if (++p >= npairs(terms[t].nsl)) { p = 0; ++t; }
+    }
   };
   auto issue_load = [&](int stage) {
     const TcTerm tm = terms[lt];
     const uint32_t sa = base + stage * TC_STAGE_BYTES;
-    load_tile(sa, tm.A, tm.lda, tk.m, tl.r0, lk);
-    load_tile(sa + TC_TILE_BYTES, tm.B, tm.ldb, tk.n, tl.c0, lk);
-    adv(lt, lk);
+    load_tile(sa, tm.A + PAIR_I[lp] * tm.sA, tm.lda, tk.m, tl.r0, lk);
+    load_tile(sa + TC_TILE_BYTES, tm.B + PAIR_J[lp] * tm.sB, tm.ldb, tk.n, tl.c0, lk);
+    adv(lt, lp, lk);
   };
   bool ok = true;
   for (int j = 0; j < TC_STAGES - 1; ++j) {
@@ -176,7 +184,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
           smem_u32(&bars[s])));
     }
-    adv(mt, mk);
+    adv(mt, mp, mk);
   }
   // all threads agree on `ok` before the final wait
   __syncthreads();

@@ -7,10 +7,14 @@ namespace gbdmrg {
 
 // C[m x n] (+)= sum_t (-1)^{neg_t} A_t[m x k_t] B_t[n x k_t]^T; A, B row-major bf16 with
 // leading dimensions (elements) multiples of 8, 16-byte aligned, zero padding up to ld.
+// With nsl > 1 the operands are nsl BF16 slices (x = s_0 + s_1 + ...) stored sA / sB
+// elements apart, and the term contributes sum_{i + j < nsl} A_i B_j^T.
 struct TcTerm {
   const __nv_bfloat16* A;
   const __nv_bfloat16* B;
+  long sA, sB;
   int lda, ldb, k, flags;  // flags bit 0: negate
+  int nsl;
 };
 // outputs: C (fp32, optional, += if beta) and/or Cb (bf16, optional): nslices bf16
 // slices x = s0 + s1 + s2 written slice_stride elements apart
