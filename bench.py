@@ -228,6 +228,7 @@ def run_ours(args, rank, world, local_rank):
         step()
     torch.cuda.synchronize()
     c0 = ctx.counters()
+    p0 = ctx.phase_times()
     l0 = G.kernel_launches()
     clocks = ClockSampler(local_rank)
     clocks.start()
@@ -245,6 +246,8 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     c1 = ctx.counters()
+    p1 = ctx.phase_times()
+    phases = {kk: round((p1[kk] - p0[kk]) / args.steps, 4) for kk in p1}
     launches = G.kernel_launches() - l0
     flops = (c1["sigma_flops"] - c0["sigma_flops"]) + (c1["other_flops"] - c0["other_flops"])
     sig_fl = c1["sigma_flops"] - c0["sigma_flops"]
@@ -314,6 +317,7 @@ def run_ours(args, rank, world, local_rank):
                    "psi_nnz": nnz, "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (no flush)",
                    "setup_s": round(setup_s, 1), "setup_launches": int(setup_launches)},
         "sigma_tflops": achieved_alg, "sigma_calls": sig_calls, "fp64_comparison": fp64_cmp,
+        "step_phase_s": phases,
         "roofline": roof,
         "e2e": {"value": e2e_flops / t_e2e / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": nnz * 8,
                 "d2h_bytes_per_step": nnz * 8},

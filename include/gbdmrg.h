@@ -142,6 +142,12 @@ gbdmrg_status gbdmrg_step(gbdmrg_ctx* ctx, int32_t k, int32_t direction, int32_t
  * grouped GEMMs (environment updates, diagonal, decimation).  Any may be NULL. */
 gbdmrg_status gbdmrg_counters(gbdmrg_ctx* ctx, double* sigma_flops, double* sigma_seconds, int64_t* sigma_calls,
                               double* other_flops);
+/* Cumulative wall seconds of the phases of gbdmrg_step / gbdmrg_run steps
+ * (stream-synchronised): [0] W-contracted operators (element-wise blocking
+ * sums), [1] work lists of H_eff.psi, [2] diagonal, [3] Davidson, [4]
+ * decimation, [5] environment update, [6..7] reserved.  seconds[8]. */
+gbdmrg_status gbdmrg_phase_times(gbdmrg_ctx* ctx, double* seconds);
+
 /* Number of CUDA kernel launches issued by this library in this process. */
 int64_t gbdmrg_kernel_launches(void);
 

@@ -56,6 +56,7 @@ SIGNATURES = {
     "gbdmrg_counters": (C.c_int, [_P, _PD, _PD, _PI64, _PD]),
     "gbdmrg_kernel_launches": (C.c_int64, []),
     "gbdmrg_gemm_bf16_selftest": (C.c_int, [_PI64, _I32, _PI64, _I32, _P]),
+    "gbdmrg_phase_times": (C.c_int, [_P, _PD]),
     "gbdmrg_sigma_flops_host": (C.c_int, [C.POINTER(Problem), _I32, _I32, _PI32, _I32, _PI32, _PD]),
     "gbdmrg_run": (C.c_int, [_P, C.POINTER(Schedule), _PD, _PD]),
     "gbdmrg_run_stats": (C.c_int, [_P, _PD, _PD, _PD, _PI32]),
@@ -276,6 +277,11 @@ class Context:
         self._check(self.lib.gbdmrg_step(self.h, k, direction, M, tol, max_iter, pin, pout, int(on_device),
                                          C.byref(e), C.byref(d), C.byref(it)), "step")
         return e.value, d.value, it.value, out
+
+    def phase_times(self):
+        t = np.zeros(8)
+        self._check(self.lib.gbdmrg_phase_times(self.h, _dptr(t)), "phase_times")
+        return dict(zip(["tilde", "plan", "diag", "davidson", "decimate", "env_update"], t[:6].tolist()))
 
     def counters(self):
         f, s, o = C.c_double(), C.c_double(), C.c_double()

@@ -1232,11 +1232,23 @@ double two_site_step(Context& c, int k, int dir, int M, const DavidsonOpts& o, b
                      double* discarded, const double* psi0, double* psi_out, long* nnz_out) {
   if (!c.left[k].valid || !c.right[k + 2].valid)
     throw Error(ST_ESTATE, "environments of the two-site step are not built");
+  auto now = [&]() {
+    cuda_check(cudaStreamSynchronize(c.stream), "sync");
+    return std::chrono::steady_clock::now();
+  };
+  auto t0 = now();
+  auto lap = [&](int ph) {
+    auto t1 = now();
+    c.phase_s[ph] += std::chrono::duration<double>(t1 - t0).count();
+    t0 = t1;
+  };
   Tilde lt, rt;
   build_tilde_left(c, c.left[k], k, lt);
   build_tilde_right(c, c.right[k + 2], k + 1, rt);
+  lap(0);
   SigmaPlan plan;
   build_sigma_plan(c, lt, rt, k, plan);
+  lap(1);
   DArr<double> psi, diag;
   psi.alloc(plan.psi.nnz, c.stream);
   diag.alloc(plan.psi.nnz, c.stream);
@@ -1245,16 +1257,19 @@ double two_site_step(Context& c, int k, int dir, int M, const DavidsonOpts& o, b
   else
     make_psi(c, c.sites[k], c.sites[k + 1], plan.psi, psi.p);
   compute_diag(c, lt, rt, k, plan.psi, diag.p);
+  lap(2);
   double e = davidson(c, plan, diag.p, psi.p, o, iters);
   if (psi_out)
     cuda_check(cudaMemcpyAsync(psi_out, psi.p, plan.psi.nnz * sizeof(double), cudaMemcpyDeviceToDevice, c.stream),
                "d2d");
   if (nnz_out) *nnz_out = plan.psi.nnz;
+  lap(3);
   SiteT A, B;
   double dw = decimate(c, plan.psi, psi.p, M, dir, A, B);
   if (discarded) *discarded = dw;
   c.sites[k] = std::move(A);
   c.sites[k + 1] = std::move(B);
+  lap(4);
   if (dir == 0) {
     env_update_left(c, lt, c.sites[k], k, c.left[k + 1]);
     if (free_used) c.right[k + 2] = Env();
@@ -1262,7 +1277,7 @@ double two_site_step(Context& c, int k, int dir, int M, const DavidsonOpts& o, b
     env_update_right(c, rt, c.sites[k + 1], k + 1, c.right[k + 1]);
     if (free_used) c.left[k + 1] = Env();
   }
-  cuda_check(cudaStreamSynchronize(c.stream), "sync");
+  lap(5);
   c.prepared = -1;
   return e;
 }

@@ -210,6 +210,10 @@ struct Context {
   double sigma_flops_total = 0, sigma_time_total = 0, other_flops_total = 0;
   long sigma_calls = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // wall seconds per phase of the two-site step (stream-synchronised):
+  // 0 W-contracted operators, 1 sigma work lists, 2 diagonal, 3 Davidson,
+  // 4 decimation, 5 environment update
+  double phase_s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int chunk_budget_mb = 2048;
   // 0: FP64 grouped GEMMs; 1: tensor cores, one BF16 pass; 2: tensor cores,
   // three BF16 slices (six products, about FP32 accuracy)
