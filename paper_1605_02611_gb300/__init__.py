@@ -51,6 +51,7 @@ SIGNATURES = {
     "gbdmrg_psi_layout": (C.c_int, [_P, _PI64, _PI64, _PI64]),
     "gbdmrg_sigma": (C.c_int, [_P, _P, _P, _I32, _PD]),
     "gbdmrg_diag": (C.c_int, [_P, _P, _I32]),
+    "gbdmrg_diag_noalloc": (C.c_int, [_P, _P]),
     "gbdmrg_sigma_timing": (C.c_int, [_P, _I32, _P, _P, _PD]),
     "gbdmrg_step": (C.c_int, [_P, _I32, _I32, _I32, C.c_double, _I32, _P, _P, _I32, _PD, _PD, _PI32]),
     "gbdmrg_counters": (C.c_int, [_P, _PD, _PD, _PI64, _PD]),
@@ -288,6 +289,10 @@ class Context:
         n = C.c_int64()
         self._check(self.lib.gbdmrg_counters(self.h, C.byref(f), C.byref(s), C.byref(n), C.byref(o)), "counters")
         return dict(sigma_flops=f.value, sigma_seconds=s.value, sigma_calls=n.value, other_flops=o.value)
+
+    def diag_noalloc(self, diag_ptr: int):
+        """Diagonal of H_eff into a device buffer without device allocation."""
+        self._check(self.lib.gbdmrg_diag_noalloc(self.h, _P(diag_ptr)), "diag_noalloc")
 
     # ---- sweeps
     def run(self, M, dav_tol, max_iter: int = 200, precision: int = 0):

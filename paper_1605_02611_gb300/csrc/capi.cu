@@ -267,6 +267,11 @@ gbdmrg_status gbdmrg_diag(gbdmrg_ctx* ctx, double* diag, int32_t on_device) {
   });
 }
 
+gbdmrg_status gbdmrg_diag_noalloc(gbdmrg_ctx* ctx, double* diag_dev) {
+  if (!ctx || !diag_dev) return GBDMRG_EINVAL;
+  return guard(ctx, [&] { gbdmrg::compute_diag_noalloc(ctx->c, diag_dev); });
+}
+
 gbdmrg_status gbdmrg_sigma_timing(gbdmrg_ctx* ctx, int32_t reps, const double* psi_dev, double* sigma_dev,
                                   double* ms_per_call) {
   if (!ctx || !psi_dev || !sigma_dev || !ms_per_call || reps <= 0) return GBDMRG_EINVAL;

@@ -241,6 +241,10 @@ int mixed_error(Context& c, SigmaPlan& plan);
 void compute_diag(Context& c, Tilde& lt, Tilde& rt, int k, const PsiLayout& P, double* diag);
 
 void prepare_two_site(Context& c, int k);
+// compute_diag for the prepared problem with all scratch in a fixed static device
+// array (noalloc.cu); no device allocation.
+void compute_diag_noalloc(Context& c, double* diag);
+size_t noalloc_scratch_bytes();
 void make_psi(Context& c, const SiteT& TL, const SiteT& TR, const PsiLayout& P, double* psi);
 
 struct DavidsonOpts {
