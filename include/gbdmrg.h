@@ -172,7 +172,8 @@ int64_t gbdmrg_kernel_launches(void);
  * row-major bf16, 16-byte aligned, leading dimensions multiples of 8 and zero
  * padding between k_t and the leading dimension.  All matrix pointers are
  * device pointers; the descriptor arrays are host arrays:
- * tasks[8*i] = (C, ldc, m, n, beta, t0, t1, 0), terms[6*t] = (A, B, lda, ldb, k, neg).
+ * tasks[8*i] = (C, ldc, m, n, beta, t0, t1, trans), terms[6*t] = (A, B, lda, ldb, k, neg);
+ * trans != 0 stores element (r, c) of the block at C[c * ldc + r].
  * GBDMRG_ETIMEOUT if a bounded wait inside the kernel ran out. */
 gbdmrg_status gbdmrg_gemm_bf16_selftest(const int64_t* tasks, int32_t ntasks, const int64_t* terms, int32_t nterms,
                                         void* stream);

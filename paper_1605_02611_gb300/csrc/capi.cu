@@ -362,7 +362,8 @@ gbdmrg_status gbdmrg_gemm_bf16_selftest(const int64_t* tasks, int32_t ntasks, co
     }
     for (int i = 0; i < ntasks; ++i) {
       const int64_t* r = tasks + 8 * i;
-      ta[i] = {(float*)r[0], nullptr, 0, (int)r[1], 0, (int)r[2], (int)r[3], (int)r[4], 0, (int)r[5], (int)r[6]};
+      ta[i] = {(float*)r[0], nullptr, 0, (int)r[1], 0, (int)r[2], (int)r[3], (int)r[4], 0, (int)r[7], (int)r[5],
+               (int)r[6]};
       if (ta[i].t0 < 0 || ta[i].t1 > nterms || ta[i].t0 >= ta[i].t1 || ta[i].m <= 0 || ta[i].n <= 0)
         throw Error(ST_EINVAL, "bad task");
       for (int r0 = 0; r0 < ta[i].m; r0 += TC_TILE_M)

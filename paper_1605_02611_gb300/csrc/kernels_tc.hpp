@@ -17,12 +17,13 @@ struct TcTerm {
   int nsl;
 };
 // outputs: C (fp32, optional, += if beta) and/or Cb (bf16, optional): nslices bf16
-// slices x = s0 + s1 + s2 written slice_stride elements apart
+// slices x = s0 + s1 + s2 written slice_stride elements apart.  trans: element
+// (i, j) of the block goes to [j * ld + i] instead of [i * ld + j].
 struct TcTask {
   float* C;
   __nv_bfloat16* Cb;
   long slice_stride;
-  int ldc, ldcb, m, n, beta, nslices, t0, t1;
+  int ldc, ldcb, m, n, beta, nslices, trans, t0, t1;
 };
 struct TcTile {
   int task, r0, c0;

@@ -14,12 +14,14 @@ def _pad8(x):
     return (x + 7) // 8 * 8
 
 
-def _case(rng, torch, shapes, beta=0):
+def _case(rng, torch, shapes, beta=0, trans=0):
     """shapes: list of tasks, each (m, n, [k_t...], [neg_t...])."""
     tasks, terms, keep, refs = [], [], [], []
     for (m, n, ks, negs) in shapes:
-        C = torch.randn(m, n, device="cuda", dtype=torch.float32) if beta else torch.zeros(m, n, device="cuda")
-        ref = C.double().clone() if beta else torch.zeros(m, n, device="cuda", dtype=torch.float64)
+        shp = (n, m) if trans else (m, n)
+        C = torch.randn(*shp, device="cuda", dtype=torch.float32) if beta else torch.zeros(*shp, device="cuda")
+        ref = C.double().clone().T.contiguous() if (beta and trans) else (
+            C.double().clone() if beta else torch.zeros(m, n, device="cuda", dtype=torch.float64))
         t0 = len(terms)
         for k, neg in zip(ks, negs):
             la, lb = _pad8(k) + 8 * int(rng.integers(0, 2)), _pad8(k)
@@ -32,12 +34,13 @@ def _case(rng, torch, shapes, beta=0):
             prod = A[:, :k].double() @ B[:, :k].double().T
             ref += -prod if neg else prod
         keep.append(C)
-        tasks.append([C.data_ptr(), n, m, n, beta, t0, len(terms), 0])
+        tasks.append([C.data_ptr(), m if trans else n, m, n, beta, t0, len(terms), trans])
         refs.append((C, ref))
     G.gemm_bf16_selftest(np.array(tasks), np.array(terms))
     torch.cuda.synchronize()
     for C, ref in refs:
-        err = (C.double() - ref).abs().max().item()
+        got = C.double().T if trans else C.double()
+        err = (got - ref).abs().max().item()
         scale = ref.abs().max().item() + 1.0
         assert err <= 1e-5 * scale, (err, scale)
 
@@ -64,6 +67,16 @@ def test_accumulate_beta_and_long_k():
     torch = require_gpu()
     rng = np.random.default_rng(2)
     _case(rng, torch, [(200, 70, [1000, 3], [0, 1]), (5, 260, [130], [0])], beta=1)
+
+
+def test_transposed_store_and_many_tiles():
+    """More tiles than resident CTAs (persistent loop, both TMEM accumulators), transposed stores."""
+    torch = require_gpu()
+    rng = np.random.default_rng(3)
+    shapes = [(int(rng.integers(1, 260)), int(rng.integers(1, 300)), [int(rng.integers(1, 150))], [0])
+              for _ in range(400)]
+    _case(rng, torch, shapes, beta=1, trans=1)
+    _case(rng, torch, shapes[:50], beta=0, trans=0)
 
 
 def test_rejects_misaligned():
