@@ -23,19 +23,22 @@ namespace {
 
 inline int pad8(int x) { return (x + 7) & ~7; }
 
+// FP64 block -> nsl BF16 slices; writes wcols columns per row (the block's columns
+// and its zero padding), rows ldd elements apart in the destination
 struct ConvJob {
   const double* src;
   __nv_bfloat16* dst;
   long slice_stride;
   int rows, cols, lds, ldd, nsl;
   double scale;
+  int wcols;
 };
 
 __global__ void conv_kernel(const ConvJob* __restrict__ jobs) {
   const ConvJob jb = jobs[blockIdx.y];
-  const long n = (long)jb.rows * jb.ldd;
+  const long n = (long)jb.rows * jb.wcols;
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(e / jb.ldd), j = (int)(e % jb.ldd);
+    const int i = (int)(e / jb.wcols), j = (int)(e % jb.wcols);
     double v = j < jb.cols ? jb.scale * jb.src[(long)i * jb.lds + j] : 0.0;
     __nv_bfloat16* d = jb.dst + (long)i * jb.ldd + j;
     for (int s = 0; s < jb.nsl; ++s) {
@@ -46,8 +49,29 @@ __global__ void conv_kernel(const ConvJob* __restrict__ jobs) {
   }
 }
 
-__global__ void f32_to_f64_kernel(const float* __restrict__ a, double* __restrict__ b, long n) {
-  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) b[e] = a[e];
+// transposed gather FP32 -> FP64: dst[i * cols + j] = src[j * lds + i]
+struct UnconvJob {
+  const float* src;
+  double* dst;
+  int rows, cols, lds;
+};
+
+__global__ void unconv_kernel(const UnconvJob* __restrict__ jobs) {
+  const UnconvJob jb = jobs[blockIdx.y];
+  const long n = (long)jb.rows * jb.cols;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / jb.cols), j = (int)(e % jb.cols);
+    jb.dst[e] = (double)jb.src[(long)j * jb.lds + i];
+  }
+}
+
+void launch_unconv(const UnconvJob* jobs, int njobs, long maxel, cudaStream_t s) {
+  for (int o0 = 0; o0 < njobs; o0 += 65535) {
+    int no = std::min(65535, njobs - o0);
+    long g = std::min<long>(std::max<long>(1, (maxel + 255) / 256), 64);
+    unconv_kernel<<<dim3((unsigned)g, no), 256, 0, s>>>(jobs + o0);
+  }
+  cuda_check(cudaGetLastError(), "unconv launch");
 }
 
 void launch_conv(const DArr<ConvJob>& jobs, int njobs, long maxel, cudaStream_t s) {
@@ -97,8 +121,10 @@ struct MixedPlan {
   DArr<__nv_bfloat16> psi_b, X_b, mirror;
   DArr<float> sig_f;
   DArr<ConvJob> psi_jobs;
-  int n_psi_jobs = 0;
-  long psi_maxel = 0;
+  DArr<UnconvJob> sig_jobs;
+  int n_psi_jobs = 0, n_sig_jobs = 0;
+  long psi_maxel = 0, sig_maxel = 0;
+  long sig_total = 0;
   std::vector<TcPlan> stage1, stage2;
   DArr<int> err;
 };
@@ -165,7 +191,8 @@ void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, 
       mref[key] = m;
       for (size_t b = 0; b < L.blocks.size(); ++b) {
         const Block& B = L.blocks[b];
-        conv.push_back({r.p + B.off, nullptr /*patched*/, sz, B.rows, B.cols, B.cols, pad8(B.cols), nsl, scale});
+        conv.push_back(
+            {r.p + B.off, nullptr /*patched*/, sz, B.rows, B.cols, B.cols, pad8(B.cols), nsl, scale, pad8(B.cols)});
         conv.back().dst = (__nv_bfloat16*)(intptr_t)(m.off + (*m.boff)[b]);  // offset, patched below
       }
     } else m = it->second;
@@ -181,43 +208,94 @@ void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, 
   for (auto& j : conv) j.dst = mx->mirror.p + (intptr_t)j.dst;
   {
     long maxel = 0;
-    for (auto& j : conv) maxel = std::max<long>(maxel, (long)j.rows * j.ldd);
+    for (auto& j : conv) maxel = std::max<long>(maxel, (long)j.rows * j.wcols);
     DArr<ConvJob> dj;
     dj.upload(conv, c.stream);
     if (!conv.empty()) launch_conv(dj, (int)conv.size(), maxel, c.stream);
     cuda_check(cudaStreamSynchronize(c.stream), "sync");
   }
-  // ---- psi mirror (padded) and its conversion jobs from plan.in
-  std::vector<long> poff(P.blocks.size());
-  long ptot = 0;
-  for (size_t b = 0; b < P.blocks.size(); ++b) {
-    poff[b] = ptot;
-    ptot += (long)P.blocks[b].rows * pad8(P.blocks[b].cols);
+  // ---- group layout.  psi reshaped to (l n1) x (n2 r) is block diagonal in the
+  // quantum number g of the cut; per group the row blocks (ql, n1) and column
+  // blocks (n2, qr) are stacked (each padded to a multiple of 8) into one matrix
+  // Psi_g (R_g x C_g).  X_beta^T and sigma^T use the same stacked blocks, so the
+  // tensor-core tiles span a whole group instead of one small block.
+  std::map<std::pair<int, int>, int> gidx;
+  std::vector<std::pair<int, int>> gq;
+  std::vector<std::vector<std::array<int, 3>>> grow, gcol;  // (ql, n1, off), (n2, qr, off)
+  std::vector<int> gR, gC;
+  {
+    std::map<std::pair<int, int>, std::pair<std::vector<std::array<int, 3>>, std::vector<std::array<int, 3>>>> tmp;
+    for (int ql = 0; ql < nL; ++ql)
+      for (int n1 = 0; n1 < 4; ++n1) tmp[{Lb.qa[ql] + LQA[n1], Lb.qb[ql] + LQB[n1]}].first.push_back({ql, n1, 0});
+    for (int qr = 0; qr < Rb.nsec(); ++qr)
+      for (int n2 = 0; n2 < 4; ++n2) tmp[{Rb.qa[qr] - LQA[n2], Rb.qb[qr] - LQB[n2]}].second.push_back({n2, qr, 0});
+    for (auto& kv : tmp) {
+      if (kv.second.first.empty() || kv.second.second.empty()) continue;
+      gidx[kv.first] = (int)gq.size();
+      gq.push_back(kv.first);
+      auto rows = kv.second.first, cols = kv.second.second;
+      int R = 0, C = 0;
+      for (auto& r : rows) { r[2] = R; R += pad8(Lb.dim[r[0]]); }
+      for (auto& cc : cols) { cc[2] = C; C += pad8(Rb.dim[cc[1]]); }
+      grow.push_back(rows);
+      gcol.push_back(cols);
+      gR.push_back(R);
+      gC.push_back(C);
+    }
+  }
+  const int ng = (int)gq.size();
+  // (ql, n1) -> (group, row offset); (n2, qr) -> (group, col offset)
+  std::vector<std::array<int, 2>> rpos((size_t)nL * 4, {-1, 0}), cpos((size_t)Rb.nsec() * 4, {-1, 0});
+  for (int g = 0; g < ng; ++g) {
+    for (auto& r : grow[g]) rpos[r[0] * 4 + r[1]] = {g, r[2]};
+    for (auto& cc : gcol[g]) cpos[cc[1] * 4 + cc[0]] = {g, cc[2]};
+  }
+  auto group_of = [&](int a, int b) {
+    auto it = gidx.find({a, b});
+    return it == gidx.end() ? -1 : it->second;
+  };
+  std::vector<long> goff(ng), sgoff(ng);
+  long ptot = 0, stot = 0;
+  for (int g = 0; g < ng; ++g) {
+    goff[g] = ptot;
+    ptot += (long)gR[g] * gC[g];
+    sgoff[g] = stot;
+    stot += (long)gC[g] * gR[g];
   }
   mx->psi_b.alloc(std::max<long>(ptot * nsl, 8), c.stream);
+  cuda_check(cudaMemsetAsync(mx->psi_b.p, 0, mx->psi_b.n * sizeof(__nv_bfloat16), c.stream), "memset");
+  mx->sig_total = std::max<long>(stot, 1);
+  mx->sig_f.alloc(mx->sig_total, c.stream);
   {
     std::vector<ConvJob> pj;
+    std::vector<UnconvJob> sj;
     for (size_t b = 0; b < P.blocks.size(); ++b) {
       const Block& B = P.blocks[b];
-      pj.push_back({plan.in.p + B.off, mx->psi_b.p + poff[b], ptot, B.rows, B.cols, B.cols, pad8(B.cols), nsl, 1.0});
+      const int n1 = P.b1[b], n2 = P.b2[b];
+      const auto rp = rpos[B.rs * 4 + n1];
+      const auto cp = cpos[B.cs * 4 + n2];
+      if (rp[0] < 0 || rp[0] != cp[0]) throw Error(ST_ECUDA, "internal: psi block outside its group");
+      const int g = rp[0];
+      pj.push_back({plan.in.p + B.off, mx->psi_b.p + goff[g] + (long)rp[1] * gC[g] + cp[1], ptot, B.rows, B.cols,
+                    B.cols, gC[g], nsl, 1.0, pad8(B.cols)});
       mx->psi_maxel = std::max<long>(mx->psi_maxel, (long)B.rows * pad8(B.cols));
+      sj.push_back({mx->sig_f.p + sgoff[g] + (long)cp[1] * gR[g] + rp[1], plan.out.p + B.off, B.rows, B.cols, gR[g]});
+      mx->sig_maxel = std::max<long>(mx->sig_maxel, (long)B.rows * B.cols);
     }
     mx->psi_jobs.upload(pj, c.stream);
     mx->n_psi_jobs = (int)pj.size();
+    mx->sig_jobs.upload(sj, c.stream);
+    mx->n_sig_jobs = (int)sj.size();
   }
-  mx->sig_f.alloc(std::max<long>(P.nnz, 1), c.stream);
   mx->err.alloc(1, c.stream);
   cuda_check(cudaMemsetAsync(mx->err.p, 0, sizeof(int), c.stream), "memset");
-  // ---- X^T sizes per beta (padded), chunking
+  // ---- X_beta^T per (beta, g'): C_g x R_g' with g = g' + dQ_beta; chunking over beta
   std::vector<size_t> xsz(mid.size(), 0);
   for (size_t beta = 0; beta < mid.size(); ++beta)
-    for (int ql = 0; ql < nL; ++ql)
-      for (int n1 = 0; n1 < 4; ++n1)
-        for (int n2 = 0; n2 < 4; ++n2) {
-          int qr = Rb.find(Lb.qa[ql] + LQA[n1] + LQA[n2] + mid[beta].dna,
-                           Lb.qb[ql] + LQB[n1] + LQB[n2] + mid[beta].dnb);
-          if (qr >= 0) xsz[beta] += (size_t)Rb.dim[qr] * pad8(Lb.dim[ql]);
-        }
+    for (int gp = 0; gp < ng; ++gp) {
+      int g = group_of(gq[gp].first + mid[beta].dna, gq[gp].second + mid[beta].dnb);
+      if (g >= 0) xsz[beta] += (size_t)gC[g] * gR[gp];
+    }
   const size_t budget = (size_t)c.chunk_budget_mb * (1u << 20) / (2 * nsl);
   std::vector<std::pair<size_t, size_t>> chunks;
   size_t maxchunk = 0;
@@ -238,74 +316,94 @@ void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, 
   for (auto ch : chunks) {
     TcBuilder g1, g2;
     size_t xoff = 0;
-    std::vector<std::vector<long>> xpos(ch.second - ch.first);
+    // X^T offsets of this chunk: [beta - b0][g'] (-1 if absent or never written)
+    std::vector<std::vector<long>> xpos(ch.second - ch.first, std::vector<long>(ng, -1));
     for (size_t beta = ch.first; beta < ch.second; ++beta) {
       auto& xp = xpos[beta - ch.first];
-      xp.assign((size_t)nL * 16, -1);
-      for (int qlp = 0; qlp < nL; ++qlp)
-        for (int n1p = 0; n1p < 4; ++n1p)
-          for (int n2 = 0; n2 < 4; ++n2) {
-            int qr = Rb.find(Lb.qa[qlp] + LQA[n1p] + LQA[n2] + mid[beta].dna,
-                             Lb.qb[qlp] + LQB[n1p] + LQB[n2] + mid[beta].dnb);
-            if (qr < 0) continue;
-            const int m = Rb.dim[qr], n = Lb.dim[qlp], ldx = pad8(n);
-            TcTask t{};
-            t.Cb = mx->X_b.p + xoff;
-            t.slice_stride = xstride;
-            t.ldcb = ldx;
-            t.m = m;
-            t.n = n;
-            t.nslices = nsl;
-            g1.begin(t);
-            for (int n2p = 0; n2p < 4; ++n2p) {
-              const TRef& r = rt.ref[beta][n2 * 4 + n2p];
-              if (!r.p) continue;
-              int pb = P.blk(qlp, n1p, n2p);
-              if (pb < 0) continue;
-              int qrp = P.blocks[pb].cs;
-              const OpLayout& Lay = Renv.cls[r.cls];
-              int bl = Lay.blk_of_col[qrp];
-              if (bl < 0 || Lay.blocks[bl].rs != qr) continue;
-              const MirrorRef& mr = rm[beta][n2 * 4 + n2p];
-              const int kk = Rb.dim[qrp], ld = pad8(kk);
-              g1.term(mir + mr.off + (*mr.boff)[bl], mr.stride, ld, mx->psi_b.p + poff[pb], ptot, ld, kk, mr.neg,
-                      nsl);
-            }
-            if (g1.end()) {
-              xp[(qlp * 4 + n1p) * 4 + n2] = (long)xoff;
-              xoff += (size_t)m * ldx;
-            }
+      for (int gp = 0; gp < ng; ++gp) {
+        const int g = group_of(gq[gp].first + mid[beta].dna, gq[gp].second + mid[beta].dnb);
+        if (g < 0) continue;
+        const long base = (long)xoff;
+        bool any = false;
+        // stage 1: X_beta[rows of g', (n2, qr) block of g] = sum_{n2'} Psi_g'[:, (n2', qr')] Rt^{n2 n2'}[qr, qr']^T,
+        // stored transposed into X^T (rows (n2, qr) of g, columns = rows of g')
+        for (const auto& cb : gcol[g]) {
+          const int n2 = cb[0], qr = cb[1];
+          TcTask t{};
+          t.Cb = mx->X_b.p + base + (long)cb[2] * gR[gp];
+          t.slice_stride = xstride;
+          t.ldcb = gR[gp];
+          t.m = gR[gp];
+          t.n = Rb.dim[qr];
+          t.nslices = nsl;
+          t.trans = 1;
+          g1.begin(t);
+          for (int n2p = 0; n2p < 4; ++n2p) {
+            const TRef& r = rt.ref[beta][n2 * 4 + n2p];
+            if (!r.p) continue;
+            const int qrp = Rb.find(gq[gp].first + LQA[n2p], gq[gp].second + LQB[n2p]);
+            if (qrp < 0) continue;
+            const auto cpp = cpos[qrp * 4 + n2p];
+            if (cpp[0] != gp) continue;
+            const OpLayout& Lay = Renv.cls[r.cls];
+            const int bl = Lay.blk_of_col[qrp];
+            if (bl < 0 || Lay.blocks[bl].rs != qr) continue;
+            const MirrorRef& mr = rm[beta][n2 * 4 + n2p];
+            const int kk = Rb.dim[qrp];
+            g1.term(mx->psi_b.p + goff[gp] + cpp[1], ptot, gC[gp], mir + mr.off + (*mr.boff)[bl], mr.stride, pad8(kk),
+                    kk, mr.neg, nsl);
           }
-    }
-    for (size_t pb = 0; pb < P.blocks.size(); ++pb) {
-      const Block& ob = P.blocks[pb];
-      int ql = ob.rs, n1 = P.b1[pb], n2 = P.b2[pb];
-      TcTask t{};
-      t.C = mx->sig_f.p + ob.off;
-      t.ldc = ob.cols;
-      t.m = ob.rows;
-      t.n = ob.cols;
-      t.beta = 1;
-      g2.begin(t);
-      for (size_t beta = ch.first; beta < ch.second; ++beta) {
-        const auto& xp = xpos[beta - ch.first];
-        for (int n1p = 0; n1p < 4; ++n1p) {
-          const TRef& r = lt.ref[beta][n1 * 4 + n1p];
-          if (!r.p) continue;
-          const OpLayout& Lay = Lenv.cls[r.cls];
-          int qlp = Lb.find(Lb.qa[ql] - Lay.da, Lb.qb[ql] - Lay.db);
-          if (qlp < 0) continue;
-          int bl = Lay.blk_of_col[qlp];
-          if (bl < 0 || Lay.blocks[bl].rs != ql) continue;
-          long xo = xp[(qlp * 4 + n1p) * 4 + n2];
-          if (xo < 0) continue;
-          const MirrorRef& mr = lm[beta][n1 * 4 + n1p];
-          const int kk = Lb.dim[qlp], ld = pad8(kk);
-          g2.term(mir + mr.off + (*mr.boff)[bl], mr.stride, ld, mx->X_b.p + xo, xstride, ld, kk, mr.neg, nsl);
+          if (g1.end()) any = true;
+        }
+        if (any) {
+          xp[gp] = base;
+          xoff += (size_t)gC[g] * gR[gp];
         }
       }
-      g2.end();
     }
+    // stage 2: sigma^T_g[:, (ql, n1) block] += sum_{beta, n1'} X_beta^T[:, (ql', n1')] Lt^{n1 n1'}[ql, ql']^T
+    for (int g = 0; g < ng; ++g)
+      for (const auto& rb : grow[g]) {
+        const int ql = rb[0], n1 = rb[1];
+        TcTask t{};
+        t.C = mx->sig_f.p + sgoff[g] + rb[2];
+        t.ldc = gR[g];
+        t.m = gC[g];
+        t.n = Lb.dim[ql];
+        t.beta = 1;
+        g2.begin(t);
+        for (size_t beta = ch.first; beta < ch.second; ++beta) {
+          const int gp = group_of(gq[g].first - mid[beta].dna, gq[g].second - mid[beta].dnb);
+          if (gp < 0) continue;
+          const long xo = xpos[beta - ch.first][gp];
+          if (xo < 0) continue;
+          for (int n1p = 0; n1p < 4; ++n1p) {
+            const TRef& r = lt.ref[beta][n1 * 4 + n1p];
+            if (!r.p) continue;
+            const OpLayout& Lay = Lenv.cls[r.cls];
+            const int qlp = Lb.find(Lb.qa[ql] - Lay.da, Lb.qb[ql] - Lay.db);
+            if (qlp < 0) continue;
+            const int bl = Lay.blk_of_col[qlp];
+            if (bl < 0 || Lay.blocks[bl].rs != ql) continue;
+            const auto rpp = rpos[qlp * 4 + n1p];
+            if (rpp[0] != gp) continue;
+            const MirrorRef& mr = lm[beta][n1 * 4 + n1p];
+            const int kk = Lb.dim[qlp];
+            g2.term(mx->X_b.p + xo + rpp[1], xstride, gR[gp], mir + mr.off + (*mr.boff)[bl], mr.stride, pad8(kk), kk,
+                    mr.neg, nsl);
+          }
+        }
+        g2.end();
+      }
+    // longest tiles first (static round-robin over persistent CTAs)
+    auto order = [&](TcBuilder& g) {
+      std::vector<long> w(g.tasks.size(), 0);
+      for (size_t i = 0; i < g.tasks.size(); ++i)
+        for (int t = g.tasks[i].t0; t < g.tasks[i].t1; ++t) w[i] += (g.terms[t].k + 63) / 64;
+      std::stable_sort(g.tiles.begin(), g.tiles.end(),
+                       [&](const TcTile& a, const TcTile& b) { return w[a.task] > w[b.task]; });
+    };
+    order(g2);
     mx->stage1.emplace_back();
     mx->stage1.back().tiles.upload(g1.tiles, c.stream);
     mx->stage1.back().tasks.upload(g1.tasks, c.stream);
@@ -326,16 +424,15 @@ void run_mixed_sigma(Context& c, SigmaPlan& plan, const double* x, double* y) {
   const size_t n = plan.psi.nnz;
   if (x != plan.in.p) cuda_check(cudaMemcpyAsync(plan.in.p, x, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "d2d");
   if (mx.n_psi_jobs) launch_conv(mx.psi_jobs, mx.n_psi_jobs, mx.psi_maxel, c.stream);
-  cuda_check(cudaMemsetAsync(mx.sig_f.p, 0, n * sizeof(float), c.stream), "memset");
+  cuda_check(cudaMemsetAsync(mx.sig_f.p, 0, mx.sig_total * sizeof(float), c.stream), "memset");
   for (size_t i = 0; i < mx.stage1.size(); ++i) {
     auto& s1 = mx.stage1[i];
     auto& s2 = mx.stage2[i];
     cuda_check(launch_gemm_bf16_tc(s1.tiles.p, s1.ntiles, s1.tasks.p, s1.terms.p, mx.err.p, c.stream), "tc stage 1");
     cuda_check(launch_gemm_bf16_tc(s2.tiles.p, s2.ntiles, s2.tasks.p, s2.terms.p, mx.err.p, c.stream), "tc stage 2");
   }
-  long g = std::min<long>(std::max<long>(1, ((long)n + 255) / 256), 152 * 16);
-  f32_to_f64_kernel<<<(unsigned)g, 256, 0, c.stream>>>(mx.sig_f.p, y, (long)n);
-  cuda_check(cudaGetLastError(), "f32->f64");
+  if (mx.n_sig_jobs) launch_unconv(mx.sig_jobs.p, mx.n_sig_jobs, mx.sig_maxel, c.stream);
+  if (y != plan.out.p) cuda_check(cudaMemcpyAsync(y, plan.out.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "d2d");
 }
 
 int mixed_error(Context& c, SigmaPlan& plan) {
