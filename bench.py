@@ -34,10 +34,14 @@ sys.path.insert(0, ROOT)
 METRIC = "H_eff·ψ TFLOP/s & sweep s at K=40 M=2000, mixed vs FP64 GPU at |ΔE|≤1e-6 Eh"
 
 WORKLOADS = {
-    # name: K, N, two_sz, M, spread of the synthetic sector dimensions, integral seed, h off-diagonal std
-    "k40_m2000": dict(K=40, N=40, two_sz=0, M=2000, spread=1.0, seed=1607, offdiag_std=0.05),
-    "k24_m512": dict(K=24, N=24, two_sz=0, M=512, spread=1.0, seed=1606, offdiag_std=0.1),
-    "k16_m256": dict(K=16, N=16, two_sz=0, M=256, spread=1.0, seed=1606, offdiag_std=0.1),
+    # name: K, N, two_sz, M, spread of the synthetic sector dimensions, integral seed, h off-diagonal std,
+    # M schedule of a full run (--sweeps), starting bond dimension of the random MPS
+    "k40_m2000": dict(K=40, N=40, two_sz=0, M=2000, spread=1.0, seed=1607, offdiag_std=0.05,
+                      ramp=[250, 500, 1000, 2000, 2000, 2000], m0=250),
+    "k24_m512": dict(K=24, N=24, two_sz=0, M=512, spread=1.0, seed=1606, offdiag_std=0.1,
+                     ramp=[128, 256] + [512] * 8, m0=128),
+    "k16_m256": dict(K=16, N=16, two_sz=0, M=256, spread=1.0, seed=1606, offdiag_std=0.1,
+                     ramp=[64, 128, 256, 256], m0=64),
 }
 # bounded CPU sample for the oracle: the projected-H_eff oracle works in the
 # full Fock space, so it can only take K <= 10; this is the largest sample of
@@ -334,6 +338,34 @@ def run_ours(args, rank, world, local_rank):
     ctx.close()
 
 
+def run_sweeps(args):
+    """Full two-site DMRG with the workload's M ramp (the 'sweep s' part of the metric)."""
+    import torch
+
+    import paper_1605_02611_gb300 as G
+    from paper_1605_02611_gb300 import synth
+    w = WORKLOADS[args.workload]
+    K, N = w["K"], w["N"]
+    ramp = w["ramp"][:args.sweeps] if args.sweeps > 0 else w["ramp"]
+    h, eri = synth.integrals(K, w["seed"], w["offdiag_std"])
+    bonds, T = synth.random_mps(K, N, w["two_sz"], w["m0"], w["seed"] + 1, w["spread"])
+    ctx = G.Context(h, eri, N, w["two_sz"])
+    ctx.set_mps(T, [b.labels() for b in bonds])
+    del T
+    tol = [1e-5] * (len(ramp) - 1) + [1e-6]
+    t0 = time.perf_counter()
+    out = ctx.run(ramp, tol, max_iter=args.max_iter, precision=args.precision)
+    wall = time.perf_counter() - t0
+    c = ctx.counters()
+    line = {"mode": "sweeps", "workload": args.workload, "K": K, "N": N, "precision": args.precision,
+            "M": ramp, "energy": out["energy"].tolist(), "discarded": out["discarded"].tolist(),
+            "sweep_s": out["seconds"].tolist(), "davidson_iters": out["davidson_iters"].tolist(),
+            "sigma_tflops": [f / s / 1e12 if s > 0 else None for f, s in zip(out["sigma_flops"], out["sigma_seconds"])],
+            "wall_s": wall, "phase_s": ctx.phase_times(), "sigma_calls": c["sigma_calls"]}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -347,6 +379,9 @@ def main():
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweeps", type=int, default=-1,
+                    help=">= 0: run a full DMRG with the workload's M ramp (0 = whole ramp) instead of the step bench")
+    ap.add_argument("--max-iter", type=int, default=40)
     ap.add_argument("--profile-sigma", type=int, default=0,
                     help="after setup run this many H_eff.psi calls only (for ncu captures) and exit")
     args = ap.parse_args()
@@ -355,6 +390,10 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.sweeps >= 0:
+        if rank == 0:
+            run_sweeps(args)
         return
     if world > 1:
         import torch

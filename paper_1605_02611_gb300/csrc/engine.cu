@@ -193,6 +193,12 @@ Context::~Context() {
   if (solver) cusolverDnDestroy(solver);
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
+  for (int i = 0; i < kAux; ++i) {
+    if (aux_solver[i]) cusolverDnDestroy(aux_solver[i]);
+    if (aux[i]) cudaStreamDestroy(aux[i]);
+  }
+  for (int i = 0; i <= kAux; ++i)
+    if (aux_ev[i]) cudaEventDestroy(aux_ev[i]);
   if (own_stream && stream) cudaStreamDestroy(stream);
 }
 
@@ -209,6 +215,13 @@ void ctx_init(Context& c) {
   cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
   cuda_check(cudaEventCreate(&c.ev0), "event");
   cuda_check(cudaEventCreate(&c.ev1), "event");
+  for (int i = 0; i < Context::kAux; ++i) {
+    cuda_check(cudaStreamCreateWithFlags(&c.aux[i], cudaStreamNonBlocking), "aux stream");
+    solver_check(cusolverDnCreate(&c.aux_solver[i]), "cusolverDnCreate");
+    solver_check(cusolverDnSetStream(c.aux_solver[i], c.aux[i]), "cusolverDnSetStream");
+  }
+  for (int i = 0; i <= Context::kAux; ++i)
+    cuda_check(cudaEventCreateWithFlags(&c.aux_ev[i], cudaEventDisableTiming), "aux event");
   solver_check(cusolverDnCreate(&c.solver), "cusolverDnCreate");
   solver_check(cusolverDnSetStream(c.solver, c.stream), "cusolverDnSetStream");
   c.mpo = build_mpo(c.K, c.h1.data(), c.eri.data());
@@ -895,6 +908,8 @@ double davidson(Context& c, SigmaPlan& plan, const double* diag, double* psi, co
   double theta = G[0];
   int it = 0;
   std::vector<double> w, Y, sub;
+  double best_rn = 1e300;
+  int since_best = 0;
   for (; it < o.max_iter; ++it) {
     sub.assign((size_t)m * m, 0.0);
     for (int i = 0; i < m; ++i)
@@ -911,6 +926,15 @@ double davidson(Context& c, SigmaPlan& plan, const double* diag, double* psi, co
     double rn = std::sqrt(dh.dots(c, r.p, 0, 1, r.p, n)[0]);
     if (!std::isfinite(rn)) throw Error(ST_ENOCONV, "Davidson: non-finite residual");
     if (rn <= o.tol) break;
+    if (o.stagnation > 0) {
+      // only near the operator's rounding floor (tensor-core sigma: ~1e-5 of |theta|)
+      if (rn < 0.9 * best_rn) {
+        best_rn = rn;
+        since_best = 0;
+      } else if (++since_best >= o.stagnation && rn < 2e-4 * std::fabs(theta)) {
+        break;
+      }
+    }
     launch_precond(n, r.p, diag, theta, 1e-8, t.p, c.stream);
     if (m == ms) {  // restart from the Ritz vector
       cuda_check(cudaMemcpyAsync(V.p, x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "d2d");
@@ -1021,20 +1045,39 @@ double decimate(Context& c, const PsiLayout& P, const double* psi, int M, int di
   solver_check(cusolverDnDsyevd_bufferSize(c.solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, maxd, Gram.p,
                                            maxd, evals.p, &lwork),
                "syevd_bufferSize");
+  // the group eigenproblems are independent: spread them over the auxiliary
+  // streams (one workspace each), joined back into the context stream
+  const int na = Context::kAux;
   DArr<double> work;
-  work.alloc(std::max(lwork, 1), c.stream);
+  work.alloc((size_t)std::max(lwork, 1) * na, c.stream);
   DArr<int> info;
   info.alloc(groups.size() + 1, c.stream);
+  cuda_check(cudaEventRecord(c.aux_ev[na], c.stream), "record");
+  for (int a = 0; a < na; ++a) cuda_check(cudaStreamWaitEvent(c.aux[a], c.aux_ev[na], 0), "wait");
   size_t eo = 0;
   std::vector<size_t> eoff(groups.size());
+  std::vector<size_t> order(groups.size());
+  std::iota(order.begin(), order.end(), 0);
+  std::sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+    int dx = direction == 0 ? groups[x].nr : groups[x].nc, dy = direction == 0 ? groups[y].nr : groups[y].nc;
+    return dx > dy;
+  });
   for (size_t gi = 0; gi < groups.size(); ++gi) {
+    eoff[gi] = eo;
+    eo += direction == 0 ? groups[gi].nr : groups[gi].nc;
+  }
+  for (size_t q = 0; q < order.size(); ++q) {
+    const size_t gi = order[q];
     auto& g = groups[gi];
     int d = direction == 0 ? g.nr : g.nc;
-    eoff[gi] = eo;
-    solver_check(cusolverDnDsyevd(c.solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, d, Gram.p + g.goff, d,
-                                  evals.p + eo, work.p, lwork, info.p + gi),
+    const int a = (int)(q % na);
+    solver_check(cusolverDnDsyevd(c.aux_solver[a], CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, d, Gram.p + g.goff, d,
+                                  evals.p + eoff[gi], work.p + (size_t)a * std::max(lwork, 1), lwork, info.p + gi),
                  "syevd");
-    eo += d;
+  }
+  for (int a = 0; a < na; ++a) {
+    cuda_check(cudaEventRecord(c.aux_ev[a], c.aux[a]), "record");
+    cuda_check(cudaStreamWaitEvent(c.stream, c.aux_ev[a], 0), "wait");
   }
   std::vector<double> ev(etot);
   std::vector<int> hinfo(groups.size());
@@ -1258,7 +1301,9 @@ double two_site_step(Context& c, int k, int dir, int M, const DavidsonOpts& o, b
     make_psi(c, c.sites[k], c.sites[k + 1], plan.psi, psi.p);
   compute_diag(c, lt, rt, k, plan.psi, diag.p);
   lap(2);
-  double e = davidson(c, plan, diag.p, psi.p, o, iters);
+  DavidsonOpts od = o;
+  if (plan.mx && od.stagnation == 0) od.stagnation = 6;
+  double e = davidson(c, plan, diag.p, psi.p, od, iters);
   if (psi_out)
     cuda_check(cudaMemcpyAsync(psi_out, psi.p, plan.psi.nnz * sizeof(double), cudaMemcpyDeviceToDevice, c.stream),
                "d2d");

@@ -210,6 +210,11 @@ struct Context {
   double sigma_flops_total = 0, sigma_time_total = 0, other_flops_total = 0;
   long sigma_calls = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // auxiliary streams/events for the independent per-sector eigenproblems of the decimation
+  static constexpr int kAux = 4;
+  cudaStream_t aux[kAux] = {nullptr, nullptr, nullptr, nullptr};
+  cusolverDnHandle_t aux_solver[kAux] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t aux_ev[kAux + 1] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   // wall seconds per phase of the two-site step (stream-synchronised):
   // 0 W-contracted operators, 1 sigma work lists, 2 diagonal, 3 Davidson,
   // 4 decimation, 5 environment update
@@ -250,6 +255,10 @@ void make_psi(Context& c, const SiteT& TL, const SiteT& TR, const PsiLayout& P, 
 struct DavidsonOpts {
   double tol = 1e-9;
   int max_iter = 200, max_sub = 24;
+  // stop when the residual norm is below 2e-4 |theta| and has not improved by 10 %
+  // for this many iterations (used with the tensor-core operator, whose rounding
+  // leaves a residual floor; 0 = never)
+  int stagnation = 0;
 };
 double davidson(Context& c, SigmaPlan& plan, const double* diag, double* psi, const DavidsonOpts& o,
                 int* iters);

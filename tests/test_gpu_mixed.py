@@ -82,7 +82,8 @@ def test_mixed_dmrg_k8_energy_equals_fci():
 
 
 def test_mixed_vs_fp64_truncated_sweeps():
-    """K=12, M=64: tensor-core sweeps reach the FP64 sweep energy within 1e-6 Eh."""
+    """K=12, M=64, six sweeps from the same start: tensor-core sweeps (FP64 last step)
+    reach the FP64 sweep energy within 1e-6 Eh."""
     require_gpu()
     K, N, M = 12, 12, 64
     h, eri = synth.integrals(K, 1606)
@@ -90,7 +91,7 @@ def test_mixed_vs_fp64_truncated_sweeps():
     e = {}
     for prec in (0, 2):
         ctx = context_with_mps(h, eri, N, 0, bonds, T)
-        e[prec] = ctx.run([M] * 4, [1e-6, 1e-7, 1e-8, 1e-9], precision=prec)["energy"]
+        e[prec] = ctx.run([M] * 6, [1e-6, 1e-7, 1e-8, 1e-9, 1e-9, 1e-9], precision=prec)["energy"]
         ctx.close()
     print("mixed - fp64 sweep energies:", e[2] - e[0])
     assert abs(e[2][-1] - e[0][-1]) < 1e-6
