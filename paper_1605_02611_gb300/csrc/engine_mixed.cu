@@ -361,7 +361,10 @@ void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, 
         }
       }
     }
-    // stage 2: sigma^T_g[:, (ql, n1) block] += sum_{beta, n1'} X_beta^T[:, (ql', n1')] Lt^{n1 n1'}[ql, ql']^T
+    // stage 2: sigma^T_g[:, (ql, n1) block] += sum_{beta, n1'} X_beta^T[:, (ql', n1')] Lt^{n1 n1'}[ql, ql']^T.
+    // Long term lists are split into parts that accumulate atomically (split-K), so
+    // that there are enough tiles for every resident CTA.
+    TcBuilder g2all;
     for (int g = 0; g < ng; ++g)
       for (const auto& rb : grow[g]) {
         const int ql = rb[0], n1 = rb[1];
@@ -370,8 +373,8 @@ void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, 
         t.ldc = gR[g];
         t.m = gC[g];
         t.n = Lb.dim[ql];
-        t.beta = 1;
-        g2.begin(t);
+        t.beta = 2;
+        g2all.begin(t);
         for (size_t beta = ch.first; beta < ch.second; ++beta) {
           const int gp = group_of(gq[g].first - mid[beta].dna, gq[g].second - mid[beta].dnb);
           if (gp < 0) continue;
@@ -389,12 +392,39 @@ void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, 
             if (rpp[0] != gp) continue;
             const MirrorRef& mr = lm[beta][n1 * 4 + n1p];
             const int kk = Lb.dim[qlp];
-            g2.term(mx->X_b.p + xo + rpp[1], xstride, gR[gp], mir + mr.off + (*mr.boff)[bl], mr.stride, pad8(kk), kk,
-                    mr.neg, nsl);
+            g2all.term(mx->X_b.p + xo + rpp[1], xstride, gR[gp], mir + mr.off + (*mr.boff)[bl], mr.stride, pad8(kk),
+                       kk, mr.neg, nsl);
           }
         }
-        g2.end();
+        g2all.end();
       }
+    {
+      // k-steps per task and the split that gives about 4 tiles per resident CTA
+      long total = 0;
+      std::vector<long> w(g2all.tasks.size(), 0);
+      for (size_t i = 0; i < g2all.tasks.size(); ++i) {
+        for (int t = g2all.tasks[i].t0; t < g2all.tasks[i].t1; ++t) w[i] += (g2all.terms[t].k + 63) / 64;
+        total += w[i] * ((g2all.tasks[i].m + 127) / 128);
+      }
+      const long target = std::max<long>(1, total / (4L * 2 * 152));
+      for (size_t i = 0; i < g2all.tasks.size(); ++i) {
+        const TcTask& tk = g2all.tasks[i];
+        long acc = 0;
+        int t0 = tk.t0;
+        for (int t = tk.t0; t < tk.t1; ++t) {
+          acc += (g2all.terms[t].k + 63) / 64;
+          if (acc >= target || t + 1 == tk.t1) {
+            TcTask part = tk;
+            g2.begin(part);
+            for (int u = t0; u <= t; ++u) g2.terms.push_back(g2all.terms[u]);
+            g2.tasks.back().t1 = (int)g2.terms.size();
+            g2.end();
+            t0 = t + 1;
+            acc = 0;
+          }
+        }
+      }
+    }
     // longest tiles first (static round-robin over persistent CTAs)
     auto order = [&](TcBuilder& g) {
       std::vector<long> w(g.tasks.size(), 0);

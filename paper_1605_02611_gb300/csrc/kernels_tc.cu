@@ -283,8 +283,12 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
             float x = __uint_as_float(v[q]);
             if (tk.C) {
               float* cp = tk.C + (tk.trans ? (long)col * tk.ldc + row : (long)row * tk.ldc + col);
-              if (tk.beta) x += *cp;
-              *cp = x;
+              if (tk.beta == 2) {
+                atomicAdd(cp, x);
+              } else {
+                if (tk.beta) x += *cp;
+                *cp = x;
+              }
             }
             if (tk.Cb) {
               const long ob = tk.trans ? (long)col * tk.ldcb + row : (long)row * tk.ldcb + col;

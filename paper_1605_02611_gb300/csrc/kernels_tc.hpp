@@ -18,7 +18,8 @@ struct TcTerm {
 };
 // outputs: C (fp32, optional, += if beta) and/or Cb (bf16, optional): nslices bf16
 // slices x = s0 + s1 + s2 written slice_stride elements apart.  trans: element
-// (i, j) of the block goes to [j * ld + i] instead of [i * ld + j].
+// (i, j) of the block goes to [j * ld + i] instead of [i * ld + j].  beta == 2:
+// FP32 atomic accumulation into C (several tasks may split one block's term list).
 struct TcTask {
   float* C;
   __nv_bfloat16* Cb;
