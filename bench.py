@@ -285,7 +285,7 @@ def run_ours(args, rank, world, local_rank):
     achieved_alg = sig_fl / sig_s / 1e12 if sig_s > 0 else None
     # products the tensor cores execute per algorithmic multiply-add: 1 (one BF16
     # pass) or 6 (three BF16 slices, products s_i t_j with i + j <= 2)
-    nprod = {0: 1, 1: 1, 2: 6}[args.precision]
+    nprod = {0: 1, 1: 1, 2: 6, 3: 3}[args.precision]
     fp64_cmp = None
     if args.precision > 0 and args.compare_fp64:
         # the same H_eff.psi on the FP64 units (one call), for the mixed/FP64 speed-up
@@ -312,7 +312,7 @@ def run_ours(args, rank, world, local_rank):
                 "kernel": "gemm_bf16_tc_kernel (sigma stages 1+2)",
                 "peak_note": f"{src} bf16 dense, sustained (kernel timed inside a long step); achieved counts the "
                              f"{nprod} tensor-core product(s) per algorithmic multiply-add"}
-        dtype = "bf16" if args.precision == 1 else "bf16x3"
+        dtype = {1: "bf16", 2: "bf16x3", 3: "bf16x2"}[args.precision]
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -367,6 +367,94 @@ def run_sweeps(args):
     ctx.close()
 
 
+BATCH = dict(P=64, K=(16, 32), M=(256, 1000), seed=4096, spread=1.0)
+
+
+def run_batched(args):
+    """Batched H_eff.psi: P independent central two-site problems (each its own
+    integrals, K and M drawn uniformly, half filling, S_z=0) whose tensor-core
+    work lists are fused into one persistent launch per stage and replayed as a
+    CUDA graph; compared with the same problems' sigmas run one by one."""
+    import concurrent.futures as cf
+
+    import torch
+
+    import paper_1605_02611_gb300 as G
+    from paper_1605_02611_gb300 import synth
+    b = dict(BATCH)
+    b["P"] = args.batched
+    prec = args.precision if args.precision > 0 else 2
+    rng = np.random.default_rng(b["seed"])
+    specs = []
+    for p in range(b["P"]):
+        K = 2 * int(rng.integers(b["K"][0] // 2, b["K"][1] // 2 + 1))
+        M = int(rng.integers(b["M"][0], b["M"][1] + 1))
+        specs.append((p, K, M))
+    torch.cuda.init()
+
+    def build(spec):
+        p, K, M = spec
+        k = K // 2 - 1
+        h, eri = synth.integrals(K, b["seed"] + p)
+        bonds, T = synth.random_isometric_mps(K, K, 0, M, b["seed"] + 1000 + p, k, b["spread"])
+        ctx = G.Context(h, eri, K, 0)
+        ctx.set_precision(prec)
+        ctx.keep_host_plans(True)
+        ctx.set_mps(T, [bd.labels() for bd in bonds])
+        del T
+        ctx.prepare(k)
+        return ctx
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        ctxs = list(ex.map(build, specs))
+    setup_s = time.perf_counter() - t0
+    xs = [torch.randn(c.nnz, device="cuda", dtype=torch.float64) for c in ctxs]
+    ys = [torch.empty_like(x) for x in xs]
+    torch.cuda.synchronize()
+    xp = [x.data_ptr() for x in xs]
+    yp = [y.data_ptr() for y in ys]
+    # the same sigmas one by one (each context on its own stream, in sequence)
+    seq_ms = 0.0
+    for c, x, y in zip(ctxs, xp, yp):
+        c.sigma_device(x, y)
+        seq_ms += c.sigma_timing(1, x, y)
+    bt = G.Batch(ctxs)
+    eager = []
+    fl = 0.0
+    for _ in range(args.warmup + args.steps):
+        ms, fl = bt.sigma(xp, yp, use_graph=False)
+        eager.append(ms)
+    bt.sigma(xp, yp, use_graph=True)  # eager pass + capture
+    graph = []
+    l0 = G.kernel_launches()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    for i in range(args.warmup + args.steps):
+        ms, fl = bt.sigma(xp, yp, use_graph=True)
+        if i >= args.warmup:
+            graph.append(ms)
+    clk = clocks.stop()
+    launches = G.kernel_launches() - l0
+    eager_ms = statistics.mean(eager[args.warmup:])
+    graph_ms = statistics.mean(graph)
+    peaks, src = _measured_peaks()
+    nprod = {1: 1, 2: 6, 3: 3}[prec]
+    line = {"mode": "batched", "problems": b["P"], "K_range": b["K"], "M_range": b["M"], "precision": prec,
+            "Ks": [s[1] for s in specs], "Ms": [s[2] for s in specs], "psi_nnz_total": int(sum(c.nnz for c in ctxs)),
+            "flops_per_batch": fl, "sequential_ms": seq_ms, "batched_eager_ms": eager_ms, "batched_graph_ms": graph_ms,
+            "sequential_tflops": fl / seq_ms / 1e9, "batched_tflops": fl / graph_ms / 1e9,
+            "speedup_over_sequential": seq_ms / graph_ms,
+            "tensor_frac": fl * nprod / graph_ms / 1e9 / peaks["bf16_tflops_sustained"],
+            "peak_note": f"{src} bf16 sustained; {nprod} tensor-core products per algorithmic multiply-add",
+            "gpu_launches_per_batch": launches / max(1, args.warmup + args.steps), "setup_s": setup_s,
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    bt.close()
+    for c in ctxs:
+        c.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -376,14 +464,16 @@ def main():
     ap.add_argument("--workload", default="k40_m2000", choices=sorted(WORKLOADS))
     ap.add_argument("--dav-iters", type=int, default=16,
                     help="Davidson iterations per step (sweeps at K=24 averaged ~20 per site)")
-    ap.add_argument("--precision", type=int, default=2, choices=[0, 1, 2],
-                    help="0 FP64 units, 1 tensor cores one BF16 pass, 2 tensor cores three BF16 slices")
+    ap.add_argument("--precision", type=int, default=2, choices=[0, 1, 2, 3],
+                    help="0 FP64 units, 1 tensor cores one BF16 pass, 2 tensor cores three BF16 slices, 3 two slices")
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweeps", type=int, default=-1,
                     help=">= 0: run a full DMRG with the workload's M ramp (0 = whole ramp) instead of the step bench")
     ap.add_argument("--max-iter", type=int, default=40)
+    ap.add_argument("--batched", type=int, default=0,
+                    help="> 0: batched H_eff.psi over this many independent problems instead of the step bench")
     ap.add_argument("--profile-sigma", type=int, default=0,
                     help="after setup run this many H_eff.psi calls only (for ncu captures) and exit")
     args = ap.parse_args()
@@ -396,6 +486,10 @@ def main():
     if args.sweeps >= 0:
         if rank == 0:
             run_sweeps(args)
+        return
+    if args.batched > 0:
+        if rank == 0:
+            run_batched(args)
         return
     if world > 1:
         import torch

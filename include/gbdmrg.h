@@ -90,8 +90,39 @@ gbdmrg_status gbdmrg_get_bond(gbdmrg_ctx* ctx, int32_t bond, int32_t* D, int32_t
  * 0 = FP64 grouped GEMMs on the FP64 units; 1 = tensor cores (tcgen05), one
  * BF16 pass with FP32 accumulation; 2 = tensor cores, every operand split in
  * three BF16 slices and the six leading slice products accumulated in FP32
- * (about FP32 accuracy).  Environments, Davidson, decimation stay FP64. */
+ * (about FP32 accuracy); 3 = tensor cores, two BF16 slices per operand and the
+ * three leading products (operands to ~2^-16 relative).  Environments,
+ * Davidson, decimation stay FP64. */
 gbdmrg_status gbdmrg_set_precision(gbdmrg_ctx* ctx, int32_t precision);
+
+/* Device memory (MB) for the per-chunk intermediates X_beta of one H_eff.psi
+ * (default 2048): the operator terms are processed in chunks whose
+ * intermediates fit this budget.  Takes effect at the next gbdmrg_prepare. */
+gbdmrg_status gbdmrg_set_chunk_budget(gbdmrg_ctx* ctx, int32_t megabytes);
+
+/* Keep host copies of the tensor-core work lists built by later gbdmrg_prepare
+ * calls (needed by gbdmrg_batch_create; costs host memory).  keep: 0 or 1. */
+gbdmrg_status gbdmrg_keep_host_plans(gbdmrg_ctx* ctx, int32_t keep);
+
+/* Batched sigma vectors: n independent two-site problems, each a context on the
+ * same device prepared (gbdmrg_prepare) in precision 1, 2 or 3 after
+ * gbdmrg_keep_host_plans(ctx, 1).  Their H_eff.psi work lists are concatenated
+ * so that one persistent tensor-core launch per stage serves every problem (the
+ * independent sums over operator terms of Sec. "Perfect parallelism in the sum
+ * of operators formulation", taken across problems).  Runs on the stream of
+ * ctxs[0].  The contexts must outlive the batch and stay prepared.  Errors of
+ * gbdmrg_batch_create are reported through gbdmrg_last_error(ctxs[0]). */
+typedef struct gbdmrg_batch gbdmrg_batch;
+gbdmrg_status gbdmrg_batch_create(int32_t n, gbdmrg_ctx* const* ctxs, gbdmrg_batch** out);
+/* sigma_p = H_eff,p psi_p for every problem p (device pointers, packed layouts of
+ * each context).  use_graph != 0: the device work is captured once into a CUDA
+ * graph (after one eager pass) and replayed on later calls.  ms (optional):
+ * device time of the batched work (CUDA events, excluding the input/output
+ * copies); flops (optional): total algorithmic flops of the batch. */
+gbdmrg_status gbdmrg_batch_sigma(gbdmrg_batch* b, const double* const* psi_dev, double* const* sigma_dev,
+                                 int32_t use_graph, double* ms, double* flops);
+const char* gbdmrg_batch_last_error(const gbdmrg_batch* b);
+void gbdmrg_batch_destroy(gbdmrg_batch* b);
 
 /* Build the renormalised operators (Eq. renormop) of bonds k and k+2 from the
  * current MPS tensors in whatever gauge they are (blocking + decimation,
@@ -169,8 +200,9 @@ int64_t gbdmrg_kernel_launches(void);
  * sigma (tcgen05, BF16 operands, FP32 accumulation).  For every task i:
  *   C_i (+)= sum_{t in [t0_i, t1_i)} (-1)^neg_t A_t B_t^T
  * with C_i fp32 row-major (m_i x n_i, ldc_i), A_t (m_i x k_t) and B_t (n_i x k_t)
- * row-major bf16, 16-byte aligned, leading dimensions multiples of 8 and zero
- * padding between k_t and the leading dimension.  All matrix pointers are
+ * row-major bf16, 16-byte aligned, leading dimensions multiples of 8; columns
+ * are read only up to the first multiple of 8 at or above k_t, and those past
+ * k_t must be zero in at least one operand (finite in the other).  All matrix pointers are
  * device pointers; the descriptor arrays are host arrays:
  * tasks[8*i] = (C, ldc, m, n, beta, t0, t1, trans), terms[6*t] = (A, B, lda, ldb, k, neg);
  * trans != 0 stores element (r, c) of the block at C[c * ldc + r].
@@ -193,7 +225,7 @@ typedef struct {
   const int32_t* M;
   const double* dav_tol;
   int32_t dav_max_iter;
-  int32_t precision; /* as gbdmrg_set_precision: 0 FP64, 1 BF16 pass, 2 BF16 x3 slices */
+  int32_t precision; /* as gbdmrg_set_precision: 0 FP64, 1 BF16 pass, 2 BF16 x3, 3 BF16 x2 slices */
 } gbdmrg_schedule;
 
 /* Run the sweeps from the current MPS (brought to right-canonical form first).
@@ -204,6 +236,83 @@ gbdmrg_status gbdmrg_run(gbdmrg_ctx* ctx, const gbdmrg_schedule* sched, double* 
  * Davidson iterations (each array nsweeps long, any may be NULL). */
 gbdmrg_status gbdmrg_run_stats(gbdmrg_ctx* ctx, double* seconds, double* sigma_flops, double* sigma_seconds,
                                int32_t* davidson_iters);
+
+/* ------------------------------------------------------------------------
+ * Learned Davidson preconditioner.
+ *
+ * The paper's solving step (Sec. "The DMRG in renormalization group language")
+ * finds the lowest eigenpair of H_eff without naming the eigensolver; the
+ * library uses Davidson, whose diagonal preconditioner turns the residual
+ * r = H_eff x - theta x into t_i = r_i / (theta - d_i), d = diag(H_eff),
+ * |theta - d_i| clamped to >= 1e-8.  The learned preconditioner keeps this form
+ * and multiplies element i by (1 + g(f_i)), where g is a 3-layer network
+ * (5 -> 256 -> 256 -> 1, GELU, BF16 weights, FP32 accumulation) of the
+ * per-element features (n elements, b the quantum-number block of element i,
+ * delta_i = d_i - theta):
+ *   f0 = r_i sqrt(n)/|r|, f1 = asinh(delta_i), f2 = delta_i/(delta_i^2 + 0.01),
+ *   f3 = asinh(rms_b(r) sqrt(n)/|r|), f4 = asinh(mean_b(d) - theta).
+ * Parameters, as one float array of gbdmrg_mlp_nparams() entries:
+ *   W1[256][5], b1[256], W2[256][256], b2[256], W3[256], b3   (row = output)
+ * Training pairs (f, P, T): P = p_i s and T = tau_i s with p the diagonal
+ * correction, tau = psi/(x . psi) - x the exact correction of a Ritz vector x
+ * towards the converged psi, s = sqrt(n)/|tau|, both clipped to [-100, 100];
+ * loss = mean(((1 + g) P - T)^2).  The untrained network (W3 = 0, b3 = 0) is
+ * the diagonal preconditioner.
+ * ------------------------------------------------------------------------ */
+typedef struct gbdmrg_mlp gbdmrg_mlp;
+int64_t gbdmrg_mlp_nparams(void);
+/* W1 and W2 drawn from N(0, 1/fan_in) with the seed, the rest zero.  stream:
+ * a cudaStream_t, or NULL for a stream owned by the network. */
+gbdmrg_status gbdmrg_mlp_create(uint64_t seed, void* stream, gbdmrg_mlp** out);
+void gbdmrg_mlp_destroy(gbdmrg_mlp* mlp);
+const char* gbdmrg_mlp_last_error(const gbdmrg_mlp* mlp);
+/* host arrays of gbdmrg_mlp_nparams() floats; set resets the Adam state.
+ * GBDMRG_EINVAL on a non-finite parameter. */
+gbdmrg_status gbdmrg_mlp_set_params(gbdmrg_mlp* mlp, const float* params);
+gbdmrg_status gbdmrg_mlp_get_params(gbdmrg_mlp* mlp, float* params);
+/* g for n feature rows features[n][5].  inference = 0: training numerics (FP32,
+ * weights rounded to BF16); 1: inference numerics (h1 rounded to BF16, the
+ * 256 x 256 layer on the tensor cores).  on_device: pointers are device (1) or
+ * host (0) memory. */
+gbdmrg_status gbdmrg_mlp_forward(gbdmrg_mlp* mlp, const float* features, int64_t n, float* g, int32_t inference,
+                                 int32_t on_device);
+/* Loss of n pairs and its gradient (training numerics; grad: host array of
+ * gbdmrg_mlp_nparams() floats, may be NULL). */
+gbdmrg_status gbdmrg_mlp_loss_grad(gbdmrg_mlp* mlp, const float* features, const float* P, const float* T, int64_t n,
+                                   int32_t on_device, float* grad, double* loss);
+/* Adam (beta 0.9/0.999, eps 1e-8, step size lr) for `epochs` passes of
+ * ceil(n/batch) minibatches drawn with replacement by a counter-based hash of
+ * seed.  loss_first / loss_last (may be NULL): mean loss of the first and the
+ * last epoch. */
+gbdmrg_status gbdmrg_mlp_train(gbdmrg_mlp* mlp, const float* features, const float* P, const float* T, int64_t n,
+                               int32_t on_device, int32_t epochs, int32_t batch, float lr, uint64_t seed,
+                               double* loss_first, double* loss_last);
+/* Davidson of this context uses the network (not owned; must outlive its use),
+ * or the diagonal preconditioner when mlp is NULL.  Per iteration the diagonal
+ * correction is used instead when the residual norm did not decrease since the
+ * previous iteration or the network produced a non-finite value. */
+gbdmrg_status gbdmrg_set_preconditioner(gbdmrg_ctx* ctx, gbdmrg_mlp* mlp);
+/* The correction t for residual r and Ritz value theta at the prepared
+ * two-site problem (packed layout), with the current preconditioner. */
+gbdmrg_status gbdmrg_precondition(gbdmrg_ctx* ctx, const double* r, double theta, double* t, int32_t on_device);
+/* Training pairs at ns elements drawn by the SplitMix64 hash of (seed + j),
+ * j = 0..ns-1, index = hash mod n: features[ns][5], P[ns], T[ns], idx[ns]
+ * (idx may be NULL) for Ritz vector x, residual r, Ritz value theta and
+ * converged vector psi of the prepared problem.  written = ns, or 0 when
+ * x = psi (no correction). */
+gbdmrg_status gbdmrg_make_pairs(gbdmrg_ctx* ctx, const double* x, const double* r, double theta, const double* psi,
+                                int64_t ns, uint64_t seed, int32_t on_device, float* features, float* P, float* T,
+                                int64_t* idx, int64_t* written);
+/* Collect up to `capacity` pairs during later Davidson runs of this context:
+ * per solve, from the Ritz vectors of iterations 0, 1, 2, 4, 7, 11 and 16
+ * (those not yet converged and with |x . psi| >= 0.5), per_iteration pairs
+ * each.  Resets the collection. */
+gbdmrg_status gbdmrg_set_harvest(gbdmrg_ctx* ctx, int64_t capacity, int32_t per_iteration, uint64_t seed);
+/* Number of pairs collected (n) and, for non-NULL host arrays, the pairs. */
+gbdmrg_status gbdmrg_get_harvest(gbdmrg_ctx* ctx, float* features, float* P, float* T, int64_t* n);
+/* Davidson iterations that used the network, and those that fell back to
+ * the diagonal correction, since the context was created. */
+gbdmrg_status gbdmrg_precond_counters(gbdmrg_ctx* ctx, int64_t* learned, int64_t* fallbacks);
 
 #ifdef __cplusplus
 }

@@ -23,6 +23,7 @@ _I32 = C.c_int32
 _PI32 = C.POINTER(C.c_int32)
 _PI64 = C.POINTER(C.c_int64)
 _PD = C.POINTER(C.c_double)
+_PF = C.POINTER(C.c_float)
 
 
 class Problem(C.Structure):
@@ -47,6 +48,12 @@ SIGNATURES = {
     "gbdmrg_get_bond": (C.c_int, [_P, _I32, _PI32, _PI32]),
     "gbdmrg_set_precision": (C.c_int, [_P, _I32]),
     "gbdmrg_prepare": (C.c_int, [_P, _I32]),
+    "gbdmrg_keep_host_plans": (C.c_int, [_P, _I32]),
+    "gbdmrg_set_chunk_budget": (C.c_int, [_P, _I32]),
+    "gbdmrg_batch_create": (C.c_int, [_I32, C.POINTER(_P), C.POINTER(_P)]),
+    "gbdmrg_batch_sigma": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), _I32, _PD, _PD]),
+    "gbdmrg_batch_last_error": (C.c_char_p, [_P]),
+    "gbdmrg_batch_destroy": (None, [_P]),
     "gbdmrg_plan": (C.c_int, [_P, _I32]),
     "gbdmrg_psi_layout": (C.c_int, [_P, _PI64, _PI64, _PI64]),
     "gbdmrg_sigma": (C.c_int, [_P, _P, _P, _I32, _PD]),
@@ -61,6 +68,22 @@ SIGNATURES = {
     "gbdmrg_sigma_flops_host": (C.c_int, [C.POINTER(Problem), _I32, _I32, _PI32, _I32, _PI32, _PD]),
     "gbdmrg_run": (C.c_int, [_P, C.POINTER(Schedule), _PD, _PD]),
     "gbdmrg_run_stats": (C.c_int, [_P, _PD, _PD, _PD, _PI32]),
+    "gbdmrg_mlp_nparams": (C.c_int64, []),
+    "gbdmrg_mlp_create": (C.c_int, [C.c_uint64, _P, C.POINTER(_P)]),
+    "gbdmrg_mlp_destroy": (None, [_P]),
+    "gbdmrg_mlp_last_error": (C.c_char_p, [_P]),
+    "gbdmrg_mlp_set_params": (C.c_int, [_P, _PF]),
+    "gbdmrg_mlp_get_params": (C.c_int, [_P, _PF]),
+    "gbdmrg_mlp_forward": (C.c_int, [_P, _P, C.c_int64, _P, _I32, _I32]),
+    "gbdmrg_mlp_loss_grad": (C.c_int, [_P, _P, _P, _P, C.c_int64, _I32, _PF, _PD]),
+    "gbdmrg_mlp_train": (C.c_int, [_P, _P, _P, _P, C.c_int64, _I32, _I32, _I32, C.c_float, C.c_uint64, _PD, _PD]),
+    "gbdmrg_set_preconditioner": (C.c_int, [_P, _P]),
+    "gbdmrg_precondition": (C.c_int, [_P, _P, C.c_double, _P, _I32]),
+    "gbdmrg_make_pairs": (C.c_int, [_P, _P, _P, C.c_double, _P, C.c_int64, C.c_uint64, _I32, _P, _P, _P, _P,
+                                    _PI64]),
+    "gbdmrg_set_harvest": (C.c_int, [_P, C.c_int64, _I32, C.c_uint64]),
+    "gbdmrg_get_harvest": (C.c_int, [_P, _P, _P, _P, _PI64]),
+    "gbdmrg_precond_counters": (C.c_int, [_P, _PI64, _PI64]),
 }
 
 _lib = None
@@ -137,6 +160,111 @@ def sigma_flops_host(h1, eri, N: int, two_sz: int, k: int, lab_l, lab_r) -> floa
     return fl.value
 
 
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+class Mlp:
+    """Learned Davidson preconditioner network (gbdmrg_mlp_*)."""
+
+    def __init__(self, seed: int = 0, stream: int | None = None):
+        self.lib = load()
+        self.nparams = int(self.lib.gbdmrg_mlp_nparams())
+        h = _P()
+        st = self.lib.gbdmrg_mlp_create(seed, _P(stream or 0), C.byref(h))
+        if st != 0:
+            raise GbdmrgError(f"gbdmrg_mlp_create failed: {STATUS.get(st, st)}")
+        self.h = h
+
+    def _check(self, st: int, what: str):
+        if st != 0:
+            msg = self.lib.gbdmrg_mlp_last_error(self.h).decode()
+            raise GbdmrgError(f"{what}: {STATUS.get(st, st)}: {msg}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gbdmrg_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        p = np.zeros(self.nparams, dtype=np.float32)
+        self._check(self.lib.gbdmrg_mlp_get_params(self.h, p.ctypes.data_as(_PF)), "get_params")
+        return p
+
+    def set_params(self, p):
+        p = _f32(p)
+        assert p.size == self.nparams
+        self._check(self.lib.gbdmrg_mlp_set_params(self.h, p.ctypes.data_as(_PF)), "set_params")
+
+    def forward(self, F, inference: bool = False) -> np.ndarray:
+        F = _f32(F).reshape(-1, 5)
+        g = np.zeros(F.shape[0], dtype=np.float32)
+        self._check(self.lib.gbdmrg_mlp_forward(self.h, F.ctypes.data_as(_P), F.shape[0], g.ctypes.data_as(_P),
+                                                int(inference), 0), "forward")
+        return g
+
+    def loss_grad(self, F, P, T):
+        F, P, T = _f32(F).reshape(-1, 5), _f32(P), _f32(T)
+        g = np.zeros(self.nparams, dtype=np.float32)
+        L = C.c_double()
+        self._check(self.lib.gbdmrg_mlp_loss_grad(self.h, F.ctypes.data_as(_P), P.ctypes.data_as(_P),
+                                                  T.ctypes.data_as(_P), F.shape[0], 0, g.ctypes.data_as(_PF),
+                                                  C.byref(L)), "loss_grad")
+        return L.value, g
+
+    def train(self, F, P, T, epochs: int = 20, batch: int = 4096, lr: float = 1e-3, seed: int = 0):
+        F, P, T = _f32(F).reshape(-1, 5), _f32(P), _f32(T)
+        a, b = C.c_double(), C.c_double()
+        self._check(self.lib.gbdmrg_mlp_train(self.h, F.ctypes.data_as(_P), P.ctypes.data_as(_P),
+                                              T.ctypes.data_as(_P), F.shape[0], 0, epochs, batch, lr, seed,
+                                              C.byref(a), C.byref(b)), "train")
+        return a.value, b.value
+
+
+class Batch:
+    """Batched tensor-core sigma over several prepared contexts (gbdmrg_batch_*)."""
+
+    def __init__(self, contexts):
+        self.lib = load()
+        self.ctxs = list(contexts)
+        arr = (_P * len(self.ctxs))(*[c.h for c in self.ctxs])
+        h = _P()
+        st = self.lib.gbdmrg_batch_create(len(self.ctxs), arr, C.byref(h))
+        if st != 0:
+            msg = self.lib.gbdmrg_last_error(self.ctxs[0].h).decode() if self.ctxs else ""
+            raise GbdmrgError(f"gbdmrg_batch_create failed: {STATUS.get(st, st)}: {msg}")
+        self.h = h
+
+    def sigma(self, psi_ptrs, sigma_ptrs, use_graph: bool = True):
+        """sigma_p = H_eff,p psi_p on device buffers; returns (device ms, algorithmic flops)."""
+        n = len(self.ctxs)
+        pin = (_P * n)(*psi_ptrs)
+        pout = (_P * n)(*sigma_ptrs)
+        ms, fl = C.c_double(), C.c_double()
+        st = self.lib.gbdmrg_batch_sigma(self.h, pin, pout, int(use_graph), C.byref(ms), C.byref(fl))
+        if st != 0:
+            msg = self.lib.gbdmrg_batch_last_error(self.h).decode()
+            raise GbdmrgError(f"gbdmrg_batch_sigma failed: {STATUS.get(st, st)}: {msg}")
+        return ms.value, fl.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gbdmrg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Context:
     """One DMRG problem on the current CUDA device (gbdmrg_create)."""
 
@@ -205,8 +333,15 @@ class Context:
         return q
 
     # ---- two-site problem
+    def keep_host_plans(self, keep: bool = True):
+        self._check(self.lib.gbdmrg_keep_host_plans(self.h, int(keep)), "keep_host_plans")
+
+    def set_chunk_budget(self, megabytes: int):
+        """Device memory for the per-chunk sigma intermediates (next prepare)."""
+        self._check(self.lib.gbdmrg_set_chunk_budget(self.h, megabytes), "set_chunk_budget")
+
     def set_precision(self, mode: int):
-        """0 FP64, 1 tensor-core BF16 single pass, 2 tensor-core BF16 x3 slices."""
+        """0 FP64, 1 tensor-core BF16 single pass, 2 BF16 x3 slices, 3 BF16 x2 slices."""
         self._check(self.lib.gbdmrg_set_precision(self.h, mode), "set_precision")
 
     def prepare(self, k: int):
@@ -289,6 +424,53 @@ class Context:
         n = C.c_int64()
         self._check(self.lib.gbdmrg_counters(self.h, C.byref(f), C.byref(s), C.byref(n), C.byref(o)), "counters")
         return dict(sigma_flops=f.value, sigma_seconds=s.value, sigma_calls=n.value, other_flops=o.value)
+
+    # ---- learned preconditioner
+    def set_preconditioner(self, mlp):
+        """Use the network `mlp` (an Mlp) in Davidson, or the diagonal one when None."""
+        self._mlp = mlp
+        self._check(self.lib.gbdmrg_set_preconditioner(self.h, mlp.h if mlp is not None else None),
+                    "set_preconditioner")
+
+    def precondition(self, r, theta: float) -> np.ndarray:
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        t = np.zeros_like(r)
+        self._check(self.lib.gbdmrg_precondition(self.h, r.ctypes.data_as(_P), theta, t.ctypes.data_as(_P), 0),
+                    "precondition")
+        return t
+
+    def make_pairs(self, x, r, theta: float, psi, ns: int, seed: int):
+        x, r, psi = (np.ascontiguousarray(v, dtype=np.float64) for v in (x, r, psi))
+        F = np.zeros((ns, 5), dtype=np.float32)
+        P = np.zeros(ns, dtype=np.float32)
+        T = np.zeros(ns, dtype=np.float32)
+        idx = np.zeros(ns, dtype=np.int64)
+        w = C.c_int64()
+        self._check(self.lib.gbdmrg_make_pairs(self.h, x.ctypes.data_as(_P), r.ctypes.data_as(_P), theta,
+                                               psi.ctypes.data_as(_P), ns, seed, 0, F.ctypes.data_as(_P),
+                                               P.ctypes.data_as(_P), T.ctypes.data_as(_P), idx.ctypes.data_as(_P),
+                                               C.byref(w)), "make_pairs")
+        k = w.value
+        return F[:k], P[:k], T[:k], idx[:k]
+
+    def set_harvest(self, capacity: int, per_iteration: int, seed: int = 0):
+        self._check(self.lib.gbdmrg_set_harvest(self.h, capacity, per_iteration, seed), "set_harvest")
+
+    def get_harvest(self):
+        n = C.c_int64()
+        self._check(self.lib.gbdmrg_get_harvest(self.h, None, None, None, C.byref(n)), "get_harvest")
+        F = np.zeros((n.value, 5), dtype=np.float32)
+        P = np.zeros(n.value, dtype=np.float32)
+        T = np.zeros(n.value, dtype=np.float32)
+        if n.value:
+            self._check(self.lib.gbdmrg_get_harvest(self.h, F.ctypes.data_as(_P), P.ctypes.data_as(_P),
+                                                    T.ctypes.data_as(_P), C.byref(n)), "get_harvest")
+        return F, P, T
+
+    def precond_counters(self):
+        a, b = C.c_int64(), C.c_int64()
+        self._check(self.lib.gbdmrg_precond_counters(self.h, C.byref(a), C.byref(b)), "precond_counters")
+        return dict(learned=a.value, fallbacks=b.value)
 
     def diag_noalloc(self, diag_ptr: int):
         """Diagonal of H_eff into a device buffer without device allocation."""

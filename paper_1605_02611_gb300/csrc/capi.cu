@@ -3,14 +3,22 @@
 #include <cstring>
 #include <exception>
 #include <memory>
+#include <string>
+#include <vector>
 
 #include "../../include/gbdmrg.h"
 #include "engine.hpp"
 #include "kernels_tc.hpp"
+#include "mlp.hpp"
 
 struct gbdmrg_ctx {
   gbdmrg::Context c;
   gbdmrg::SweepStats stats;
+};
+
+struct gbdmrg_mlp {
+  gbdmrg::Mlp m;
+  std::string err;
 };
 
 namespace {
@@ -65,6 +73,45 @@ void check_problem(const gbdmrg_problem* p) {
               std::fabs(v - E(c, d, a, b)) > tol)
             throw Error(ST_EINVAL, "eri not 8-fold symmetric");
         }
+}
+
+template <class F>
+gbdmrg_status mguard(gbdmrg_mlp* h, F&& f) {
+  try {
+    f();
+    if (h) h->err.clear();
+    return GBDMRG_OK;
+  } catch (const gbdmrg::Error& e) {
+    if (h) h->err = e.what();
+    return (gbdmrg_status)e.code;
+  } catch (const std::bad_alloc&) {
+    if (h) h->err = "host allocation failed";
+    return GBDMRG_ENOMEM;
+  } catch (const std::exception& e) {
+    if (h) h->err = e.what();
+    return GBDMRG_EINVAL;
+  } catch (...) {
+    if (h) h->err = "unknown error";
+    return GBDMRG_ECUDA;
+  }
+}
+
+// device copy of a caller array (host or device) on stream s
+template <class T>
+const T* to_device(const T* p, size_t n, int32_t on_device, gbdmrg::DArr<T>& tmp, cudaStream_t s) {
+  if (on_device) return p;
+  tmp.alloc(n, s);
+  gbdmrg::cuda_check(cudaMemcpyAsync(tmp.p, p, n * sizeof(T), cudaMemcpyHostToDevice, s), "h2d");
+  return tmp.p;
+}
+
+double host_norm(const double* dev, size_t n, cudaStream_t s) {
+  std::vector<double> h(n);
+  gbdmrg::cuda_check(cudaMemcpyAsync(h.data(), dev, n * sizeof(double), cudaMemcpyDeviceToHost, s), "d2h");
+  gbdmrg::cuda_check(cudaStreamSynchronize(s), "sync");
+  double r = 0;
+  for (double v : h) r += v * v;
+  return std::sqrt(r);
 }
 
 }  // namespace
@@ -178,12 +225,82 @@ gbdmrg_status gbdmrg_get_bond(gbdmrg_ctx* ctx, int32_t bond, int32_t* D, int32_t
 }
 
 gbdmrg_status gbdmrg_set_precision(gbdmrg_ctx* ctx, int32_t precision) {
-  if (!ctx || precision < 0 || precision > 2) return GBDMRG_EINVAL;
+  if (!ctx || precision < 0 || precision > 3) return GBDMRG_EINVAL;
   return guard(ctx, [&] {
     ctx->c.precision = precision;
     ctx->c.prepared = -1;
   });
 }
+
+gbdmrg_status gbdmrg_set_chunk_budget(gbdmrg_ctx* ctx, int32_t megabytes) {
+  if (!ctx || megabytes <= 0) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    ctx->c.chunk_budget_mb = megabytes;
+    ctx->c.prepared = -1;
+  });
+}
+
+gbdmrg_status gbdmrg_keep_host_plans(gbdmrg_ctx* ctx, int32_t keep) {
+  if (!ctx) return GBDMRG_EINVAL;
+  return guard(ctx, [&] { ctx->c.keep_host_plans = keep != 0; });
+}
+
+struct gbdmrg_batch {
+  gbdmrg::BatchPlan* b = nullptr;
+  std::string err;
+  ~gbdmrg_batch() {
+    if (b) gbdmrg::batch_free(b);
+  }
+};
+
+gbdmrg_status gbdmrg_batch_create(int32_t n, gbdmrg_ctx* const* ctxs, gbdmrg_batch** out) {
+  if (!out || n <= 0 || !ctxs) return GBDMRG_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i)
+    if (!ctxs[i]) return GBDMRG_EINVAL;
+  try {
+    std::vector<gbdmrg::Context*> v;
+    for (int i = 0; i < n; ++i) v.push_back(&ctxs[i]->c);
+    auto* bt = new gbdmrg_batch();
+    try {
+      bt->b = gbdmrg::batch_create(v);
+    } catch (...) {
+      delete bt;
+      throw;
+    }
+    *out = bt;
+    return GBDMRG_OK;
+  } catch (const gbdmrg::Error& e) {
+    ctxs[0]->c.last_error = e.what();
+    return (gbdmrg_status)e.code;
+  } catch (const std::bad_alloc&) {
+    return GBDMRG_ENOMEM;
+  } catch (...) {
+    return GBDMRG_ECUDA;
+  }
+}
+
+gbdmrg_status gbdmrg_batch_sigma(gbdmrg_batch* b, const double* const* psi_dev, double* const* sigma_dev,
+                                 int32_t use_graph, double* ms, double* flops) {
+  if (!b || !b->b || !psi_dev || !sigma_dev) return GBDMRG_EINVAL;
+  try {
+    float t = gbdmrg::batch_sigma(*b->b, psi_dev, sigma_dev, use_graph != 0);
+    if (ms) *ms = t;
+    if (flops) *flops = gbdmrg::batch_flops(b->b);
+    b->err.clear();
+    return GBDMRG_OK;
+  } catch (const gbdmrg::Error& e) {
+    b->err = e.what();
+    return (gbdmrg_status)e.code;
+  } catch (...) {
+    b->err = "unknown error";
+    return GBDMRG_ECUDA;
+  }
+}
+
+const char* gbdmrg_batch_last_error(const gbdmrg_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+void gbdmrg_batch_destroy(gbdmrg_batch* b) { delete b; }
 
 gbdmrg_status gbdmrg_plan(gbdmrg_ctx* ctx, int32_t k) {
   if (!ctx) return GBDMRG_EINVAL;
@@ -434,7 +551,7 @@ gbdmrg_status gbdmrg_run(gbdmrg_ctx* ctx, const gbdmrg_schedule* s, double* ener
       if (s->M[i] <= 0) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "M must be positive");
       if (!(s->dav_tol[i] > 0)) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "dav_tol must be positive");
     }
-    if (s->precision < 0 || s->precision > 2) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "precision must be 0, 1 or 2");
+    if (s->precision < 0 || s->precision > 3) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "precision must be 0 to 3");
     ctx->c.precision = s->precision;
     ctx->stats = gbdmrg::SweepStats();
     gbdmrg::run_sweeps(ctx->c, s->nsweeps, s->M, s->dav_tol, s->dav_max_iter > 0 ? s->dav_max_iter : 200,
@@ -457,6 +574,219 @@ gbdmrg_status gbdmrg_run_stats(gbdmrg_ctx* ctx, double* seconds, double* sigma_f
       if (sigma_seconds) sigma_seconds[i] = st.sigma_seconds[i];
       if (iters) iters[i] = st.davidson_iters[i];
     }
+  });
+}
+
+// ---------------------------------------------------------------- learned preconditioner
+
+int64_t gbdmrg_mlp_nparams(void) { return gbdmrg::MLP_NPARAMS; }
+
+gbdmrg_status gbdmrg_mlp_create(uint64_t seed, void* stream, gbdmrg_mlp** out) {
+  if (!out) return GBDMRG_EINVAL;
+  *out = nullptr;
+  auto* h = new (std::nothrow) gbdmrg_mlp();
+  if (!h) return GBDMRG_ENOMEM;
+  gbdmrg_status st = mguard(h, [&] { gbdmrg::mlp_init(h->m, seed, (cudaStream_t)stream); });
+  if (st != GBDMRG_OK) {
+    delete h;
+    return st;
+  }
+  *out = h;
+  return GBDMRG_OK;
+}
+
+void gbdmrg_mlp_destroy(gbdmrg_mlp* mlp) { delete mlp; }
+
+const char* gbdmrg_mlp_last_error(const gbdmrg_mlp* mlp) { return mlp ? mlp->err.c_str() : "null network"; }
+
+gbdmrg_status gbdmrg_mlp_set_params(gbdmrg_mlp* mlp, const float* params) {
+  if (!mlp || !params) return GBDMRG_EINVAL;
+  return mguard(mlp, [&] {
+    for (long i = 0; i < gbdmrg::MLP_NPARAMS; ++i)
+      if (!std::isfinite(params[i])) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "non-finite parameter");
+    gbdmrg::mlp_set_params(mlp->m, params);
+  });
+}
+
+gbdmrg_status gbdmrg_mlp_get_params(gbdmrg_mlp* mlp, float* params) {
+  if (!mlp || !params) return GBDMRG_EINVAL;
+  return mguard(mlp, [&] { gbdmrg::mlp_get_params(mlp->m, params); });
+}
+
+gbdmrg_status gbdmrg_mlp_forward(gbdmrg_mlp* mlp, const float* features, int64_t n, float* g, int32_t inference,
+                                 int32_t on_device) {
+  if (!mlp || n < 0 || (n > 0 && (!features || !g))) return GBDMRG_EINVAL;
+  return mguard(mlp, [&] {
+    if (n == 0) return;
+    cudaStream_t s = mlp->m.stream;
+    gbdmrg::DArr<float> tf, tg;
+    const float* F = to_device(features, (size_t)n * gbdmrg::MLP_F, on_device, tf, s);
+    float* G = g;
+    if (!on_device) {
+      tg.alloc(n, s);
+      G = tg.p;
+    }
+    gbdmrg::mlp_forward(mlp->m, F, n, G, inference != 0);
+    if (!on_device) gbdmrg::cuda_check(cudaMemcpyAsync(g, G, n * sizeof(float), cudaMemcpyDeviceToHost, s), "d2h");
+    gbdmrg::cuda_check(cudaStreamSynchronize(s), "sync");
+  });
+}
+
+gbdmrg_status gbdmrg_mlp_loss_grad(gbdmrg_mlp* mlp, const float* features, const float* P, const float* T, int64_t n,
+                                   int32_t on_device, float* grad, double* loss) {
+  if (!mlp || n <= 0 || !features || !P || !T) return GBDMRG_EINVAL;
+  return mguard(mlp, [&] {
+    cudaStream_t s = mlp->m.stream;
+    gbdmrg::DArr<float> tf, tp, tt;
+    const float* F = to_device(features, (size_t)n * gbdmrg::MLP_F, on_device, tf, s);
+    const float* Pd = to_device(P, n, on_device, tp, s);
+    const float* Td = to_device(T, n, on_device, tt, s);
+    double L = gbdmrg::mlp_loss_grad(mlp->m, F, Pd, Td, n);
+    if (loss) *loss = L;
+    if (grad) {
+      gbdmrg::cuda_check(
+          cudaMemcpyAsync(grad, mlp->m.grad.p, gbdmrg::MLP_NPARAMS * sizeof(float), cudaMemcpyDeviceToHost, s), "d2h");
+      gbdmrg::cuda_check(cudaStreamSynchronize(s), "sync");
+    }
+  });
+}
+
+gbdmrg_status gbdmrg_mlp_train(gbdmrg_mlp* mlp, const float* features, const float* P, const float* T, int64_t n,
+                               int32_t on_device, int32_t epochs, int32_t batch, float lr, uint64_t seed,
+                               double* loss_first, double* loss_last) {
+  if (!mlp || n <= 0 || !features || !P || !T || epochs <= 0 || batch <= 0 || !(lr > 0)) return GBDMRG_EINVAL;
+  return mguard(mlp, [&] {
+    cudaStream_t s = mlp->m.stream;
+    gbdmrg::DArr<float> tf, tp, tt;
+    const float* F = to_device(features, (size_t)n * gbdmrg::MLP_F, on_device, tf, s);
+    const float* Pd = to_device(P, n, on_device, tp, s);
+    const float* Td = to_device(T, n, on_device, tt, s);
+    gbdmrg::mlp_train(mlp->m, F, Pd, Td, n, epochs, batch, lr, seed, loss_first, loss_last);
+  });
+}
+
+gbdmrg_status gbdmrg_set_preconditioner(gbdmrg_ctx* ctx, gbdmrg_mlp* mlp) {
+  if (!ctx) return GBDMRG_EINVAL;
+  return guard(ctx, [&] { ctx->c.mlp = mlp ? &mlp->m : nullptr; });
+}
+
+gbdmrg_status gbdmrg_precondition(gbdmrg_ctx* ctx, const double* r, double theta, double* t, int32_t on_device) {
+  if (!ctx || !r || !t || !std::isfinite(theta)) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    auto& c = ctx->c;
+    if (c.prepared < 0) throw gbdmrg::Error(gbdmrg::ST_ESTATE, "call gbdmrg_prepare first");
+    const auto& P = c.plan.psi;
+    const size_t n = P.nnz;
+    gbdmrg::DArr<double> tr, tt, d;
+    const double* rd = to_device(r, n, on_device, tr, c.stream);
+    double* td = t;
+    if (!on_device) {
+      tt.alloc(n, c.stream);
+      td = tt.p;
+    }
+    d.alloc(n, c.stream);
+    gbdmrg::compute_diag(c, c.lt, c.rt, c.prepared, P, d.p);
+    const double rn = host_norm(rd, n, c.stream);
+    if (!(rn > 0) || !std::isfinite(rn)) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "zero or non-finite residual");
+    if (c.mlp) {
+      gbdmrg::MlpScratch sc;
+      gbdmrg::mlp_scratch_build(sc, c.mlp, P, c.stream);
+      gbdmrg::mlp_scratch_set_diag(sc, d.p, c.stream);
+      if (!gbdmrg::mlp_precondition(*c.mlp, sc, rd, d.p, theta, rn, td, c.stream))
+        throw gbdmrg::Error(gbdmrg::ST_ENOCONV, "learned preconditioner produced a non-finite value");
+    } else {
+      gbdmrg::launch_precond((long)n, rd, d.p, theta, 1e-8, td, c.stream);
+    }
+    if (!on_device)
+      gbdmrg::cuda_check(cudaMemcpyAsync(t, td, n * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "d2h");
+    gbdmrg::cuda_check(cudaStreamSynchronize(c.stream), "sync");
+  });
+}
+
+gbdmrg_status gbdmrg_make_pairs(gbdmrg_ctx* ctx, const double* x, const double* r, double theta, const double* psi,
+                                int64_t ns, uint64_t seed, int32_t on_device, float* features, float* P, float* T,
+                                int64_t* idx, int64_t* written) {
+  if (!ctx || !x || !r || !psi || ns < 0 || !features || !P || !T || !std::isfinite(theta)) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    auto& c = ctx->c;
+    if (c.prepared < 0) throw gbdmrg::Error(gbdmrg::ST_ESTATE, "call gbdmrg_prepare first");
+    const auto& Pl = c.plan.psi;
+    const size_t n = Pl.nnz;
+    gbdmrg::DArr<double> tx, tr, tp, d;
+    const double* xd = to_device(x, n, on_device, tx, c.stream);
+    const double* rd = to_device(r, n, on_device, tr, c.stream);
+    const double* pd = to_device(psi, n, on_device, tp, c.stream);
+    d.alloc(n, c.stream);
+    gbdmrg::compute_diag(c, c.lt, c.rt, c.prepared, Pl, d.p);
+    const double rn = host_norm(rd, n, c.stream);
+    if (!(rn > 0) || !std::isfinite(rn)) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "zero or non-finite residual");
+    gbdmrg::MlpScratch sc;
+    gbdmrg::mlp_scratch_build(sc, nullptr, Pl, c.stream);
+    gbdmrg::mlp_scratch_set_diag(sc, d.p, c.stream);
+    gbdmrg::DArr<float> fF, fP, fT;
+    gbdmrg::DArr<long> fi;
+    float *oF = features, *oP = P, *oT = T;
+    long* oi = (long*)idx;
+    if (!on_device) {
+      fF.alloc((size_t)ns * gbdmrg::MLP_F, c.stream);
+      fP.alloc(ns, c.stream);
+      fT.alloc(ns, c.stream);
+      fi.alloc(ns, c.stream);
+      oF = fF.p;
+      oP = fP.p;
+      oT = fT.p;
+      oi = fi.p;
+    }
+    long w = gbdmrg::mlp_make_pairs(sc, xd, rd, d.p, theta, rn, pd, ns, seed, oF, oP, oT, oi, 0.0, c.stream);
+    if (!on_device && w > 0) {
+      gbdmrg::cuda_check(cudaMemcpyAsync(features, oF, w * gbdmrg::MLP_F * sizeof(float), cudaMemcpyDeviceToHost,
+                                         c.stream), "d2h");
+      gbdmrg::cuda_check(cudaMemcpyAsync(P, oP, w * sizeof(float), cudaMemcpyDeviceToHost, c.stream), "d2h");
+      gbdmrg::cuda_check(cudaMemcpyAsync(T, oT, w * sizeof(float), cudaMemcpyDeviceToHost, c.stream), "d2h");
+      if (idx) gbdmrg::cuda_check(cudaMemcpyAsync(idx, oi, w * sizeof(long), cudaMemcpyDeviceToHost, c.stream), "d2h");
+    }
+    gbdmrg::cuda_check(cudaStreamSynchronize(c.stream), "sync");
+    if (written) *written = w;
+  });
+}
+
+gbdmrg_status gbdmrg_set_harvest(gbdmrg_ctx* ctx, int64_t capacity, int32_t per_iteration, uint64_t seed) {
+  if (!ctx || capacity < 0 || per_iteration < 0) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    auto& H = ctx->c.harvest;
+    H.cap = capacity;
+    H.count = 0;
+    H.per_iter = per_iteration;
+    H.seed = seed;
+    H.solves = 0;
+    H.F.alloc((size_t)capacity * gbdmrg::MLP_F, ctx->c.stream);
+    H.P.alloc(capacity, ctx->c.stream);
+    H.T.alloc(capacity, ctx->c.stream);
+    gbdmrg::cuda_check(cudaStreamSynchronize(ctx->c.stream), "sync");
+  });
+}
+
+gbdmrg_status gbdmrg_get_harvest(gbdmrg_ctx* ctx, float* features, float* P, float* T, int64_t* n) {
+  if (!ctx || !n) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    auto& H = ctx->c.harvest;
+    *n = H.count;
+    if (H.count == 0) return;
+    cudaStream_t s = ctx->c.stream;
+    if (features)
+      gbdmrg::cuda_check(cudaMemcpyAsync(features, H.F.p, H.count * gbdmrg::MLP_F * sizeof(float),
+                                         cudaMemcpyDeviceToHost, s), "d2h");
+    if (P) gbdmrg::cuda_check(cudaMemcpyAsync(P, H.P.p, H.count * sizeof(float), cudaMemcpyDeviceToHost, s), "d2h");
+    if (T) gbdmrg::cuda_check(cudaMemcpyAsync(T, H.T.p, H.count * sizeof(float), cudaMemcpyDeviceToHost, s), "d2h");
+    gbdmrg::cuda_check(cudaStreamSynchronize(s), "sync");
+  });
+}
+
+gbdmrg_status gbdmrg_precond_counters(gbdmrg_ctx* ctx, int64_t* learned, int64_t* fallbacks) {
+  if (!ctx) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    if (learned) *learned = ctx->c.mlp_applied;
+    if (fallbacks) *fallbacks = ctx->c.mlp_fallbacks;
   });
 }
 

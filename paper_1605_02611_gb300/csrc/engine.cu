@@ -10,6 +10,7 @@
 #include <numeric>
 
 #include "engine.hpp"
+#include "mlp.hpp"
 
 namespace gbdmrg {
 
@@ -189,6 +190,11 @@ Context::~Context() {
   lt.combo.release();
   rt.combo.release();
   plan = SigmaPlan();
+  // device arrays are freed on the context stream: release them before it goes
+  mlp_s.reset();
+  harvest.F.release();
+  harvest.P.release();
+  harvest.T.release();
   if (stream) cudaStreamSynchronize(stream);
   if (solver) cusolverDnDestroy(solver);
   if (ev0) cudaEventDestroy(ev0);
@@ -589,7 +595,7 @@ void build_sigma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) 
   plan.in.alloc(P.nnz, c.stream);
   plan.out.alloc(P.nnz, c.stream);
   if (c.precision > 0) {
-    build_mixed_plan(c, lt, rt, k, plan, c.precision == 1 ? 1 : 3);
+    build_mixed_plan(c, lt, rt, k, plan, c.precision == 1 ? 1 : c.precision == 2 ? 3 : 2);
     return;
   }
   const int nL = Lb.nsec();
@@ -910,6 +916,17 @@ double davidson(Context& c, SigmaPlan& plan, const double* diag, double* psi, co
   std::vector<double> w, Y, sub;
   double best_rn = 1e300;
   int since_best = 0;
+  // learned preconditioner and training-pair collection
+  const bool use_mlp = c.mlp != nullptr;
+  const bool harvest = c.harvest.per_iter > 0 && c.harvest.count < c.harvest.cap;
+  if (use_mlp || harvest) {
+    c.mlp_s.reset(new MlpScratch());
+    mlp_scratch_build(*c.mlp_s, use_mlp ? c.mlp : nullptr, plan.psi, c.stream);
+    mlp_scratch_set_diag(*c.mlp_s, diag, c.stream);
+  }
+  double prev_rn = 1e300;
+  std::vector<DArr<double>> sv_x, sv_r;  // saved Ritz vectors / residuals
+  std::vector<double> sv_theta, sv_rn;
   for (; it < o.max_iter; ++it) {
     sub.assign((size_t)m * m, 0.0);
     for (int i = 0; i < m; ++i)
@@ -924,8 +941,20 @@ double davidson(Context& c, SigmaPlan& plan, const double* diag, double* psi, co
     cuda_check(cudaMemcpyAsync(r.p, hx.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "d2d");
     launch_axpby(n, -theta, x.p, 1.0, r.p, c.stream);
     double rn = std::sqrt(dh.dots(c, r.p, 0, 1, r.p, n)[0]);
-    if (!std::isfinite(rn)) throw Error(ST_ENOCONV, "Davidson: non-finite residual");
+    if (!std::isfinite(rn))
+      throw Error(ST_ENOCONV, "Davidson: non-finite residual (iteration " + std::to_string(it) + ", subspace " +
+                                  std::to_string(m) + ", theta " + std::to_string(theta) + ")");
     if (rn <= o.tol) break;
+    if (harvest && sv_x.size() < 7 && (it == 0 || it == 1 || it == 2 || it == 4 || it == 7 || it == 11 || it == 16)) {
+      sv_x.emplace_back();
+      sv_r.emplace_back();
+      sv_x.back().alloc(n, c.stream);
+      sv_r.back().alloc(n, c.stream);
+      cuda_check(cudaMemcpyAsync(sv_x.back().p, x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "d2d");
+      cuda_check(cudaMemcpyAsync(sv_r.back().p, r.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "d2d");
+      sv_theta.push_back(theta);
+      sv_rn.push_back(rn);
+    }
     if (o.stagnation > 0) {
       // only near the operator's rounding floor (tensor-core sigma: ~1e-5 of |theta|)
       if (rn < 0.9 * best_rn) {
@@ -935,7 +964,17 @@ double davidson(Context& c, SigmaPlan& plan, const double* diag, double* psi, co
         break;
       }
     }
-    launch_precond(n, r.p, diag, theta, 1e-8, t.p, c.stream);
+    bool learned = false;
+    if (use_mlp && rn < prev_rn) learned = mlp_precondition(*c.mlp, *c.mlp_s, r.p, diag, theta, rn, t.p, c.stream);
+    if (learned) {
+      ++c.mlp_applied;
+    } else {
+      // diagonal correction; also the fallback when the residual did not decrease
+      // or the network produced a non-finite value
+      if (use_mlp) ++c.mlp_fallbacks;
+      launch_precond(n, r.p, diag, theta, 1e-8, t.p, c.stream);
+    }
+    prev_rn = rn;
     if (m == ms) {  // restart from the Ritz vector
       cuda_check(cudaMemcpyAsync(V.p, x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "d2d");
       cuda_check(cudaMemcpyAsync(S.p, hx.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "d2d");
@@ -964,6 +1003,17 @@ double davidson(Context& c, SigmaPlan& plan, const double* diag, double* psi, co
   double xn = std::sqrt(dh.dots(c, x.p, 0, 1, x.p, n)[0]);
   launch_axpby(n, 1.0 / xn, x.p, 0.0, psi, c.stream);
   cuda_check(cudaStreamSynchronize(c.stream), "sync");
+  if (harvest) {
+    Harvest& H = c.harvest;
+    for (size_t j = 0; j < sv_x.size() && H.count < H.cap; ++j) {
+      const long ns = std::min<long>(H.per_iter, H.cap - H.count);
+      const uint64_t key = H.seed * 0x100000001B3ULL + (uint64_t)H.solves * 64 + j;
+      // iterates with |x . psi| < 0.5 are skipped: their unit-weight correction is ill-defined
+      H.count += mlp_make_pairs(*c.mlp_s, sv_x[j].p, sv_r[j].p, diag, sv_theta[j], sv_rn[j], psi, ns, key,
+                                H.F.p + H.count * 5, H.P.p + H.count, H.T.p + H.count, nullptr, 0.5, c.stream);
+    }
+    ++H.solves;
+  }
   if (iters) *iters = it;
   return theta;
 }
@@ -1399,7 +1449,14 @@ void run_sweeps(Context& c, int nsweeps, const int* M, const double* tol, int ma
     auto step = [&](int k, int dir) {
       int it = 0;
       double dw = 0;
-      e = two_site_step(c, k, dir, M[s], o, true, &it, &dw);
+      try {
+        e = two_site_step(c, k, dir, M[s], o, true, &it, &dw);
+      } catch (const Error& err) {
+        throw Error(err.code, std::string(err.what()) + " (sweep " + std::to_string(s) + ", sites " +
+                                  std::to_string(k) + "," + std::to_string(k + 1) + ", direction " +
+                                  std::to_string(dir) + ", M " + std::to_string(M[s]) + ", precision " +
+                                  std::to_string(c.precision) + ")");
+      }
       iters += it;
       dmax = std::max(dmax, dw);
     };

@@ -5,6 +5,7 @@
 #include <cusolverDn.h>
 
 #include <array>
+#include <cstdint>
 #include <memory>
 #include <stdexcept>
 #include <string>
@@ -178,6 +179,20 @@ struct SigmaPlan {
 };
 
 struct Context;
+struct Mlp;
+struct MlpScratch;
+struct MlpScratchDeleter {
+  void operator()(MlpScratch* p) const;
+};
+
+// training pairs collected by Davidson for the learned preconditioner
+struct Harvest {
+  long cap = 0, count = 0;  // capacity and pairs collected
+  int per_iter = 0;         // pairs drawn from each saved Davidson iterate
+  uint64_t seed = 0;
+  long solves = 0;
+  DArr<float> F, P, T;
+};
 
 struct SweepStats {
   std::vector<double> energy, discarded, seconds, sigma_flops, sigma_seconds;
@@ -221,8 +236,16 @@ struct Context {
   double phase_s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int chunk_budget_mb = 2048;
   // 0: FP64 grouped GEMMs; 1: tensor cores, one BF16 pass; 2: tensor cores,
-  // three BF16 slices (six products, about FP32 accuracy)
+  // three BF16 slices (six products, about FP32 accuracy); 3: two BF16 slices
+  // (three products)
   int precision = 0;
+  // keep host copies of tensor-core work lists (needed to fuse problems into batches)
+  bool keep_host_plans = false;
+  // learned Davidson preconditioner (not owned; null: diagonal) and its scratch
+  Mlp* mlp = nullptr;
+  std::unique_ptr<MlpScratch, MlpScratchDeleter> mlp_s;
+  Harvest harvest;
+  long mlp_applied = 0, mlp_fallbacks = 0;
 
   ~Context();
 };
@@ -243,6 +266,13 @@ void run_sigma(Context& c, SigmaPlan& plan, const double* x, double* y);
 void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, int nslices);
 void run_mixed_sigma(Context& c, SigmaPlan& plan, const double* x, double* y);
 int mixed_error(Context& c, SigmaPlan& plan);
+
+// batched tensor-core sigma over several prepared contexts (engine_mixed.cu)
+struct BatchPlan;
+BatchPlan* batch_create(const std::vector<Context*>& ctxs);
+void batch_free(BatchPlan* b);
+double batch_flops(const BatchPlan* b);
+float batch_sigma(BatchPlan& b, const double* const* psi, double* const* sigma, bool use_graph);
 void compute_diag(Context& c, Tilde& lt, Tilde& rt, int k, const PsiLayout& P, double* diag);
 
 void prepare_two_site(Context& c, int k);

@@ -70,8 +70,34 @@ void launch_unconv(const UnconvJob* jobs, int njobs, long maxel, cudaStream_t s)
     int no = std::min(65535, njobs - o0);
     long g = std::min<long>(std::max<long>(1, (maxel + 255) / 256), 64);
     unconv_kernel<<<dim3((unsigned)g, no), 256, 0, s>>>(jobs + o0);
+    count_launches(1);
   }
   cuda_check(cudaGetLastError(), "unconv launch");
+}
+
+// zero n elements at p + s * stride for every slice s < nsl
+struct ZeroJob {
+  __nv_bfloat16* p;
+  long n, stride;
+  int nsl;
+};
+
+__global__ void zero_kernel(const ZeroJob* __restrict__ jobs) {
+  const ZeroJob jb = jobs[blockIdx.y];
+  const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
+  for (int sl = 0; sl < jb.nsl; ++sl)
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < jb.n; e += (long)gridDim.x * blockDim.x)
+      jb.p[sl * jb.stride + e] = z;
+}
+
+void launch_zero(const ZeroJob* jobs, int njobs, long maxel, cudaStream_t s) {
+  for (int o0 = 0; o0 < njobs; o0 += 65535) {
+    int no = std::min(65535, njobs - o0);
+    long g = std::min<long>(std::max<long>(1, (maxel + 255) / 256), 64);
+    zero_kernel<<<dim3((unsigned)g, no), 256, 0, s>>>(jobs + o0);
+    count_launches(1);
+  }
+  cuda_check(cudaGetLastError(), "zero launch");
 }
 
 void launch_conv(const DArr<ConvJob>& jobs, int njobs, long maxel, cudaStream_t s) {
@@ -79,6 +105,7 @@ void launch_conv(const DArr<ConvJob>& jobs, int njobs, long maxel, cudaStream_t 
     int no = std::min(65535, njobs - o0);
     long g = std::min<long>(std::max<long>(1, (maxel + 255) / 256), 64);
     conv_kernel<<<dim3((unsigned)g, no), 256, 0, s>>>(jobs.p + o0);
+    count_launches(1);
   }
   cuda_check(cudaGetLastError(), "conv launch");
 }
@@ -114,7 +141,21 @@ struct TcPlan {
   DArr<TcTask> tasks;
   DArr<TcTerm> terms;
   int ntiles = 0;
+  // host copies, kept when the plan may be fused into a batched launch
+  std::vector<TcTile> htiles;
+  std::vector<TcTask> htasks;
+  std::vector<TcTerm> hterms;
+  // regions of the shared X buffer to clear before this launch (stage 1 of a
+  // multi-chunk plan: blocks of X that no term of this chunk writes)
+  DArr<ZeroJob> zeros;
+  std::vector<ZeroJob> hzeros;
+  int nzeros = 0;
+  long zmax = 0;
 };
+
+void run_zeros(const TcPlan& tp, cudaStream_t s) {
+  if (tp.nzeros) launch_zero(tp.zeros.p, tp.nzeros, tp.zmax, s);
+}
 
 struct MixedPlan {
   int nsl = 1;
@@ -122,6 +163,8 @@ struct MixedPlan {
   DArr<float> sig_f;
   DArr<ConvJob> psi_jobs;
   DArr<UnconvJob> sig_jobs;
+  std::vector<ConvJob> h_psi_jobs;
+  std::vector<UnconvJob> h_sig_jobs;
   int n_psi_jobs = 0, n_sig_jobs = 0;
   long psi_maxel = 0, sig_maxel = 0;
   long sig_total = 0;
@@ -286,6 +329,8 @@ void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, 
     mx->n_psi_jobs = (int)pj.size();
     mx->sig_jobs.upload(sj, c.stream);
     mx->n_sig_jobs = (int)sj.size();
+    mx->h_psi_jobs = pj;
+    mx->h_sig_jobs = sj;
   }
   mx->err.alloc(1, c.stream);
   cuda_check(cudaMemsetAsync(mx->err.p, 0, sizeof(int), c.stream), "memset");
@@ -313,8 +358,10 @@ void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, 
   cuda_check(cudaMemsetAsync(mx->X_b.p, 0, mx->X_b.n * sizeof(__nv_bfloat16), c.stream), "memset");
   const long xstride = (long)maxchunk;
   const __nv_bfloat16* mir = mx->mirror.p;
+  const bool multi = chunks.size() > 1;
   for (auto ch : chunks) {
     TcBuilder g1, g2;
+    std::vector<ZeroJob> zj;
     size_t xoff = 0;
     // X^T offsets of this chunk: [beta - b0][g'] (-1 if absent or never written)
     std::vector<std::vector<long>> xpos(ch.second - ch.first, std::vector<long>(ng, -1));
@@ -325,6 +372,7 @@ void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, 
         if (g < 0) continue;
         const long base = (long)xoff;
         bool any = false;
+        std::vector<ZeroJob> empty_cb;  // column blocks of X^T without a term
         // stage 1: X_beta[rows of g', (n2, qr) block of g] = sum_{n2'} Psi_g'[:, (n2', qr')] Rt^{n2 n2'}[qr, qr']^T,
         // stored transposed into X^T (rows (n2, qr) of g, columns = rows of g')
         for (const auto& cb : gcol[g]) {
@@ -353,11 +401,17 @@ void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, 
             g1.term(mx->psi_b.p + goff[gp] + cpp[1], ptot, gC[gp], mir + mr.off + (*mr.boff)[bl], mr.stride, pad8(kk),
                     kk, mr.neg, nsl);
           }
-          if (g1.end()) any = true;
+          if (g1.end())
+            any = true;
+          else
+            empty_cb.push_back({mx->X_b.p + base + (long)cb[2] * gR[gp], (long)Rb.dim[qr] * gR[gp], xstride, nsl});
         }
         if (any) {
           xp[gp] = base;
           xoff += (size_t)gC[g] * gR[gp];
+          // with several chunks the X buffer is shared, so rows that stay exactly zero
+          // here may hold another chunk's values: clear them (one chunk: zero from the start)
+          if (multi) zj.insert(zj.end(), empty_cb.begin(), empty_cb.end());
         }
       }
     }
@@ -434,17 +488,30 @@ void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, 
                        [&](const TcTile& a, const TcTile& b) { return w[a.task] > w[b.task]; });
     };
     order(g2);
+    auto keep = [&](TcPlan& tp, TcBuilder& g) {
+      tp.tiles.upload(g.tiles, c.stream);
+      tp.tasks.upload(g.tasks, c.stream);
+      tp.terms.upload(g.terms, c.stream);
+      tp.ntiles = (int)g.tiles.size();
+      cuda_check(cudaStreamSynchronize(c.stream), "sync");
+      if (c.keep_host_plans) {
+        tp.htiles.swap(g.tiles);
+        tp.htasks.swap(g.tasks);
+        tp.hterms.swap(g.terms);
+      }
+    };
     mx->stage1.emplace_back();
-    mx->stage1.back().tiles.upload(g1.tiles, c.stream);
-    mx->stage1.back().tasks.upload(g1.tasks, c.stream);
-    mx->stage1.back().terms.upload(g1.terms, c.stream);
-    mx->stage1.back().ntiles = (int)g1.tiles.size();
+    keep(mx->stage1.back(), g1);
+    {
+      TcPlan& tp = mx->stage1.back();
+      tp.nzeros = (int)zj.size();
+      for (const ZeroJob& z : zj) tp.zmax = std::max(tp.zmax, z.n);
+      tp.zeros.upload(zj, c.stream);
+      tp.hzeros = zj;
+      cuda_check(cudaStreamSynchronize(c.stream), "sync");
+    }
     mx->stage2.emplace_back();
-    mx->stage2.back().tiles.upload(g2.tiles, c.stream);
-    mx->stage2.back().tasks.upload(g2.tasks, c.stream);
-    mx->stage2.back().terms.upload(g2.terms, c.stream);
-    mx->stage2.back().ntiles = (int)g2.tiles.size();
-    cuda_check(cudaStreamSynchronize(c.stream), "sync");
+    keep(mx->stage2.back(), g2);
   }
   plan.flops = count_sigma_flops(c.mpo, k, Lb, Rb);
 }
@@ -458,6 +525,7 @@ void run_mixed_sigma(Context& c, SigmaPlan& plan, const double* x, double* y) {
   for (size_t i = 0; i < mx.stage1.size(); ++i) {
     auto& s1 = mx.stage1[i];
     auto& s2 = mx.stage2[i];
+    run_zeros(s1, c.stream);
     cuda_check(launch_gemm_bf16_tc(s1.tiles.p, s1.ntiles, s1.tasks.p, s1.terms.p, mx.err.p, c.stream), "tc stage 1");
     cuda_check(launch_gemm_bf16_tc(s2.tiles.p, s2.ntiles, s2.tasks.p, s2.terms.p, mx.err.p, c.stream), "tc stage 2");
   }
@@ -470,6 +538,186 @@ int mixed_error(Context& c, SigmaPlan& plan) {
   cuda_check(cudaMemcpyAsync(&h, plan.mx->err.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h");
   cuda_check(cudaStreamSynchronize(c.stream), "sync");
   return h;
+}
+
+// ---------------------------------------------------------------- batched sigma
+
+// Several independent two-site problems (each prepared in tensor-core precision
+// on the same device) fused into one launch per stage and chunk: the tile, task
+// and term lists are concatenated, so one persistent kernel walks the tiles of
+// every problem.  Optionally the whole sequence (conversions, stage launches,
+// gathers) is captured once in a CUDA graph and replayed.
+struct BatchPlan {
+  std::vector<Context*> ctx;
+  cudaStream_t stream = nullptr;
+  std::vector<TcPlan> stage1, stage2;
+  DArr<ConvJob> conv;
+  DArr<UnconvJob> unconv;
+  int nconv = 0, nunconv = 0;
+  long conv_maxel = 0, unconv_maxel = 0;
+  DArr<int> err;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long graph_launches = 0, graph_tc_launches = 0;  // kernels in one replay of the graph
+  double flops = 0;
+  ~BatchPlan() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+};
+
+static void concat_into(TcPlan& out, const std::vector<const TcPlan*>& parts, cudaStream_t s) {
+  std::vector<TcTile> ti;
+  std::vector<TcTask> ta;
+  std::vector<TcTerm> te;
+  std::vector<ZeroJob> zj;
+  for (const TcPlan* p : parts) {
+    if (p->ntiles && p->htiles.empty()) throw Error(ST_ESTATE, "batched sigma: plan was built without host copies");
+    const int toff = (int)ta.size(), eoff = (int)te.size();
+    for (TcTask t : p->htasks) {
+      t.t0 += eoff;
+      t.t1 += eoff;
+      ta.push_back(t);
+    }
+    te.insert(te.end(), p->hterms.begin(), p->hterms.end());
+    for (TcTile x : p->htiles) {
+      x.task += toff;
+      ti.push_back(x);
+    }
+    zj.insert(zj.end(), p->hzeros.begin(), p->hzeros.end());
+    out.zmax = std::max(out.zmax, p->zmax);
+  }
+  out.tiles.upload(ti, s);
+  out.tasks.upload(ta, s);
+  out.terms.upload(te, s);
+  out.ntiles = (int)ti.size();
+  out.nzeros = (int)zj.size();
+  out.zeros.upload(zj, s);
+  out.hzeros = zj;
+  cuda_check(cudaStreamSynchronize(s), "sync");
+}
+
+BatchPlan* batch_create(const std::vector<Context*>& ctxs) {
+  auto* b = new BatchPlan();
+  b->ctx = ctxs;
+  b->stream = ctxs[0]->stream;
+  size_t nch = 0;
+  std::vector<ConvJob> cj;
+  std::vector<UnconvJob> uj;
+  for (Context* c : ctxs) {
+    if (c->prepared < 0 || !c->plan.mx) {
+      delete b;
+      throw Error(ST_ESTATE, "batched sigma: every context must be prepared in a tensor-core precision");
+    }
+    MixedPlan& mx = *c->plan.mx;
+    nch = std::max(nch, mx.stage1.size());
+    cj.insert(cj.end(), mx.h_psi_jobs.begin(), mx.h_psi_jobs.end());
+    uj.insert(uj.end(), mx.h_sig_jobs.begin(), mx.h_sig_jobs.end());
+    b->conv_maxel = std::max(b->conv_maxel, mx.psi_maxel);
+    b->unconv_maxel = std::max(b->unconv_maxel, mx.sig_maxel);
+    b->flops += c->plan.flops;
+  }
+  try {
+    for (size_t ch = 0; ch < nch; ++ch) {
+      std::vector<const TcPlan*> p1, p2;
+      for (Context* c : ctxs) {
+        MixedPlan& mx = *c->plan.mx;
+        if (ch < mx.stage1.size()) {
+          p1.push_back(&mx.stage1[ch]);
+          p2.push_back(&mx.stage2[ch]);
+        }
+      }
+      b->stage1.emplace_back();
+      concat_into(b->stage1.back(), p1, b->stream);
+      b->stage2.emplace_back();
+      concat_into(b->stage2.back(), p2, b->stream);
+    }
+    b->conv.upload(cj, b->stream);
+    b->nconv = (int)cj.size();
+    b->unconv.upload(uj, b->stream);
+    b->nunconv = (int)uj.size();
+    b->err.alloc(1, b->stream);
+    cuda_check(cudaMemsetAsync(b->err.p, 0, sizeof(int), b->stream), "memset");
+    cuda_check(cudaStreamSynchronize(b->stream), "sync");
+  } catch (...) {
+    delete b;
+    throw;
+  }
+  return b;
+}
+
+void batch_free(BatchPlan* b) {
+  if (b && b->stream) cudaStreamSynchronize(b->stream);
+  delete b;
+}
+double batch_flops(const BatchPlan* b) { return b->flops; }
+
+// the device work of one batched sigma (plan.in -> plan.out of every problem)
+static void batch_enqueue(BatchPlan& b) {
+  cudaStream_t s = b.stream;
+  for (Context* c : b.ctx) {
+    MixedPlan& mx = *c->plan.mx;
+    cuda_check(cudaMemsetAsync(mx.sig_f.p, 0, mx.sig_total * sizeof(float), s), "memset");
+  }
+  if (b.nconv) launch_conv(b.conv, b.nconv, b.conv_maxel, s);
+  for (size_t i = 0; i < b.stage1.size(); ++i) {
+    run_zeros(b.stage1[i], s);
+    cuda_check(launch_gemm_bf16_tc(b.stage1[i].tiles.p, b.stage1[i].ntiles, b.stage1[i].tasks.p,
+                                   b.stage1[i].terms.p, b.err.p, s),
+               "tc stage 1");
+    cuda_check(launch_gemm_bf16_tc(b.stage2[i].tiles.p, b.stage2[i].ntiles, b.stage2[i].tasks.p,
+                                   b.stage2[i].terms.p, b.err.p, s),
+               "tc stage 2");
+  }
+  if (b.nunconv) launch_unconv(b.unconv.p, b.nunconv, b.unconv_maxel, s);
+}
+
+float batch_sigma(BatchPlan& b, const double* const* psi, double* const* sigma, bool use_graph) {
+  cudaStream_t s = b.stream;
+  for (size_t p = 0; p < b.ctx.size(); ++p) {
+    SigmaPlan& pl = b.ctx[p]->plan;
+    cuda_check(cudaMemcpyAsync(pl.in.p, psi[p], pl.psi.nnz * sizeof(double), cudaMemcpyDeviceToDevice, s), "d2d");
+  }
+  cudaEvent_t e0, e1;
+  cuda_check(cudaEventCreate(&e0), "event");
+  cuda_check(cudaEventCreate(&e1), "event");
+  cuda_check(cudaEventRecord(e0, s), "record");
+  if (use_graph && b.exec) {
+    cuda_check(cudaGraphLaunch(b.exec, s), "graph launch");
+    count_launches(b.graph_launches);
+    count_tc_launches(b.graph_tc_launches);
+  } else {
+    batch_enqueue(b);
+  }
+  cuda_check(cudaEventRecord(e1, s), "record");
+  if (use_graph && !b.exec) {
+    // captured after one eager pass (which set up every launch attribute); the
+    // captured work does not run now, later calls replay it
+    const long l0 = launch_count(), t0 = tc_launch_count();
+    cuda_check(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "begin capture");
+    batch_enqueue(b);
+    cuda_check(cudaStreamEndCapture(s, &b.graph), "end capture");
+    // captured launches run only when the graph is replayed: count them there
+    b.graph_launches = launch_count() - l0;
+    b.graph_tc_launches = tc_launch_count() - t0;
+    count_launches(-b.graph_launches);
+    count_tc_launches(-b.graph_tc_launches);
+    cuda_check(cudaGraphInstantiate(&b.exec, b.graph, 0), "graph instantiate");
+  }
+  for (size_t p = 0; p < b.ctx.size(); ++p) {
+    SigmaPlan& pl = b.ctx[p]->plan;
+    cuda_check(cudaMemcpyAsync(sigma[p], pl.out.p, pl.psi.nnz * sizeof(double), cudaMemcpyDeviceToDevice, s), "d2d");
+  }
+  cuda_check(cudaEventSynchronize(e1), "sync");
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int h = 0;
+  cuda_check(cudaMemcpy(&h, b.err.p, sizeof(int), cudaMemcpyDeviceToHost), "d2h");
+  if (h) throw Error(ST_ETIMEOUT, "tensor-core GEMM: a bounded wait ran out");
+  cuda_check(cudaStreamSynchronize(s), "sync");
+  return ms;
 }
 
 }  // namespace gbdmrg

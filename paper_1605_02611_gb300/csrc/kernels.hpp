@@ -51,6 +51,8 @@ struct CopyJob {
 
 // number of kernel launches issued by this library (all launch wrappers)
 long launch_count();
+// adds kernel launches made outside this file to the count
+void count_launches(long n);
 
 void launch_gemm(const GemmTile* d_tiles, int ntiles, const GemmTask* d_tasks,
                  const GemmTerm* d_terms, cudaStream_t s);

@@ -112,14 +112,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile
 __device__ __forceinline__ int round16(int x) { return (x + 15) & ~15; }
 
 // `nrows` rows of a 64-K tile (rows r0.., k0..) of a row-major bf16 matrix with
-// `rows` valid rows and leading dimension ld; zero fill outside
-__device__ __forceinline__ void load_tile(uint32_t sbase, const __nv_bfloat16* M, int ld, int rows, int r0, int k0,
-                                          int nrows, int ptid) {
+// `rows` valid rows, leading dimension ld and contraction length k; 16-byte
+// chunks that start at or beyond k (or ld) are zero-filled without a read, so
+// nothing past the block's own padded columns is touched
+__device__ __forceinline__ void load_tile(uint32_t sbase, const __nv_bfloat16* M, int ld, int k, int rows, int r0,
+                                          int k0, int nrows, int ptid) {
   const int nchunks = nrows * 8;
+  const int kend = k < ld ? k : ld;
   for (int e = ptid; e < nchunks; e += TC_PRODUCERS) {
     const int r = e >> 3, c = e & 7;
     const int gr = r0 + r, gk = k0 + 8 * c;
-    const bool ok = gr < rows && gk < ld;
+    const bool ok = gr < rows && gk < kend;
     const __nv_bfloat16* src = ok ? M + (long)gr * ld + gk : M;
     cp_async16(sbase + r * 128 + ((c ^ (r & 7)) << 4), src, ok ? 16 : 0);
   }
@@ -185,8 +188,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
               break;
             }
             const uint32_t sa = base + s * TC_STAGE_BYTES;
-            load_tile(sa, tm.A + PAIR_I[p] * tm.sA, tm.lda, tk.m, tl.r0, k0, TC_M, ptid);
-            load_tile(sa + TC_TILE_BYTES, tm.B + PAIR_J[p] * tm.sB, tm.ldb, tk.n, tl.c0, k0, nt, ptid);
+            load_tile(sa, tm.A + PAIR_I[p] * tm.sA, tm.lda, tm.k, tk.m, tl.r0, k0, TC_M, ptid);
+            load_tile(sa + TC_TILE_BYTES, tm.B + PAIR_J[p] * tm.sB, tm.ldb, tm.k, tk.n, tl.c0, k0, nt, ptid);
             // the full barrier completes when every producer's copies of this stage
             // have landed (asynchronous arrivals) and the parameters are written
             asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(&full_b[s]))
@@ -322,19 +325,21 @@ std::atomic<long> g_tc_launches{0};
 }  // namespace
 
 long tc_launch_count() { return g_tc_launches.load(); }
+void count_tc_launches(long n) { g_tc_launches += n; }
 
 cudaError_t launch_gemm_bf16_tc(const TcTile* d_tiles, int ntiles, const TcTask* d_tasks, const TcTerm* d_terms,
                                 int* d_err, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
-  static int nsm = 0;
-  if (!nsm) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-    if (e != cudaSuccess) return e;
-    int dev = 0;
+  // one-time set-up, thread-safe (function-local static)
+  static const int nsm = [] {
+    if (cudaFuncSetAttribute(gemm_bf16_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) != cudaSuccess)
+      return -1;
+    int dev = 0, n = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (nsm <= 0) nsm = 148;
-  }
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 148;
+  }();
+  if (nsm < 0) return cudaErrorInvalidValue;
   // persistent: two resident CTAs per SM (97 KB shared memory, 256 TMEM columns each)
   const int grid = ntiles < 2 * nsm ? ntiles : 2 * nsm;
   ++g_tc_launches;

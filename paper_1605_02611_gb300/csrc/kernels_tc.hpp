@@ -6,7 +6,10 @@
 namespace gbdmrg {
 
 // C[m x n] (+)= sum_t (-1)^{neg_t} A_t[m x k_t] B_t[n x k_t]^T; A, B row-major bf16 with
-// leading dimensions (elements) multiples of 8, 16-byte aligned, zero padding up to ld.
+// leading dimensions (elements) multiples of 8, 16-byte aligned.  Columns are read
+// in 16-byte chunks up to the first multiple of 8 at or above k_t (never beyond
+// ld); over the columns between k_t and that multiple one operand must be zero
+// and the other finite.
 // With nsl > 1 the operands are nsl BF16 slices (x = s_0 + s_1 + ...) stored sA / sB
 // elements apart, and the term contributes sum_{i + j < nsl} A_i B_j^T.
 struct TcTerm {
@@ -34,5 +37,6 @@ constexpr int TC_TILE_M = 128, TC_TILE_N = 128;
 cudaError_t launch_gemm_bf16_tc(const TcTile* d_tiles, int ntiles, const TcTask* d_tasks, const TcTerm* d_terms,
                                 int* d_err, cudaStream_t s);
 long tc_launch_count();
+void count_tc_launches(long n);
 
 }  // namespace gbdmrg

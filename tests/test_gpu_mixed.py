@@ -39,6 +39,18 @@ def test_bf16_single_pass_close_to_fp64(K, M, k):
 
 
 @pytest.mark.parametrize("K,M,k", CASES)
+def test_bf16_two_slices_close_to_fp64(K, M, k):
+    """Two BF16 slices carry the operands to ~2^-16; three products."""
+    ctx, x, ref, _ = _pair(K, K, M, k, 250 + K)
+    ctx.set_precision(3)
+    ctx.prepare(k)
+    y, _ = ctx.sigma(x)
+    err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+    print(f"two-slice sigma relative error K={K} M={M}: {err:.2e}")
+    assert err < 1e-4
+
+
+@pytest.mark.parametrize("K,M,k", CASES)
 def test_bf16_three_slices_close_to_fp64(K, M, k):
     """Three BF16 slices carry the operands to ~2^-24; what remains is the
     tensor-core FP32 accumulation, which rounds toward zero (a small systematic
@@ -89,9 +101,36 @@ def test_mixed_vs_fp64_truncated_sweeps():
     h, eri = synth.integrals(K, 1606)
     bonds, T = synth.random_mps(K, N, 0, M, 1607)
     e = {}
-    for prec in (0, 2):
+    for prec in (0, 2, 3):
         ctx = context_with_mps(h, eri, N, 0, bonds, T)
         e[prec] = ctx.run([M] * 6, [1e-6, 1e-7, 1e-8, 1e-9, 1e-9, 1e-9], precision=prec)["energy"]
         ctx.close()
-    print("mixed - fp64 sweep energies:", e[2] - e[0])
+    print("three-slice - fp64 sweep energies:", e[2] - e[0])
+    print("two-slice - fp64 sweep energies:", e[3] - e[0])
     assert abs(e[2][-1] - e[0][-1]) < 1e-6
+    assert abs(e[3][-1] - e[0][-1]) < 1e-6
+
+
+@pytest.mark.parametrize("precision", [1, 2, 3])
+def test_chunked_plans_match_unchunked(precision):
+    """A small intermediate budget splits the operator terms into many chunks
+    (the regime of large bonds); results must not depend on the chunking and
+    must stay finite (the shared intermediate buffer is reused between chunks)."""
+    ctx, x, ref, _ = _pair(10, 10, 1000, 3, 400)
+    ctx.set_chunk_budget(1)
+    ctx.prepare(3)
+    y64c, _ = ctx.sigma(x)
+    assert np.linalg.norm(y64c - ref) / np.linalg.norm(ref) < 1e-12
+    ctx.set_precision(precision)
+    ctx.set_chunk_budget(2048)
+    ctx.prepare(3)
+    y1, _ = ctx.sigma(x)
+    tol = 1e-2 if precision == 1 else 1e-4
+    for mb in (4, 1):
+        ctx.set_chunk_budget(mb)
+        ctx.prepare(3)
+        for _ in range(2):
+            yc, _ = ctx.sigma(x)
+            assert np.all(np.isfinite(yc))
+            assert np.linalg.norm(yc - ref) / np.linalg.norm(ref) < tol
+            assert np.linalg.norm(yc - y1) / np.linalg.norm(y1) < (1e-5 if precision == 1 else 1e-6)
