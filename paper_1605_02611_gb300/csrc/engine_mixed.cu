@@ -526,8 +526,10 @@ void run_mixed_sigma(Context& c, SigmaPlan& plan, const double* x, double* y) {
     auto& s1 = mx.stage1[i];
     auto& s2 = mx.stage2[i];
     run_zeros(s1, c.stream);
-    cuda_check(launch_gemm_bf16_tc(s1.tiles.p, s1.ntiles, s1.tasks.p, s1.terms.p, mx.err.p, c.stream), "tc stage 1");
-    cuda_check(launch_gemm_bf16_tc(s2.tiles.p, s2.ntiles, s2.tasks.p, s2.terms.p, mx.err.p, c.stream), "tc stage 2");
+    cuda_check(launch_gemm_bf16_tc(s1.tiles.p, s1.ntiles, s1.tasks.p, s1.terms.p, mx.err.p, c.stream, mx.nsl),
+               "tc stage 1");
+    cuda_check(launch_gemm_bf16_tc(s2.tiles.p, s2.ntiles, s2.tasks.p, s2.terms.p, mx.err.p, c.stream, mx.nsl),
+               "tc stage 2");
   }
   if (mx.n_sig_jobs) launch_unconv(mx.sig_jobs.p, mx.n_sig_jobs, mx.sig_maxel, c.stream);
   if (y != plan.out.p) cuda_check(cudaMemcpyAsync(y, plan.out.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "d2d");
@@ -559,6 +561,7 @@ struct BatchPlan {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   long graph_launches = 0, graph_tc_launches = 0;  // kernels in one replay of the graph
+  int nsl = 1;                                      // largest slice count of the problems
   double flops = 0;
   ~BatchPlan() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -616,6 +619,7 @@ BatchPlan* batch_create(const std::vector<Context*>& ctxs) {
     b->conv_maxel = std::max(b->conv_maxel, mx.psi_maxel);
     b->unconv_maxel = std::max(b->unconv_maxel, mx.sig_maxel);
     b->flops += c->plan.flops;
+    b->nsl = std::max(b->nsl, mx.nsl);
   }
   try {
     for (size_t ch = 0; ch < nch; ++ch) {
@@ -663,10 +667,10 @@ static void batch_enqueue(BatchPlan& b) {
   for (size_t i = 0; i < b.stage1.size(); ++i) {
     run_zeros(b.stage1[i], s);
     cuda_check(launch_gemm_bf16_tc(b.stage1[i].tiles.p, b.stage1[i].ntiles, b.stage1[i].tasks.p,
-                                   b.stage1[i].terms.p, b.err.p, s),
+                                   b.stage1[i].terms.p, b.err.p, s, b.nsl),
                "tc stage 1");
     cuda_check(launch_gemm_bf16_tc(b.stage2[i].tiles.p, b.stage2[i].ntiles, b.stage2[i].tasks.p,
-                                   b.stage2[i].terms.p, b.err.p, s),
+                                   b.stage2[i].terms.p, b.err.p, s, b.nsl),
                "tc stage 2");
   }
   if (b.nunconv) launch_unconv(b.unconv.p, b.nunconv, b.unconv_maxel, s);

@@ -41,8 +41,22 @@ namespace {
 
 constexpr int TC_M = 128, TC_NMAX = 128, TC_K = 64, TC_STAGES = 3;
 constexpr int TC_TILE_BYTES = TC_M * TC_K * 2;  // 16 KB per operand tile
-constexpr int TC_STAGE_BYTES = 2 * TC_TILE_BYTES;
-constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024;
+
+// With three slices a stage holds every BF16 slice of both operands for one
+// 64-wide K step, so each loaded slice serves all the slice products it takes
+// part in (six products from six tiles instead of twelve), at two stages and
+// one CTA per SM.  With one or two slices a stage holds one A and one B slice
+// (one slice pair), three stages, two CTAs per SM: measured faster for two
+// slices, where reuse saves only a third of the loads but halves the CTAs.
+template <int NSL>
+struct TcCfg {
+  static constexpr bool REUSE = NSL == 3;
+  static constexpr int SLOTS = REUSE ? NSL : 1;  // slices of each operand per stage
+  static constexpr int STAGES = REUSE ? 2 : 3;
+  static constexpr int STAGE_BYTES = SLOTS * 2 * TC_TILE_BYTES;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+  static constexpr int CTAS_PER_SM = REUSE ? 1 : 2;
+};
 constexpr int TC_THREADS = 288;
 constexpr int TC_PRODUCERS = 128;  // warps 4-7
 constexpr int TC_TMEM_COLS = 256;  // two accumulators of 128 columns
@@ -128,16 +142,21 @@ __device__ __forceinline__ void load_tile(uint32_t sbase, const __nv_bfloat16* M
   }
 }
 
+template <int NSL>
 __global__ void __launch_bounds__(TC_THREADS, 2)
     gemm_bf16_tc_kernel(const TcTile* __restrict__ tiles, int ntiles, const TcTask* __restrict__ tasks,
                         const TcTerm* __restrict__ terms, int* __restrict__ err) {
+  constexpr int S = TcCfg<NSL>::STAGES;
+  constexpr int STAGE_BYTES = TcCfg<NSL>::STAGE_BYTES;
+  constexpr bool REUSE = TcCfg<NSL>::REUSE;
+  constexpr int SLOTS = TcCfg<NSL>::SLOTS;
   extern __shared__ uint8_t dsm[];
   __shared__ __align__(8) uint64_t full_b[TC_STAGES], empty_b[TC_STAGES], tfull_b[2], tempty_b[2];
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
   // per stage: instruction descriptor, number of K=16 steps, first/last k-step of the tile
   __shared__ uint32_t meta_id[TC_STAGES];
-  __shared__ int meta_nk[TC_STAGES], meta_first[TC_STAGES], meta_last[TC_STAGES];
+  __shared__ int meta_nk[TC_STAGES], meta_np[TC_STAGES], meta_first[TC_STAGES], meta_last[TC_STAGES];
   const uint32_t base = (smem_u32(dsm) + 1023u) & ~1023u;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -147,7 +166,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
   }
   if (tid == 32) {
-    for (int s = 0; s < TC_STAGES; ++s) {
+    for (int s = 0; s < S; ++s) {
       mbar_init(&full_b[s], TC_PRODUCERS + 1);  // async copy arrivals + the metadata writer
       mbar_init(&empty_b[s], 1);
     }
@@ -178,32 +197,42 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
       for (int t = tk.t0; t < tk.t1 && ok; ++t) {
         const TcTerm tm = nxt;
         if (t + 1 < tk.t1) nxt = terms[t + 1];  // prefetch the next descriptor
-        const int np = npairs(tm.nsl);
+        const int ns = tm.nsl < 1 ? 1 : (tm.nsl > NSL ? NSL : tm.nsl);
         const uint32_t id = idesc_bf16(nt, tm.flags & 1);
-        for (int p = 0; p < np && ok; ++p)
-          for (int k0 = 0; k0 < tm.k; k0 += TC_K) {
-            const int s = (int)(j % TC_STAGES);
-            if (j >= TC_STAGES && !mbar_wait(&empty_b[s], (uint32_t)(((j / TC_STAGES) - 1) & 1), abort_flag)) {
-              ok = false;
-              break;
-            }
-            const uint32_t sa = base + s * TC_STAGE_BYTES;
+        const int np = npairs(ns);
+        // stage sequence: one per K step (slice reuse) or one per (slice pair, K step)
+        for (int p = 0; p < (REUSE ? 1 : np) && ok; ++p)
+        for (int k0 = 0; k0 < tm.k; k0 += TC_K) {
+          const int s = (int)(j % S);
+          if (j >= S && !mbar_wait(&empty_b[s], (uint32_t)(((j / S) - 1) & 1), abort_flag)) {
+            ok = false;
+            break;
+          }
+          const uint32_t sa = base + s * STAGE_BYTES;
+          if (REUSE) {
+            for (int i = 0; i < ns; ++i)
+              load_tile(sa + i * TC_TILE_BYTES, tm.A + i * tm.sA, tm.lda, tm.k, tk.m, tl.r0, k0, TC_M, ptid);
+            for (int i = 0; i < ns; ++i)
+              load_tile(sa + (SLOTS + i) * TC_TILE_BYTES, tm.B + i * tm.sB, tm.ldb, tm.k, tk.n, tl.c0, k0, nt, ptid);
+          } else {
             load_tile(sa, tm.A + PAIR_I[p] * tm.sA, tm.lda, tm.k, tk.m, tl.r0, k0, TC_M, ptid);
             load_tile(sa + TC_TILE_BYTES, tm.B + PAIR_J[p] * tm.sB, tm.ldb, tm.k, tk.n, tl.c0, k0, nt, ptid);
-            // the full barrier completes when every producer's copies of this stage
-            // have landed (asynchronous arrivals) and the parameters are written
-            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(&full_b[s]))
-                         : "memory");
-            if (ptid == 0) {
-              meta_id[s] = id;
-              meta_nk[s] = min(TC_K / 16, (tm.k - k0 + 15) / 16);
-              meta_first[s] = first ? 1 : 0;
-              meta_last[s] = (t + 1 == tk.t1 && p + 1 == np && k0 + TC_K >= tm.k) ? 1 : 0;
-              mbar_arrive(&full_b[s]);
-            }
-            first = false;
-            ++j;
           }
+          // the full barrier completes when every producer's copies of this stage
+          // have landed (asynchronous arrivals) and the parameters are written
+          asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(&full_b[s]))
+                       : "memory");
+          if (ptid == 0) {
+            meta_id[s] = id;
+            meta_nk[s] = min(TC_K / 16, (tm.k - k0 + 15) / 16);
+            meta_np[s] = REUSE ? np : 1;
+            meta_first[s] = first ? 1 : 0;
+            meta_last[s] = (t + 1 == tk.t1 && (REUSE || p + 1 == np) && k0 + TC_K >= tm.k) ? 1 : 0;
+            mbar_arrive(&full_b[s]);
+          }
+          first = false;
+          ++j;
+        }
       }
     }
     // let every copy land before the CTA can exit
@@ -223,8 +252,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
         const uint32_t dacc = tmem + (uint32_t)(acc * TC_NMAX);
         for (;;) {
-          const int s = (int)(j % TC_STAGES);
-          if (!mbar_wait(&full_b[s], (uint32_t)((j / TC_STAGES) & 1), abort_flag)) {
+          const int s = (int)(j % S);
+          if (!mbar_wait(&full_b[s], (uint32_t)((j / S) & 1), abort_flag)) {
             ok = false;
             break;
           }
@@ -232,15 +261,19 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
           asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
           const uint32_t id = meta_id[s];
-          const int nk = meta_nk[s], first = meta_first[s], last = meta_last[s];
-          const uint32_t sa = base + s * TC_STAGE_BYTES;
-          for (int kk = 0; kk < nk; ++kk) {
-            const uint64_t ad = sdesc(sa + kk * 32), bd = sdesc(sa + TC_TILE_BYTES + kk * 32);
-            const uint32_t accum = (first && kk == 0) ? 0u : 1u;
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dacc),
-                "l"(ad), "l"(bd), "r"(id), "r"(accum));
+          const int nk = meta_nk[s], np = meta_np[s], first = meta_first[s], last = meta_last[s];
+          const uint32_t sa = base + s * STAGE_BYTES;
+          for (int p = 0; p < np; ++p) {
+            const uint32_t sa_a = sa + (REUSE ? PAIR_I[p] : 0) * TC_TILE_BYTES;
+            const uint32_t sa_b = sa + (SLOTS + (REUSE ? PAIR_J[p] : 0)) * TC_TILE_BYTES;
+            for (int kk = 0; kk < nk; ++kk) {
+              const uint64_t ad = sdesc(sa_a + kk * 32), bd = sdesc(sa_b + kk * 32);
+              const uint32_t accum = (first && p == 0 && kk == 0) ? 0u : 1u;
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dacc),
+                  "l"(ad), "l"(bd), "r"(id), "r"(accum));
+            }
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
               smem_u32(&empty_b[s])));
@@ -327,12 +360,13 @@ std::atomic<long> g_tc_launches{0};
 long tc_launch_count() { return g_tc_launches.load(); }
 void count_tc_launches(long n) { g_tc_launches += n; }
 
-cudaError_t launch_gemm_bf16_tc(const TcTile* d_tiles, int ntiles, const TcTask* d_tasks, const TcTerm* d_terms,
-                                int* d_err, cudaStream_t s) {
-  if (ntiles <= 0) return cudaSuccess;
-  // one-time set-up, thread-safe (function-local static)
+template <int NSL>
+static cudaError_t launch_nsl(const TcTile* d_tiles, int ntiles, const TcTask* d_tasks, const TcTerm* d_terms,
+                              int* d_err, cudaStream_t s) {
+  // one-time set-up per instantiation, thread-safe (function-local static)
   static const int nsm = [] {
-    if (cudaFuncSetAttribute(gemm_bf16_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) != cudaSuccess)
+    if (cudaFuncSetAttribute(gemm_bf16_tc_kernel<NSL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TcCfg<NSL>::SMEM) != cudaSuccess)
       return -1;
     int dev = 0, n = 0;
     cudaGetDevice(&dev);
@@ -340,11 +374,21 @@ cudaError_t launch_gemm_bf16_tc(const TcTile* d_tiles, int ntiles, const TcTask*
     return n > 0 ? n : 148;
   }();
   if (nsm < 0) return cudaErrorInvalidValue;
-  // persistent: two resident CTAs per SM (97 KB shared memory, 256 TMEM columns each)
-  const int grid = ntiles < 2 * nsm ? ntiles : 2 * nsm;
+  // persistent: one wave of resident CTAs (256 TMEM columns each)
+  const int resident = TcCfg<NSL>::CTAS_PER_SM * nsm;
+  const int grid = ntiles < resident ? ntiles : resident;
   ++g_tc_launches;
-  gemm_bf16_tc_kernel<<<grid, TC_THREADS, TC_SMEM, s>>>(d_tiles, ntiles, d_tasks, d_terms, d_err);
+  gemm_bf16_tc_kernel<NSL><<<grid, TC_THREADS, TcCfg<NSL>::SMEM, s>>>(d_tiles, ntiles, d_tasks, d_terms, d_err);
   return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_bf16_tc(const TcTile* d_tiles, int ntiles, const TcTask* d_tasks, const TcTerm* d_terms,
+                                int* d_err, cudaStream_t s, int nsl) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (nsl <= 1) return launch_nsl<1>(d_tiles, ntiles, d_tasks, d_terms, d_err, s);
+  if (nsl == 2) return launch_nsl<2>(d_tiles, ntiles, d_tasks, d_terms, d_err, s);
+  if (nsl == 3) return launch_nsl<3>(d_tiles, ntiles, d_tasks, d_terms, d_err, s);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace gbdmrg

@@ -34,8 +34,9 @@ struct TcTile {
 };
 constexpr int TC_TILE_M = 128, TC_TILE_N = 128;
 
+// nsl: the largest slice count of any term in the list (1, 2 or 3)
 cudaError_t launch_gemm_bf16_tc(const TcTile* d_tiles, int ntiles, const TcTask* d_tasks, const TcTerm* d_terms,
-                                int* d_err, cudaStream_t s);
+                                int* d_err, cudaStream_t s, int nsl = 1);
 long tc_launch_count();
 void count_tc_launches(long n);
 
