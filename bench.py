@@ -234,6 +234,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     c0 = ctx.counters()
     p0 = ctx.phase_times()
+    pf0 = ctx.phase_flops()
     l0 = G.kernel_launches()
     clocks = ClockSampler(local_rank)
     clocks.start()
@@ -252,7 +253,9 @@ def run_ours(args, rank, world, local_rank):
     ms = e0.elapsed_time(e1)
     c1 = ctx.counters()
     p1 = ctx.phase_times()
+    pf1 = ctx.phase_flops()
     phases = {kk: round((p1[kk] - p0[kk]) / args.steps, 4) for kk in p1}
+    phase_tf = {kk: round((pf1[kk] - pf0[kk]) / max(p1[kk] - p0[kk], 1e-12) / 1e12, 3) for kk in p1}
     launches = G.kernel_launches() - l0
     flops = (c1["sigma_flops"] - c0["sigma_flops"]) + (c1["other_flops"] - c0["other_flops"])
     sig_fl = c1["sigma_flops"] - c0["sigma_flops"]
@@ -323,6 +326,7 @@ def run_ours(args, rank, world, local_rank):
                    "setup_s": round(setup_s, 1), "setup_launches": int(setup_launches)},
         "sigma_tflops": achieved_alg, "sigma_calls": sig_calls, "fp64_comparison": fp64_cmp,
         "step_phase_s": phases,
+        "step_phase_tflops": phase_tf,
         "roofline": roof,
         "e2e": {"value": e2e_flops / t_e2e / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": nnz * 8,
                 "d2h_bytes_per_step": nnz * 8},

@@ -192,6 +192,9 @@ gbdmrg_status gbdmrg_counters(gbdmrg_ctx* ctx, double* sigma_flops, double* sigm
  * sums), [1] work lists of H_eff.psi, [2] diagonal, [3] Davidson, [4]
  * decimation, [5] environment update, [6..7] reserved.  seconds[8]. */
 gbdmrg_status gbdmrg_phase_times(gbdmrg_ctx* ctx, double* seconds);
+/* Algorithmic flops of the same phases (sums 2mnk of their GEMMs and 2 per
+ * multiply-add of the W-contracted sums), accumulated like gbdmrg_phase_times. */
+gbdmrg_status gbdmrg_phase_flops(gbdmrg_ctx* ctx, double* flops);
 
 /* Number of CUDA kernel launches issued by this library in this process. */
 int64_t gbdmrg_kernel_launches(void);

@@ -65,6 +65,7 @@ SIGNATURES = {
     "gbdmrg_kernel_launches": (C.c_int64, []),
     "gbdmrg_gemm_bf16_selftest": (C.c_int, [_PI64, _I32, _PI64, _I32, _P]),
     "gbdmrg_phase_times": (C.c_int, [_P, _PD]),
+    "gbdmrg_phase_flops": (C.c_int, [_P, _PD]),
     "gbdmrg_sigma_flops_host": (C.c_int, [C.POINTER(Problem), _I32, _I32, _PI32, _I32, _PI32, _PD]),
     "gbdmrg_run": (C.c_int, [_P, C.POINTER(Schedule), _PD, _PD]),
     "gbdmrg_run_stats": (C.c_int, [_P, _PD, _PD, _PD, _PI32]),
@@ -417,6 +418,11 @@ class Context:
     def phase_times(self):
         t = np.zeros(8)
         self._check(self.lib.gbdmrg_phase_times(self.h, _dptr(t)), "phase_times")
+        return dict(zip(["tilde", "plan", "diag", "davidson", "decimate", "env_update"], t[:6].tolist()))
+
+    def phase_flops(self):
+        t = np.zeros(8)
+        self._check(self.lib.gbdmrg_phase_flops(self.h, _dptr(t)), "phase_flops")
         return dict(zip(["tilde", "plan", "diag", "davidson", "decimate", "env_update"], t[:6].tolist()))
 
     def counters(self):

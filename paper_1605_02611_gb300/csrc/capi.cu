@@ -522,6 +522,13 @@ gbdmrg_status gbdmrg_phase_times(gbdmrg_ctx* ctx, double* seconds) {
   });
 }
 
+gbdmrg_status gbdmrg_phase_flops(gbdmrg_ctx* ctx, double* flops) {
+  if (!ctx || !flops) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    for (int i = 0; i < 8; ++i) flops[i] = ctx->c.phase_flops[i];
+  });
+}
+
 gbdmrg_status gbdmrg_sigma_flops_host(const gbdmrg_problem* prob, int32_t k, int32_t Dl, const int32_t* qn_l,
                                       int32_t Dr, const int32_t* qn_r, double* flops) {
   if (!flops || !qn_l || !qn_r || Dl <= 0 || Dr <= 0) return GBDMRG_EINVAL;

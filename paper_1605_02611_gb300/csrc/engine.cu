@@ -394,6 +394,7 @@ static void finish_tilde(Context& c, Env& env, std::vector<std::vector<std::pair
       t.combo_flops += 2L * (long)L.size() * o.nnz;
     }
   }
+  c.other_flops_total += (double)t.combo_flops;
   if (!outs.empty()) {
     DArr<ComboOut> d_o;
     DArr<ComboTerm> d_t;
@@ -1330,10 +1331,14 @@ double two_site_step(Context& c, int k, int dir, int M, const DavidsonOpts& o, b
     return std::chrono::steady_clock::now();
   };
   auto t0 = now();
+  double f0 = c.other_flops_total + c.sigma_flops_total;
   auto lap = [&](int ph) {
     auto t1 = now();
     c.phase_s[ph] += std::chrono::duration<double>(t1 - t0).count();
+    const double f1 = c.other_flops_total + c.sigma_flops_total;
+    c.phase_flops[ph] += f1 - f0;
     t0 = t1;
+    f0 = f1;
   };
   Tilde lt, rt;
   build_tilde_left(c, c.left[k], k, lt);

@@ -234,6 +234,7 @@ struct Context {
   // 0 W-contracted operators, 1 sigma work lists, 2 diagonal, 3 Davidson,
   // 4 decimation, 5 environment update
   double phase_s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double phase_flops[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // algorithmic flops per phase
   int chunk_budget_mb = 2048;
   // 0: FP64 grouped GEMMs; 1: tensor cores, one BF16 pass; 2: tensor cores,
   // three BF16 slices (six products, about FP32 accuracy); 3: two BF16 slices
