@@ -41,6 +41,10 @@ namespace {
 
 constexpr int TC_M = 128, TC_NMAX = 128, TC_K = 64, TC_STAGES = 3;
 constexpr int TC_TILE_BYTES = TC_M * TC_K * 2;  // 16 KB per operand tile
+// epilogue staging for transposed BF16 stores: per epilogue warp a 32 x 32 block,
+// rows padded to 40 elements (80 B) against bank conflicts
+constexpr int TC_EPI_LD = 40;
+constexpr int TC_EPI_BYTES = 4 * 32 * TC_EPI_LD * 2;
 
 // With three slices a stage holds every BF16 slice of both operands for one
 // 64-wide K step, so each loaded slice serves all the slice products it takes
@@ -54,7 +58,7 @@ struct TcCfg {
   static constexpr int SLOTS = REUSE ? NSL : 1;  // slices of each operand per stage
   static constexpr int STAGES = REUSE ? 2 : 3;
   static constexpr int STAGE_BYTES = SLOTS * 2 * TC_TILE_BYTES;
-  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + TC_EPI_BYTES;
   static constexpr int CTAS_PER_SM = REUSE ? 1 : 2;
 };
 constexpr int TC_THREADS = 288;
@@ -125,6 +129,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile
 
 __device__ __forceinline__ int round16(int x) { return (x + 15) & ~15; }
 
+// four FP32 atomic adds in one vector reduction (16-byte aligned address)
+__device__ __forceinline__ void red_add_v4(float* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(p), "f"(__uint_as_float(a)),
+               "f"(__uint_as_float(b)), "f"(__uint_as_float(c)), "f"(__uint_as_float(d))
+               : "memory");
+}
+
+// BF16 slice s of x: x = s0 + s1 + s2 + O(2^-24 |x|)
+__device__ __forceinline__ __nv_bfloat16 bf16_slice(float x, int s) {
+  const __nv_bfloat16 h0 = __float2bfloat16_rn(x);
+  if (s == 0) return h0;
+  const float r1 = x - __bfloat162float(h0);
+  const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+  if (s == 1) return h1;
+  return __float2bfloat16_rn(r1 - __bfloat162float(h1));
+}
+
 // `nrows` rows of a 64-K tile (rows r0.., k0..) of a row-major bf16 matrix with
 // `rows` valid rows, leading dimension ld and contraction length k; 16-byte
 // chunks that start at or beyond k (or ld) are zero-filled without a read, so
@@ -159,6 +180,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   __shared__ int meta_nk[TC_STAGES], meta_np[TC_STAGES], meta_first[TC_STAGES], meta_last[TC_STAGES];
   const uint32_t base = (smem_u32(dsm) + 1023u) & ~1023u;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  __nv_bfloat16* const epi = reinterpret_cast<__nv_bfloat16*>(dsm + (base - smem_u32(dsm)) + S * STAGE_BYTES);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base_sh)),
@@ -311,13 +333,30 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
               "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-        if (row < tk.m) {
+        const int colb = tl.c0 + c0;          // first column of this 32-column chunk
+        const int nv = min(32, tk.n - colb);  // valid columns in it (>= 1)
+        if (tk.C && row < tk.m) {
+          if (tk.beta == 2 && !tk.trans) {
+            // split-K accumulation: vector reductions along the row
+            float* cp = tk.C + (long)row * tk.ldc + colb;
+            const bool al = (reinterpret_cast<uintptr_t>(cp) & 15) == 0;
 #pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            const int col = tl.c0 + c0 + q;
-            if (col >= tk.n) break;
-            float x = __uint_as_float(v[q]);
-            if (tk.C) {
+            for (int q = 0; q < 32; q += 4) {
+              if (q >= nv) break;
+              if (al && q + 4 <= nv) {
+                red_add_v4(cp + q, v[q], v[q + 1], v[q + 2], v[q + 3]);
+              } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                  if (q + u < nv) atomicAdd(cp + q + u, __uint_as_float(v[q + u]));
+              }
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+              if (q >= nv) break;
+              const int col = colb + q;
+              float x = __uint_as_float(v[q]);
               float* cp = tk.C + (tk.trans ? (long)col * tk.ldc + row : (long)row * tk.ldc + col);
               if (tk.beta == 2) {
                 atomicAdd(cp, x);
@@ -326,16 +365,39 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
                 *cp = x;
               }
             }
-            if (tk.Cb) {
-              const long ob = tk.trans ? (long)col * tk.ldcb + row : (long)row * tk.ldcb + col;
-              const __nv_bfloat16 h0 = __float2bfloat16_rn(x);
-              tk.Cb[ob] = h0;
-              if (tk.nslices > 1) {
-                const float r1 = x - __bfloat162float(h0);
-                const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
-                tk.Cb[tk.slice_stride + ob] = h1;
-                if (tk.nslices > 2) tk.Cb[2 * tk.slice_stride + ob] = __float2bfloat16_rn(r1 - __bfloat162float(h1));
+          }
+        }
+        if (tk.Cb) {
+          if (tk.trans) {
+            // transposed BF16 slices through shared memory: lane = row on the way in,
+            // lane = column on the way out, 16-byte stores along the output rows
+            __nv_bfloat16* st = epi + warp * 32 * TC_EPI_LD;
+            const int rbase = tl.r0 + warp * 32;
+            const bool full = rbase + 32 <= tk.m;
+            for (int sl = 0; sl < tk.nslices; ++sl) {
+#pragma unroll
+              for (int q = 0; q < 32; ++q) st[q * TC_EPI_LD + lane] = bf16_slice(__uint_as_float(v[q]), sl);
+              __syncwarp();
+              if (lane < nv && rbase < tk.m) {
+                __nv_bfloat16* dst = tk.Cb + (long)sl * tk.slice_stride + (long)(colb + lane) * tk.ldcb + rbase;
+                const __nv_bfloat16* src = st + lane * TC_EPI_LD;
+                if (full && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+                  for (int p4 = 0; p4 < 4; ++p4)
+                    *reinterpret_cast<uint4*>(dst + 8 * p4) = *reinterpret_cast<const uint4*>(src + 8 * p4);
+                } else {
+                  for (int r = 0; r < 32 && rbase + r < tk.m; ++r) dst[r] = src[r];
+                }
               }
+              __syncwarp();
+            }
+          } else if (row < tk.m) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+              if (q >= nv) break;
+              const long ob = (long)row * tk.ldcb + colb + q;
+              const float x = __uint_as_float(v[q]);
+              for (int sl = 0; sl < tk.nslices; ++sl) tk.Cb[sl * tk.slice_stride + ob] = bf16_slice(x, sl);
             }
           }
         }
