@@ -240,6 +240,18 @@ gbdmrg_status gbdmrg_run(gbdmrg_ctx* ctx, const gbdmrg_schedule* sched, double* 
 gbdmrg_status gbdmrg_run_stats(gbdmrg_ctx* ctx, double* seconds, double* sigma_flops, double* sigma_seconds,
                                int32_t* davidson_iters);
 
+/* Checkpoint / resume of the MPS (the state a sweep continues from; Sec.
+ * "Matrix product states", Eq. FSMPS): every site's bond sectors
+ * (n_alpha, n_beta, dimension) and quantum-number block data in FP64, written
+ * to a binary file at `path` (host byte order, header "GBDMRGv1", K, N, 2S_z).
+ * gbdmrg_save: GBDMRG_ESTATE if a site is not set, GBDMRG_EIO if the file
+ * cannot be written.  gbdmrg_load: GBDMRG_EINVAL if K, N or 2S_z differ from
+ * the context's problem, GBDMRG_EIO for an unreadable, truncated or
+ * inconsistent file; the context's MPS changes only when the whole file is
+ * valid.  Environments are rebuilt by the next gbdmrg_prepare / gbdmrg_run. */
+gbdmrg_status gbdmrg_save(gbdmrg_ctx* ctx, const char* path);
+gbdmrg_status gbdmrg_load(gbdmrg_ctx* ctx, const char* path);
+
 /* ------------------------------------------------------------------------
  * Learned Davidson preconditioner.
  *

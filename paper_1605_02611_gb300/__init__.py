@@ -69,6 +69,8 @@ SIGNATURES = {
     "gbdmrg_sigma_flops_host": (C.c_int, [C.POINTER(Problem), _I32, _I32, _PI32, _I32, _PI32, _PD]),
     "gbdmrg_run": (C.c_int, [_P, C.POINTER(Schedule), _PD, _PD]),
     "gbdmrg_run_stats": (C.c_int, [_P, _PD, _PD, _PD, _PI32]),
+    "gbdmrg_save": (C.c_int, [_P, C.c_char_p]),
+    "gbdmrg_load": (C.c_int, [_P, C.c_char_p]),
     "gbdmrg_mlp_nparams": (C.c_int64, []),
     "gbdmrg_mlp_create": (C.c_int, [C.c_uint64, _P, C.POINTER(_P)]),
     "gbdmrg_mlp_destroy": (None, [_P]),
@@ -430,6 +432,15 @@ class Context:
         n = C.c_int64()
         self._check(self.lib.gbdmrg_counters(self.h, C.byref(f), C.byref(s), C.byref(n), C.byref(o)), "counters")
         return dict(sigma_flops=f.value, sigma_seconds=s.value, sigma_calls=n.value, other_flops=o.value)
+
+    # ---- checkpoint
+    def save(self, path: str):
+        """Write the MPS to a checkpoint file (gbdmrg_save)."""
+        self._check(self.lib.gbdmrg_save(self.h, os.fsencode(path)), "save")
+
+    def load(self, path: str):
+        """Replace the MPS by the one in a checkpoint file (gbdmrg_load)."""
+        self._check(self.lib.gbdmrg_load(self.h, os.fsencode(path)), "load")
 
     # ---- learned preconditioner
     def set_preconditioner(self, mlp):

@@ -797,4 +797,16 @@ gbdmrg_status gbdmrg_precond_counters(gbdmrg_ctx* ctx, int64_t* learned, int64_t
   });
 }
 
+// ---------------------------------------------------------------- checkpoint
+
+gbdmrg_status gbdmrg_save(gbdmrg_ctx* ctx, const char* path) {
+  if (!ctx || !path) return GBDMRG_EINVAL;
+  return guard(ctx, [&] { gbdmrg::save_mps(ctx->c, path); });
+}
+
+gbdmrg_status gbdmrg_load(gbdmrg_ctx* ctx, const char* path) {
+  if (!ctx || !path) return GBDMRG_EINVAL;
+  return guard(ctx, [&] { gbdmrg::load_mps(ctx->c, path); });
+}
+
 }  // extern "C"

@@ -3,6 +3,8 @@
 // in the kernels of kernels.cu (cuSOLVER syevd serves the dense symmetric
 // eigenproblems of the decimation step).
 #include <algorithm>
+#include <cstdint>
+#include <cstdio>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -283,6 +285,111 @@ void set_site_dense(Context& c, int k, int Dl, int Dr, const int* qn_l, const in
   s.d.upload(h, c.stream);
   cuda_check(cudaStreamSynchronize(c.stream), "sync");
   c.site_set[k] = true;
+  c.prepared = -1;
+}
+
+// ---------------------------------------------------------------- checkpoint
+
+namespace {
+const char kMagic[8] = {'G', 'B', 'D', 'M', 'R', 'G', 'v', '1'};
+
+struct FileCloser {
+  void operator()(FILE* f) const {
+    if (f) std::fclose(f);
+  }
+};
+
+void put(FILE* f, const void* p, size_t n) {
+  if (n && std::fwrite(p, 1, n, f) != n) throw Error(ST_EIO, "checkpoint: write failed");
+}
+void get(FILE* f, void* p, size_t n) {
+  if (n && std::fread(p, 1, n, f) != n) throw Error(ST_EIO, "checkpoint: file truncated or unreadable");
+}
+void put_bond(FILE* f, const Bond& b) {
+  const int32_t ns = b.nsec();
+  put(f, &ns, 4);
+  for (int i = 0; i < ns; ++i) {
+    const int32_t v[3] = {b.qa[i], b.qb[i], b.dim[i]};
+    put(f, v, 12);
+  }
+}
+Bond get_bond(FILE* f) {
+  int32_t ns = 0;
+  get(f, &ns, 4);
+  if (ns < 0 || ns > (1 << 20)) throw Error(ST_EIO, "checkpoint: corrupt bond");
+  Bond b;
+  for (int i = 0; i < ns; ++i) {
+    int32_t v[3];
+    get(f, v, 12);
+    if (v[2] <= 0) throw Error(ST_EIO, "checkpoint: corrupt bond");
+    if (i > 0 && !(v[0] > b.qa.back() || (v[0] == b.qa.back() && v[1] > b.qb.back())))
+      throw Error(ST_EIO, "checkpoint: bond sectors out of order");
+    b.add(v[0], v[1], v[2]);
+  }
+  return b;
+}
+}  // namespace
+
+void save_mps(Context& c, const char* path) {
+  for (int j = 0; j < c.K; ++j)
+    if (!c.site_set[j]) throw Error(ST_ESTATE, "MPS tensor of site " + std::to_string(j) + " not set");
+  std::unique_ptr<FILE, FileCloser> f(std::fopen(path, "wb"));
+  if (!f) throw Error(ST_EIO, std::string("checkpoint: cannot open ") + path + " for writing");
+  put(f.get(), kMagic, 8);
+  const int32_t hdr[4] = {c.K, c.N, c.two_sz, 0};
+  put(f.get(), hdr, 16);
+  std::vector<double> h;
+  for (int k = 0; k < c.K; ++k) {
+    const SiteT& st = c.sites[k];
+    put_bond(f.get(), st.L);
+    put_bond(f.get(), st.R);
+    const int64_t nnz = st.nnz;
+    put(f.get(), &nnz, 8);
+    h.resize(st.nnz);
+    if (st.nnz) cuda_check(cudaMemcpy(h.data(), st.d.p, st.nnz * sizeof(double), cudaMemcpyDeviceToHost), "d2h");
+    put(f.get(), h.data(), st.nnz * sizeof(double));
+  }
+  if (std::fflush(f.get()) != 0) throw Error(ST_EIO, "checkpoint: write failed");
+}
+
+void load_mps(Context& c, const char* path) {
+  std::unique_ptr<FILE, FileCloser> f(std::fopen(path, "rb"));
+  if (!f) throw Error(ST_EIO, std::string("checkpoint: cannot open ") + path);
+  char magic[8];
+  get(f.get(), magic, 8);
+  if (std::memcmp(magic, kMagic, 8) != 0) throw Error(ST_EIO, "checkpoint: not an MPS checkpoint of this library");
+  int32_t hdr[4];
+  get(f.get(), hdr, 16);
+  if (hdr[0] != c.K || hdr[1] != c.N || hdr[2] != c.two_sz)
+    throw Error(ST_EINVAL, "checkpoint: K, N or 2S_z differ from this problem");
+  // read everything first: the context's MPS changes only if the whole file is valid
+  std::vector<SiteT> sites(c.K);
+  std::vector<std::vector<double>> data(c.K);
+  for (int k = 0; k < c.K; ++k) {
+    Bond l = get_bond(f.get()), r = get_bond(f.get());
+    if (k > 0 && !same_bond(sites[k - 1].R, l)) throw Error(ST_EIO, "checkpoint: bonds of neighbouring sites differ");
+    sites[k].layout(l, r);
+    int64_t nnz = 0;
+    get(f.get(), &nnz, 8);
+    if (nnz != sites[k].nnz) throw Error(ST_EIO, "checkpoint: block sizes do not match the bond sectors");
+    data[k].resize(nnz);
+    get(f.get(), data[k].data(), nnz * sizeof(double));
+    for (double v : data[k])
+      if (!std::isfinite(v)) throw Error(ST_EIO, "checkpoint: non-finite MPS entry");
+  }
+  const Bond& l0 = sites[0].L;
+  const Bond& rK = sites[c.K - 1].R;
+  if (!(l0.nsec() == 1 && l0.qa[0] == 0 && l0.qb[0] == 0 && l0.dim[0] == 1) ||
+      !(rK.nsec() == 1 && rK.qa[0] == c.Na && rK.qb[0] == c.Nb && rK.dim[0] == 1))
+    throw Error(ST_EIO, "checkpoint: boundary bonds do not fit this problem");
+  for (int k = 0; k < c.K; ++k) {
+    c.sites[k] = std::move(sites[k]);
+    c.sites[k].d.upload(data[k], c.stream);
+    cuda_check(cudaStreamSynchronize(c.stream), "sync");
+    c.site_set[k] = true;
+  }
+  for (auto& e : c.left) e.valid = false;   // environments of the previous MPS
+  for (auto& e : c.right) e.valid = false;
   c.prepared = -1;
 }
 

@@ -11,6 +11,10 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <exception>
+#include <thread>
+#include <mutex>
+#include <atomic>
 #include <cmath>
 #include <map>
 
@@ -359,9 +363,15 @@ void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, 
   const long xstride = (long)maxchunk;
   const __nv_bfloat16* mir = mx->mirror.p;
   const bool multi = chunks.size() > 1;
-  for (auto ch : chunks) {
+  // the chunks' work lists are independent: built on host threads, uploaded in order
+  struct ChunkLists {
     TcBuilder g1, g2;
     std::vector<ZeroJob> zj;
+  };
+  auto build_chunk = [&](std::pair<size_t, size_t> ch, ChunkLists& out) {
+    TcBuilder& g1 = out.g1;
+    TcBuilder& g2 = out.g2;
+    std::vector<ZeroJob>& zj = out.zj;
     size_t xoff = 0;
     // X^T offsets of this chunk: [beta - b0][g'] (-1 if absent or never written)
     std::vector<std::vector<long>> xpos(ch.second - ch.first, std::vector<long>(ng, -1));
@@ -488,6 +498,34 @@ void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, 
                        [&](const TcTile& a, const TcTile& b) { return w[a.task] > w[b.task]; });
     };
     order(g2);
+  };
+  std::vector<ChunkLists> lists(chunks.size());
+  {
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const size_t nth = std::min<size_t>(chunks.size(), std::min(hw, 16u));
+    std::atomic<size_t> next{0};
+    std::exception_ptr fail;
+    std::mutex fail_mu;
+    auto worker = [&] {
+      for (size_t i; (i = next.fetch_add(1)) < chunks.size();) {
+        try {
+          build_chunk(chunks[i], lists[i]);
+        } catch (...) {
+          std::lock_guard<std::mutex> lk(fail_mu);
+          if (!fail) fail = std::current_exception();
+        }
+      }
+    };
+    std::vector<std::thread> pool;
+    for (size_t t = 1; t < nth; ++t) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
+    if (fail) std::rethrow_exception(fail);
+  }
+  for (ChunkLists& cl : lists) {
+    TcBuilder& g1 = cl.g1;
+    TcBuilder& g2 = cl.g2;
+    std::vector<ZeroJob>& zj = cl.zj;
     auto keep = [&](TcPlan& tp, TcBuilder& g) {
       tp.tiles.upload(g.tiles, c.stream);
       tp.tasks.upload(g.tasks, c.stream);
