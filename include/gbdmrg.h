@@ -240,6 +240,19 @@ gbdmrg_status gbdmrg_run(gbdmrg_ctx* ctx, const gbdmrg_schedule* sched, double* 
 gbdmrg_status gbdmrg_run_stats(gbdmrg_ctx* ctx, double* seconds, double* sigma_flops, double* sigma_seconds,
                                int32_t* davidson_iters);
 
+/* Expectation value <psi|H|psi>/<psi|psi> + ecore of the context's Hamiltonian
+ * in the current MPS, evaluated at the prepared two-site position (gbdmrg_prepare)
+ * as psi . H_eff psi with psi the contraction of sites k, k+1 (Eq. MPSCform, the
+ * two-site form; the renormalised operators of Eq. renormop carry the rest of
+ * the chain).  The value is exact when the sites left of k are left-orthonormal
+ * and those right of k+1 right-orthonormal (as after gbdmrg_run, for k = 0 and
+ * k = 1); elsewhere the norm is only approximated by |psi|^2.  An expectation of
+ * another operator of the same form (for
+ * example a one-body operator: eri = 0) is obtained from a second context with
+ * those integrals and the same MPS (gbdmrg_save / gbdmrg_load or gbdmrg_set_mps).
+ * GBDMRG_ESTATE without gbdmrg_prepare. */
+gbdmrg_status gbdmrg_expectation(gbdmrg_ctx* ctx, double* value);
+
 /* Checkpoint / resume of the MPS (the state a sweep continues from; Sec.
  * "Matrix product states", Eq. FSMPS): every site's bond sectors
  * (n_alpha, n_beta, dimension) and quantum-number block data in FP64, written

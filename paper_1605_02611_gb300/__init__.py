@@ -69,6 +69,7 @@ SIGNATURES = {
     "gbdmrg_sigma_flops_host": (C.c_int, [C.POINTER(Problem), _I32, _I32, _PI32, _I32, _PI32, _PD]),
     "gbdmrg_run": (C.c_int, [_P, C.POINTER(Schedule), _PD, _PD]),
     "gbdmrg_run_stats": (C.c_int, [_P, _PD, _PD, _PD, _PI32]),
+    "gbdmrg_expectation": (C.c_int, [_P, _PD]),
     "gbdmrg_save": (C.c_int, [_P, C.c_char_p]),
     "gbdmrg_load": (C.c_int, [_P, C.c_char_p]),
     "gbdmrg_mlp_nparams": (C.c_int64, []),
@@ -432,6 +433,12 @@ class Context:
         n = C.c_int64()
         self._check(self.lib.gbdmrg_counters(self.h, C.byref(f), C.byref(s), C.byref(n), C.byref(o)), "counters")
         return dict(sigma_flops=f.value, sigma_seconds=s.value, sigma_calls=n.value, other_flops=o.value)
+
+    def expectation(self) -> float:
+        """<psi|H|psi>/<psi|psi> + ecore of the current MPS at the prepared position."""
+        v = C.c_double()
+        self._check(self.lib.gbdmrg_expectation(self.h, C.byref(v)), "expectation")
+        return v.value
 
     # ---- checkpoint
     def save(self, path: str):

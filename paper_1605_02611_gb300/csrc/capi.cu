@@ -809,4 +809,9 @@ gbdmrg_status gbdmrg_load(gbdmrg_ctx* ctx, const char* path) {
   return guard(ctx, [&] { gbdmrg::load_mps(ctx->c, path); });
 }
 
+gbdmrg_status gbdmrg_expectation(gbdmrg_ctx* ctx, double* value) {
+  if (!ctx || !value) return GBDMRG_EINVAL;
+  return guard(ctx, [&] { *value = gbdmrg::expectation(ctx->c); });
+}
+
 }  // extern "C"

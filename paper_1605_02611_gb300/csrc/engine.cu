@@ -1126,6 +1126,27 @@ double davidson(Context& c, SigmaPlan& plan, const double* diag, double* psi, co
   return theta;
 }
 
+// <psi|H|psi> / <psi|psi> for the two-site wavefunction of the current MPS at the
+// prepared position (the MPS contracted with its own environments)
+double expectation(Context& c) {
+  if (c.prepared < 0) throw Error(ST_ESTATE, "call gbdmrg_prepare first");
+  const int k = c.prepared;
+  SigmaPlan& plan = c.plan;
+  const long n = plan.psi.nnz;
+  DArr<double> psi, sig;
+  psi.alloc(n, c.stream);
+  sig.alloc(n, c.stream);
+  make_psi(c, c.sites[k], c.sites[k + 1], plan.psi, psi.p);
+  run_sigma(c, plan, psi.p, sig.p);
+  if (plan.mx && mixed_error(c, plan)) throw Error(ST_ETIMEOUT, "tensor-core GEMM: a bounded wait ran out");
+  DotHelper dh;
+  dh.init(1, c.stream);
+  const double num = dh.dots(c, psi.p, 0, 1, sig.p, n)[0];
+  const double den = dh.dots(c, psi.p, 0, 1, psi.p, n)[0];
+  if (!(den > 0)) throw Error(ST_ESTATE, "the MPS has zero norm at this position");
+  return num / den + c.ecore;
+}
+
 // ---------------------------------------------------------------- decimation
 
 double decimate(Context& c, const PsiLayout& P, const double* psi, int M, int direction, SiteT& left, SiteT& right) {

@@ -254,6 +254,8 @@ struct Context {
 void ctx_init(Context& c);
 void set_site_dense(Context& c, int k, int Dl, int Dr, const int* qn_l, const int* qn_r, const double* A);
 void get_site_dense(Context& c, int k, std::vector<double>& A);
+// <psi|H|psi>/<psi|psi> (+ ecore) of the current MPS at the prepared position
+double expectation(Context& c);
 // checkpoint of the MPS (bond sectors and block data of every site) to a file
 void save_mps(Context& c, const char* path);
 void load_mps(Context& c, const char* path);
