@@ -164,6 +164,20 @@ def dgemm_measured(torch):
     return 2 * n ** 3 / best / 1e9
 
 
+def aggregate_ranks(ms, flops, t_e2e, e2e_flops, world, device):
+    """Whole-job figures over the replicas: times are the maximum over ranks,
+    flops the sum (every rank runs its own replica of the workload)."""
+    if world <= 1:
+        return ms, flops, t_e2e, e2e_flops
+    import torch
+    t = torch.tensor([ms, flops, t_e2e, e2e_flops], dtype=torch.float64, device=device)
+    mx = t.clone()
+    torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+    sm = t.clone()
+    torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1]), float(mx[2]), float(sm[3])
+
+
 def run_reference(args, rank, world):
     """Oracle arm: the CPU oracle on a bounded sample of the workload (rank 0 only)."""
     if rank != 0:
@@ -273,14 +287,7 @@ def run_ours(args, rank, world, local_rank):
     ce1 = ctx.counters()
     e2e_flops = (ce1["sigma_flops"] - ce0["sigma_flops"]) + (ce1["other_flops"] - ce0["other_flops"])
 
-    t = torch.tensor([ms, flops, t_e2e, e2e_flops], dtype=torch.float64, device="cuda")
-    if world > 1:
-        mx = t.clone()
-        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
-        sm = t.clone()
-        torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
-        ms, t_e2e = float(mx[0]), float(mx[2])
-        flops, e2e_flops = float(sm[1]), float(sm[3])
+    ms, flops, t_e2e, e2e_flops = aggregate_ranks(ms, flops, t_e2e, e2e_flops, world, "cuda")
     if rank != 0:
         return
     value = flops / (ms * 1e-3) / 1e12
