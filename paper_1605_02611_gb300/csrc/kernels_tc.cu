@@ -60,10 +60,14 @@ struct TcCfg {
   static constexpr int STAGE_BYTES = SLOTS * 2 * TC_TILE_BYTES;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + TC_EPI_BYTES;
   static constexpr int CTAS_PER_SM = REUSE ? 1 : 2;
+  // one CTA per SM owns all 512 TMEM columns: four accumulators let the MMAs run
+  // up to three tiles ahead of the epilogue; two CTAs per SM share them (two each)
+  static constexpr int NACC = REUSE ? 4 : 2;
+  static constexpr int TMEM_COLS = NACC * TC_NMAX;
 };
 constexpr int TC_THREADS = 288;
 constexpr int TC_PRODUCERS = 128;  // warps 4-7
-constexpr int TC_TMEM_COLS = 256;  // two accumulators of 128 columns
+constexpr int TC_MAXACC = 4;  // tensor-memory accumulators of 128 columns (at most)
 constexpr long TC_WAIT_LIMIT = 1L << 24;
 
 // slice pairs (i, j) with i + j < nsl, largest products first
@@ -172,7 +176,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   constexpr bool REUSE = TcCfg<NSL>::REUSE;
   constexpr int SLOTS = TcCfg<NSL>::SLOTS;
   extern __shared__ uint8_t dsm[];
-  __shared__ __align__(8) uint64_t full_b[TC_STAGES], empty_b[TC_STAGES], tfull_b[2], tempty_b[2];
+  constexpr int NACC = TcCfg<NSL>::NACC;
+  __shared__ __align__(8) uint64_t full_b[TC_STAGES], empty_b[TC_STAGES], tfull_b[TC_MAXACC], tempty_b[TC_MAXACC];
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
   // per stage: instruction descriptor, number of K=16 steps, first/last k-step of the tile
@@ -184,7 +189,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base_sh)),
-                 "r"(TC_TMEM_COLS));
+                 "r"(TcCfg<NSL>::TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
   }
   if (tid == 32) {
@@ -192,7 +197,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
       mbar_init(&full_b[s], TC_PRODUCERS + 1);  // async copy arrivals + the metadata writer
       mbar_init(&empty_b[s], 1);
     }
-    for (int a = 0; a < 2; ++a) {
+    for (int a = 0; a < NACC; ++a) {
       mbar_init(&tfull_b[a], 1);
       mbar_init(&tempty_b[a], 128);
     }
@@ -266,8 +271,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
       int it = 0;
       bool ok = true;
       for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x, ++it) {
-        const int acc = it & 1;
-        if (it >= 2 && !mbar_wait(&tempty_b[acc], (uint32_t)(((it >> 1) - 1) & 1), abort_flag)) {
+        const int acc = it % NACC;
+        if (it >= NACC && !mbar_wait(&tempty_b[acc], (uint32_t)(((it / NACC) - 1) & 1), abort_flag)) {
           ok = false;
           break;
         }
@@ -314,8 +319,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
       const TcTile tl = tiles[ti];
       const TcTask tk = tasks[tl.task];
       const int nt = min(TC_NMAX, round16(tk.n - tl.c0));
-      const int acc = it & 1;
-      bool ok = mbar_wait(&tfull_b[acc], (uint32_t)((it >> 1) & 1), abort_flag);
+      const int acc = it % NACC;
+      bool ok = mbar_wait(&tfull_b[acc], (uint32_t)((it / NACC) & 1), abort_flag);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
@@ -411,7 +416,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   if (tid == 0 && abort_sh) atomicExch(err, 1);
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_TMEM_COLS));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(TcCfg<NSL>::TMEM_COLS));
   }
 }
 
