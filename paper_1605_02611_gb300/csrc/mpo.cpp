@@ -6,6 +6,9 @@
 #include <cmath>
 #include <map>
 #include <stdexcept>
+#include <unordered_map>
+#include <utility>
+#include <vector>
 
 namespace gbdmrg {
 
@@ -114,15 +117,80 @@ void local_op(const FOp* ops, int nops, int site, int pend, double* m) {
       m[n * 4 + np] = la.a[n & 1][np & 1] * lb.a[n >> 1][np >> 1];
 }
 
-struct PairHash {
-  size_t operator()(const std::pair<uint64_t, uint64_t>& p) const {
-    return std::hash<uint64_t>()(p.first * 0x9E3779B97F4A7C15ull ^ p.second);
-  }
-};
-
 struct EntryAcc {
   double m[16];
   bool structural;
+};
+
+// Open-addressing hash table with 64-bit keys (stored as key + 1, 0 = empty),
+// linear probing, values in a dense vector in insertion order.  Much lighter
+// than node-based maps for the tens of millions of insertions of a K=40 build.
+template <class V>
+class FlatMap {
+ public:
+  explicit FlatMap(size_t expect = 16) { rehash(capacity_for(expect)); }
+  // value of key k, default-constructed on first use
+  V& operator[](uint64_t k) {
+    if (2 * (vals_.size() + 1) > slots_.size()) rehash(2 * slots_.size());
+    size_t i = mix(k) & mask_;
+    for (;;) {
+      const uint64_t s = keys_[i];
+      if (s == 0) {
+        keys_[i] = k + 1;
+        slots_[i] = (uint32_t)vals_.size();
+        vals_.emplace_back();
+        order_.push_back(k);
+        return vals_.back();
+      }
+      if (s == k + 1) return vals_[slots_[i]];
+      i = (i + 1) & mask_;
+    }
+  }
+  const V* find(uint64_t k) const {
+    size_t i = mix(k) & mask_;
+    for (;;) {
+      const uint64_t s = keys_[i];
+      if (s == 0) return nullptr;
+      if (s == k + 1) return &vals_[slots_[i]];
+      i = (i + 1) & mask_;
+    }
+  }
+  size_t size() const { return vals_.size(); }
+  uint64_t key(size_t j) const { return order_[j]; }
+  const V& value(size_t j) const { return vals_[j]; }
+  V& value(size_t j) { return vals_[j]; }
+
+ private:
+  // finaliser of MurmurHash3 (Appleby): spreads the bits of packed keys
+  static uint64_t mix(uint64_t x) {
+    x ^= x >> 33;
+    x *= 0xff51afd7ed558ccdULL;
+    x ^= x >> 33;
+    x *= 0xc4ceb9fe1a85ec53ULL;
+    x ^= x >> 33;
+    return x;
+  }
+  static size_t capacity_for(size_t n) {
+    size_t c = 16;
+    while (c < 2 * n) c <<= 1;
+    return c;
+  }
+  void rehash(size_t cap) {
+    keys_.assign(cap, 0);
+    slots_.assign(cap, 0);
+    mask_ = cap - 1;
+    for (size_t j = 0; j < order_.size(); ++j) {
+      size_t i = mix(order_[j]) & mask_;
+      while (keys_[i] != 0) i = (i + 1) & mask_;
+      keys_[i] = order_[j] + 1;
+      slots_[i] = (uint32_t)j;
+    }
+  }
+  std::vector<uint64_t> keys_;
+  std::vector<uint32_t> slots_;
+  std::vector<V> vals_;
+  std::vector<uint64_t> order_;
+  size_t mask_ = 0;
 };
 
 }  // namespace
@@ -130,8 +198,7 @@ struct EntryAcc {
 MPO build_mpo(int K, const double* h, const double* eri, double drop_tol) {
   if (K < 1 || K > 200) throw std::runtime_error("K out of range");
   // 1) unique sorted terms with accumulated coefficients
-  std::unordered_map<uint64_t, double> terms;
-  terms.reserve((size_t)K * K * K * K);
+  FlatMap<double> terms((size_t)K * K * K * K);
   auto add = [&](FOp* o, int n, double c) {
     // zero operator: repeated creator or annihilator on the same spin-orbital
     for (int i = 0; i < n; ++i)
@@ -166,8 +233,8 @@ MPO build_mpo(int K, const double* h, const double* eri, double drop_tol) {
 
   const int half = K / 2;
   // 2) route every term
-  std::unordered_map<uint64_t, std::pair<int, int>> alive;  // key -> [first bond, last bond]
-  std::vector<std::unordered_map<std::pair<uint64_t, uint64_t>, EntryAcc, PairHash>> acc(K);
+  FlatMap<std::pair<int, int>> alive;  // key -> [first bond, last bond]
+  std::vector<FlatMap<EntryAcc>> acc(K);  // per site: (from state, to state) -> W entry
   auto state_at = [&](const Term& t, int b) -> StateKey {
     int e = 0;
     for (int i = 0; i < t.n; ++i)
@@ -187,15 +254,16 @@ MPO build_mpo(int K, const double* h, const double* eri, double drop_tol) {
     return k;
   };
   auto note_alive = [&](uint64_t key, int b) {
-    auto it = alive.find(key);
-    if (it == alive.end()) alive.emplace(key, std::make_pair(b, b));
-    else { it->second.first = std::min(it->second.first, b); it->second.second = std::max(it->second.second, b); }
+    const size_t before = alive.size();
+    std::pair<int, int>& r = alive[key];
+    if (alive.size() != before) r = std::make_pair(b, b);
+    else { r.first = std::min(r.first, b); r.second = std::max(r.second, b); }
   };
   Term t;
-  for (const auto& kv : terms) {
-    double c = kv.second;
+  for (size_t ti = 0; ti < terms.size(); ++ti) {
+    double c = terms.value(ti);
     if (std::fabs(c) <= drop_tol) continue;
-    term_unpack(kv.first, t);
+    term_unpack(terms.key(ti), t);
     // the state only changes at sites carrying operators of the term and at the
     // switch site K/2, so only those sites are visited
     int ev[5], nev = 0;
@@ -222,7 +290,13 @@ MPO build_mpo(int K, const double* h, const double* eri, double drop_tol) {
       bool coef = (prev.kind == 0 || prev.kind == 2) && (nxt.kind == 1 || nxt.kind == 3);
       double m[16];
       local_op(site_ops, ns, s, later, m);
-      auto& slot = acc[s][std::make_pair(pk, nk)];
+      // state keys use 30 bits: the pair packs into one 64-bit key
+      const size_t before = acc[s].size();
+      EntryAcc& slot = acc[s][(pk << 30) | nk];
+      if (acc[s].size() != before) {
+        for (int i = 0; i < 16; ++i) slot.m[i] = 0.0;
+        slot.structural = false;
+      }
       if (coef) {
         for (int i = 0; i < 16; ++i) slot.m[i] += c * m[i];
         slot.structural = false;
@@ -239,8 +313,8 @@ MPO build_mpo(int K, const double* h, const double* eri, double drop_tol) {
   std::vector<std::unordered_map<uint64_t, int>> index(K + 1);
   {
     std::vector<std::vector<uint64_t>> keys(K + 1);
-    for (const auto& kv : alive)
-      for (int b = kv.second.first; b <= kv.second.second; ++b) keys[b].push_back(kv.first);
+    for (size_t j = 0; j < alive.size(); ++j)
+      for (int b = alive.value(j).first; b <= alive.value(j).second; ++b) keys[b].push_back(alive.key(j));
     for (int b = 0; b <= K; ++b) {
       auto& v = keys[b];
       std::vector<BondState> st;
@@ -270,12 +344,14 @@ MPO build_mpo(int K, const double* h, const double* eri, double drop_tol) {
   mpo.W.resize(K);
   for (int s = 0; s < K; ++s) {
     auto& out = mpo.W[s];
-    for (const auto& kv : acc[s]) {
+    for (size_t j = 0; j < acc[s].size(); ++j) {
+      const uint64_t kk = acc[s].key(j);
+      const EntryAcc& a = acc[s].value(j);
       WEntry e;
-      e.row = index[s].at(kv.first.first);
-      e.col = index[s + 1].at(kv.first.second);
+      e.row = index[s].at(kk >> 30);
+      e.col = index[s + 1].at(kk & ((1ULL << 30) - 1));
       bool nz = false;
-      for (int i = 0; i < 16; ++i) { e.m[i] = kv.second.m[i]; if (std::fabs(e.m[i]) > 0) nz = true; }
+      for (int i = 0; i < 16; ++i) { e.m[i] = a.m[i]; if (std::fabs(e.m[i]) > 0) nz = true; }
       if (nz) out.push_back(e);
     }
     for (const auto& kv : index[s]) {
