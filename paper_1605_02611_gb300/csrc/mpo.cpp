@@ -3,6 +3,10 @@
 #include "mpo.hpp"
 
 #include <algorithm>
+#include <thread>
+#include <mutex>
+#include <exception>
+#include <atomic>
 #include <cmath>
 #include <map>
 #include <stdexcept>
@@ -193,6 +197,27 @@ class FlatMap {
   size_t mask_ = 0;
 };
 
+// run f(0..n-1) on n host threads (the calling thread takes 0); the first
+// exception thrown by any of them is rethrown
+template <class F>
+void run_parallel(int n, F&& f) {
+  std::exception_ptr fail;
+  std::mutex mu;
+  auto body = [&](int w) {
+    try {
+      f(w);
+    } catch (...) {
+      std::lock_guard<std::mutex> lk(mu);
+      if (!fail) fail = std::current_exception();
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int w = 1; w < n; ++w) pool.emplace_back(body, w);
+  body(0);
+  for (auto& th : pool) th.join();
+  if (fail) std::rethrow_exception(fail);
+}
+
 }  // namespace
 
 MPO build_mpo(int K, const double* h, const double* eri, double drop_tol) {
@@ -232,8 +257,9 @@ MPO build_mpo(int K, const double* h, const double* eri, double drop_tol) {
         }
 
   const int half = K / 2;
-  // 2) route every term
-  FlatMap<std::pair<int, int>> alive;  // key -> [first bond, last bond]
+  // 2) route every term.  Sites are divided among host threads; every thread
+  // scans all terms and records the transitions at its own sites, so each site's
+  // entries accumulate in the same (term) order whatever the number of threads.
   std::vector<FlatMap<EntryAcc>> acc(K);  // per site: (from state, to state) -> W entry
   auto state_at = [&](const Term& t, int b) -> StateKey {
     int e = 0;
@@ -253,59 +279,89 @@ MPO build_mpo(int K, const double* h, const double* eri, double drop_tol) {
     else { k.kind = 3; k.n = 2; k.ops[0] = t.o[2]; k.ops[1] = t.o[3]; }
     return k;
   };
-  auto note_alive = [&](uint64_t key, int b) {
-    const size_t before = alive.size();
-    std::pair<int, int>& r = alive[key];
-    if (alive.size() != before) r = std::make_pair(b, b);
-    else { r.first = std::min(r.first, b); r.second = std::max(r.second, b); }
-  };
-  Term t;
-  for (size_t ti = 0; ti < terms.size(); ++ti) {
-    double c = terms.value(ti);
-    if (std::fabs(c) <= drop_tol) continue;
-    term_unpack(terms.key(ti), t);
-    // the state only changes at sites carrying operators of the term and at the
-    // switch site K/2, so only those sites are visited
-    int ev[5], nev = 0;
-    for (int i = 0; i < t.n; ++i) ev[nev++] = t.o[i].x / 2;
-    if (half < K) ev[nev++] = half;
-    std::sort(ev, ev + nev);
-    nev = (int)(std::unique(ev, ev + nev) - ev);
-    note_alive(state_at(t, 0).pack(), 0);
-    note_alive(state_at(t, K).pack(), K);
-    for (int e = 0; e < nev; ++e) {
-      const int s = ev[e];
-      StateKey prev = state_at(t, s), nxt = state_at(t, s + 1);
-      uint64_t pk = prev.pack(), nk = nxt.pack();
-      FOp site_ops[4];
-      int ns = 0, later = 0;
-      for (int i = 0; i < t.n; ++i) {
-        int si = t.o[i].x / 2;
-        if (si == s) site_ops[ns++] = t.o[i];
-        else if (si > s) ++later;
-      }
-      if (nk == pk && ns == 0) continue;
-      note_alive(pk, s);
-      note_alive(nk, s + 1);
-      bool coef = (prev.kind == 0 || prev.kind == 2) && (nxt.kind == 1 || nxt.kind == 3);
-      double m[16];
-      local_op(site_ops, ns, s, later, m);
-      // state keys use 30 bits: the pair packs into one 64-bit key
-      const size_t before = acc[s].size();
-      EntryAcc& slot = acc[s][(pk << 30) | nk];
-      if (acc[s].size() != before) {
-        for (int i = 0; i < 16; ++i) slot.m[i] = 0.0;
-        slot.structural = false;
-      }
-      if (coef) {
-        for (int i = 0; i < 16; ++i) slot.m[i] += c * m[i];
-        slot.structural = false;
-      } else if (!slot.structural) {
-        for (int i = 0; i < 16; ++i) slot.m[i] = m[i];
-        slot.structural = true;
-      }
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int nw = (int)std::min<unsigned>(std::min(hw, 16u), (unsigned)K);
+  // owner of each site: the switch site K/2 sees a transition of most terms, so it
+  // gets a worker of its own; the others are dealt out round-robin
+  std::vector<int> owner(K);
+  {
+    int w = nw > 1 ? 1 : 0;
+    for (int s = 0; s < K; ++s) {
+      if (s == half && nw > 1) { owner[s] = 0; continue; }
+      owner[s] = w;
+      w = nw > 1 ? 1 + (w % (nw - 1)) : 0;
     }
   }
+  std::vector<FlatMap<std::pair<int, int>>> alive_w(nw);  // key -> [first bond, last bond]
+  auto route = [&](int w) {
+    FlatMap<std::pair<int, int>>& alive = alive_w[w];
+    auto note_alive = [&](uint64_t key, int b) {
+      const size_t before = alive.size();
+      std::pair<int, int>& r = alive[key];
+      if (alive.size() != before) r = std::make_pair(b, b);
+      else { r.first = std::min(r.first, b); r.second = std::max(r.second, b); }
+    };
+    Term t;
+    for (size_t ti = 0; ti < terms.size(); ++ti) {
+      double c = terms.value(ti);
+      if (std::fabs(c) <= drop_tol) continue;
+      term_unpack(terms.key(ti), t);
+      // the state only changes at sites carrying operators of the term and at the
+      // switch site K/2, so only those sites are visited
+      int ev[5], nev = 0;
+      for (int i = 0; i < t.n; ++i) ev[nev++] = t.o[i].x / 2;
+      if (half < K) ev[nev++] = half;
+      std::sort(ev, ev + nev);
+      nev = (int)(std::unique(ev, ev + nev) - ev);
+      if (w == 0) {
+        note_alive(state_at(t, 0).pack(), 0);
+        note_alive(state_at(t, K).pack(), K);
+      }
+      for (int e = 0; e < nev; ++e) {
+        const int s = ev[e];
+        if (owner[s] != w) continue;
+        StateKey prev = state_at(t, s), nxt = state_at(t, s + 1);
+        uint64_t pk = prev.pack(), nk = nxt.pack();
+        FOp site_ops[4];
+        int ns = 0, later = 0;
+        for (int i = 0; i < t.n; ++i) {
+          int si = t.o[i].x / 2;
+          if (si == s) site_ops[ns++] = t.o[i];
+          else if (si > s) ++later;
+        }
+        if (nk == pk && ns == 0) continue;
+        note_alive(pk, s);
+        note_alive(nk, s + 1);
+        bool coef = (prev.kind == 0 || prev.kind == 2) && (nxt.kind == 1 || nxt.kind == 3);
+        double m[16];
+        local_op(site_ops, ns, s, later, m);
+        // state keys use 30 bits: the pair packs into one 64-bit key
+        const size_t before = acc[s].size();
+        EntryAcc& slot = acc[s][(pk << 30) | nk];
+        if (acc[s].size() != before) {
+          for (int i = 0; i < 16; ++i) slot.m[i] = 0.0;
+          slot.structural = false;
+        }
+        if (coef) {
+          for (int i = 0; i < 16; ++i) slot.m[i] += c * m[i];
+          slot.structural = false;
+        } else if (!slot.structural) {
+          for (int i = 0; i < 16; ++i) slot.m[i] = m[i];
+          slot.structural = true;
+        }
+      }
+    }
+  };
+  run_parallel(nw, route);
+  FlatMap<std::pair<int, int>> alive;
+  for (int w = 0; w < nw; ++w)
+    for (size_t j = 0; j < alive_w[w].size(); ++j) {
+      const std::pair<int, int>& v = alive_w[w].value(j);
+      const size_t before = alive.size();
+      std::pair<int, int>& r = alive[alive_w[w].key(j)];
+      if (alive.size() != before) r = v;
+      else { r.first = std::min(r.first, v.first); r.second = std::max(r.second, v.second); }
+    }
   // 3) bond state lists (deterministic order)
   MPO mpo;
   mpo.K = K;
@@ -342,7 +398,9 @@ MPO build_mpo(int K, const double* h, const double* eri, double drop_tol) {
   }
   // 4) entries: routed transitions + pass-throughs
   mpo.W.resize(K);
-  for (int s = 0; s < K; ++s) {
+  std::atomic<int> next_site{0};
+  run_parallel(nw, [&](int) {
+    for (int s; (s = next_site.fetch_add(1)) < K;) {
     auto& out = mpo.W[s];
     for (size_t j = 0; j < acc[s].size(); ++j) {
       const uint64_t kk = acc[s].key(j);
@@ -369,7 +427,8 @@ MPO build_mpo(int K, const double* h, const double* eri, double drop_tol) {
     std::sort(out.begin(), out.end(), [](const WEntry& a, const WEntry& b) {
       return a.col != b.col ? a.col < b.col : a.row < b.row;
     });
-  }
+    }
+  });
   return mpo;
 }
 
