@@ -164,6 +164,15 @@ def dgemm_measured(torch):
     return 2 * n ** 3 / best / 1e9
 
 
+def workload_name(args):
+    """The workload both arms report: the central two-site step of the named workload."""
+    w = WORKLOADS[args.workload]
+    K = w["K"]
+    k = K // 2 - 1
+    return (f"{args.workload}: K={K} N={w['N']} 2Sz={w['two_sz']} M={w['M']}, two-site step at sites "
+            f"({k},{k + 1}), Davidson {args.dav_iters} iterations/step, precision {args.precision}")
+
+
 def aggregate_ranks(ms, flops, t_e2e, e2e_flops, world, device):
     """Whole-job figures over the replicas: times are the maximum over ranks,
     flops the sum (every rank runs its own replica of the workload)."""
@@ -199,7 +208,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "sample": sample},
+        "config": {"workload": workload_name(args), "parallelism": f"replicas{world}", "sample": sample},
         "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -327,8 +336,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-        "config": {"workload": f"{args.workload}: K={K} N={N} 2Sz={w['two_sz']} M={M}, two-site step at sites "
-                               f"({k},{k + 1}), Davidson {dav} iterations/step, precision {args.precision}",
+        "config": {"workload": workload_name(args),
                    "psi_nnz": nnz, "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (no flush)",
                    "setup_s": round(setup_s, 1), "setup_launches": int(setup_launches)},
         "sigma_tflops": achieved_alg, "sigma_calls": sig_calls, "fp64_comparison": fp64_cmp,
