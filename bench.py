@@ -438,6 +438,12 @@ def run_batched(args):
     for c, x, y in zip(ctxs, xp, yp):
         c.sigma_device(x, y)
         seq_ms += c.sigma_timing(1, x, y)
+    tune = None
+    if args.autotune:
+        # split-K granularity of the fused work lists, chosen by timing the batched launch
+        t_ms, t_split, t_budget = G.autotune(ctxs, reps=3)
+        tune = {"split_tiles_per_sm": t_split, "chunk_budget_mb": t_budget,
+                "candidates": [32, 8, 2, 0.5, 0.125, 0.03125, 0], "ms": [float(v) for v in t_ms[:, 0]]}
     bt = G.Batch(ctxs)
     eager = []
     fl = 0.0
@@ -467,7 +473,7 @@ def run_batched(args):
             "tensor_frac": fl * nprod / graph_ms / 1e9 / peaks["bf16_tflops_sustained"],
             "peak_note": f"{src} bf16 sustained; {nprod} tensor-core products per algorithmic multiply-add",
             "gpu_launches_per_batch": launches / max(1, args.warmup + args.steps), "setup_s": setup_s,
-            "clocks": clk}
+            "autotune": tune, "clocks": clk}
     print(json.dumps(line), flush=True)
     bt.close()
     for c in ctxs:
@@ -493,6 +499,8 @@ def main():
     ap.add_argument("--max-iter", type=int, default=40)
     ap.add_argument("--batched", type=int, default=0,
                     help="> 0: batched H_eff.psi over this many independent problems instead of the step bench")
+    ap.add_argument("--autotune", action="store_true",
+                    help="with --batched: choose the split-K granularity of the fused work lists by timing")
     ap.add_argument("--profile-sigma", type=int, default=0,
                     help="after setup run this many H_eff.psi calls only (for ncu captures) and exit")
     args = ap.parse_args()

@@ -124,6 +124,36 @@ gbdmrg_status gbdmrg_batch_sigma(gbdmrg_batch* b, const double* const* psi_dev, 
 const char* gbdmrg_batch_last_error(const gbdmrg_batch* b);
 void gbdmrg_batch_destroy(gbdmrg_batch* b);
 
+/* Split-K granularity of the tensor-core work lists built by later
+ * gbdmrg_prepare / gbdmrg_plan calls: in the second stage of H_eff.psi the term
+ * list of an output block (the sum over operator terms and symmetry blocks of
+ * Eq. Hpartition) is cut into parts that add atomically, sized so that the stage
+ * has about tiles_per_sm tiles per SM (152 SMs); tiles_per_sm <= 0: never cut.
+ * Default 8.  Every value gives the same sigma up to the order of the FP32
+ * additions.  EINVAL for a null context or a non-finite value. */
+gbdmrg_status gbdmrg_set_split(gbdmrg_ctx* ctx, double tiles_per_sm);
+/* Current plan parameters (either pointer may be NULL). */
+gbdmrg_status gbdmrg_get_plan_params(gbdmrg_ctx* ctx, double* tiles_per_sm, int32_t* chunk_budget_mb);
+
+/* Autotuner of the tensor-core work lists.  For every candidate pair
+ * (splits[i], budgets_mb[j]) (gbdmrg_set_split, gbdmrg_set_chunk_budget) the
+ * work lists of the prepared problems are rebuilt and H_eff.psi is timed with
+ * CUDA events over reps calls after warm-up: with n == 1 the context's own
+ * sigma, with n > 1 the n problems fused into one batched launch per stage and
+ * replayed from a CUDA graph (as gbdmrg_batch_sigma; the contexts need
+ * gbdmrg_keep_host_plans).  The inputs are zero vectors (the time does not
+ * depend on the values).  ms[i * nbudgets + j] (caller-allocated, may be NULL)
+ * receives the time per call of each candidate; the contexts are left with the
+ * fastest pair, returned in best_split / best_budget_mb (may be NULL), and
+ * their work lists rebuilt with it (a batch created earlier must be created
+ * again).  splits == NULL: {32, 8, 2, 0.5, 0.125, 0.03125, 0}; budgets_mb ==
+ * NULL: the current budget of ctxs[0].  EINVAL for empty lists, non-positive
+ * budgets or reps; ESTATE if a context is not prepared in a tensor-core
+ * precision.  Errors are reported through gbdmrg_last_error(ctxs[0]). */
+gbdmrg_status gbdmrg_autotune(int32_t n, gbdmrg_ctx* const* ctxs, int32_t reps, const double* splits,
+                              int32_t nsplits, const int32_t* budgets_mb, int32_t nbudgets, double* ms,
+                              double* best_split, int32_t* best_budget_mb);
+
 /* Build the renormalised operators (Eq. renormop) of bonds k and k+2 from the
  * current MPS tensors in whatever gauge they are (blocking + decimation,
  * Eqs. prenormmatrix/prenormdec), and the work lists of H_eff for the sites

@@ -54,6 +54,9 @@ SIGNATURES = {
     "gbdmrg_batch_sigma": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), _I32, _PD, _PD]),
     "gbdmrg_batch_last_error": (C.c_char_p, [_P]),
     "gbdmrg_batch_destroy": (None, [_P]),
+    "gbdmrg_set_split": (C.c_int, [_P, C.c_double]),
+    "gbdmrg_get_plan_params": (C.c_int, [_P, _PD, _PI32]),
+    "gbdmrg_autotune": (C.c_int, [_I32, C.POINTER(_P), _I32, _PD, _I32, _PI32, _I32, _PD, _PD, _PI32]),
     "gbdmrg_plan": (C.c_int, [_P, _I32]),
     "gbdmrg_psi_layout": (C.c_int, [_P, _PI64, _PI64, _PI64]),
     "gbdmrg_sigma": (C.c_int, [_P, _P, _P, _I32, _PD]),
@@ -269,6 +272,27 @@ class Batch:
             pass
 
 
+def autotune(contexts, reps: int = 3, splits=None, budgets_mb=None):
+    """gbdmrg_autotune over prepared contexts (one: its own sigma; several: the
+    batched launch).  Returns (ms per call [nsplits, nbudgets], best split, best budget)."""
+    lib = load()
+    ctxs = list(contexts)
+    arr = (_P * len(ctxs))(*[c.h for c in ctxs])
+    sp = None if splits is None else np.ascontiguousarray(splits, dtype=np.float64)
+    bu = None if budgets_mb is None else np.ascontiguousarray(budgets_mb, dtype=np.int32)
+    ns = 7 if sp is None else len(sp)
+    nb = 1 if bu is None else len(bu)
+    ms = np.zeros((ns, nb))
+    bs, bb = C.c_double(), C.c_int32()
+    st = lib.gbdmrg_autotune(len(ctxs), arr, reps, None if sp is None else _dptr(sp), 0 if sp is None else ns,
+                             None if bu is None else bu.ctypes.data_as(_PI32), 0 if bu is None else nb,
+                             _dptr(ms), C.byref(bs), C.byref(bb))
+    if st != 0:
+        msg = lib.gbdmrg_last_error(ctxs[0].h).decode() if ctxs else ""
+        raise GbdmrgError(f"gbdmrg_autotune failed: {STATUS.get(st, st)}: {msg}")
+    return ms, bs.value, bb.value
+
+
 class Context:
     """One DMRG problem on the current CUDA device (gbdmrg_create)."""
 
@@ -343,6 +367,16 @@ class Context:
     def set_chunk_budget(self, megabytes: int):
         """Device memory for the per-chunk sigma intermediates (next prepare)."""
         self._check(self.lib.gbdmrg_set_chunk_budget(self.h, megabytes), "set_chunk_budget")
+
+    def set_split(self, tiles_per_sm: float):
+        """Split-K granularity of later tensor-core work lists (tiles per SM; <= 0: none)."""
+        self._check(self.lib.gbdmrg_set_split(self.h, float(tiles_per_sm)), "set_split")
+
+    def plan_params(self):
+        """(split tiles per SM, chunk budget MB) of the work lists built next."""
+        t, b = C.c_double(), C.c_int32()
+        self._check(self.lib.gbdmrg_get_plan_params(self.h, C.byref(t), C.byref(b)), "get_plan_params")
+        return t.value, b.value
 
     def set_precision(self, mode: int):
         """0 FP64, 1 tensor-core BF16 single pass, 2 BF16 x3 slices, 3 BF16 x2 slices."""

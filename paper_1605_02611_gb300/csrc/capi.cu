@@ -1,4 +1,5 @@
 // extern "C" boundary of the library (declarations and contracts: include/gbdmrg.h).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <exception>
@@ -301,6 +302,43 @@ gbdmrg_status gbdmrg_batch_sigma(gbdmrg_batch* b, const double* const* psi_dev, 
 const char* gbdmrg_batch_last_error(const gbdmrg_batch* b) { return b ? b->err.c_str() : "null batch"; }
 
 void gbdmrg_batch_destroy(gbdmrg_batch* b) { delete b; }
+
+gbdmrg_status gbdmrg_set_split(gbdmrg_ctx* ctx, double tiles_per_sm) {
+  if (!ctx || !std::isfinite(tiles_per_sm)) return GBDMRG_EINVAL;
+  return guard(ctx, [&] { ctx->c.split_tps = tiles_per_sm; });
+}
+
+gbdmrg_status gbdmrg_get_plan_params(gbdmrg_ctx* ctx, double* tiles_per_sm, int32_t* chunk_budget_mb) {
+  if (!ctx) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    if (tiles_per_sm) *tiles_per_sm = ctx->c.split_tps;
+    if (chunk_budget_mb) *chunk_budget_mb = ctx->c.chunk_budget_mb;
+  });
+}
+
+gbdmrg_status gbdmrg_autotune(int32_t n, gbdmrg_ctx* const* ctxs, int32_t reps, const double* splits,
+                              int32_t nsplits, const int32_t* budgets_mb, int32_t nbudgets, double* ms,
+                              double* best_split, int32_t* best_budget_mb) {
+  if (n <= 0 || !ctxs || reps <= 0) return GBDMRG_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (!ctxs[i]) return GBDMRG_EINVAL;
+  if ((splits && nsplits <= 0) || (budgets_mb && nbudgets <= 0)) return GBDMRG_EINVAL;
+  return guard(ctxs[0], [&] {
+    std::vector<gbdmrg::Context*> v;
+    for (int i = 0; i < n; ++i) v.push_back(&ctxs[i]->c);
+    std::vector<double> sp = splits ? std::vector<double>(splits, splits + nsplits)
+                                    : std::vector<double>{32, 8, 2, 0.5, 0.125, 0.03125, 0};
+    for (double x : sp)
+      if (!std::isfinite(x)) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "autotune: non-finite split candidate");
+    std::vector<int> bu = budgets_mb ? std::vector<int>(budgets_mb, budgets_mb + nbudgets)
+                                     : std::vector<int>{ctxs[0]->c.chunk_budget_mb};
+    std::vector<double> t;
+    const gbdmrg::TuneChoice best = gbdmrg::autotune_plans(v, sp, bu, reps, t);
+    if (ms) std::copy(t.begin(), t.end(), ms);
+    if (best_split) *best_split = best.split_tps;
+    if (best_budget_mb) *best_budget_mb = best.budget_mb;
+  });
+}
 
 gbdmrg_status gbdmrg_plan(gbdmrg_ctx* ctx, int32_t k) {
   if (!ctx) return GBDMRG_EINVAL;

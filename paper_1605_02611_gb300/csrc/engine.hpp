@@ -236,6 +236,10 @@ struct Context {
   double phase_s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   double phase_flops[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // algorithmic flops per phase
   int chunk_budget_mb = 2048;
+  // stage-2 split-K granularity of tensor-core plans: the term list of an output block
+  // is cut into parts of about (k-steps of the whole stage) / (split_tps x 152), i.e.
+  // about split_tps tiles per SM; <= 0: no split
+  double split_tps = 8.0;
   // 0: FP64 grouped GEMMs; 1: tensor cores, one BF16 pass; 2: tensor cores,
   // three BF16 slices (six products, about FP32 accuracy); 3: two BF16 slices
   // (three products)
@@ -279,6 +283,18 @@ BatchPlan* batch_create(const std::vector<Context*>& ctxs);
 void batch_free(BatchPlan* b);
 double batch_flops(const BatchPlan* b);
 float batch_sigma(BatchPlan& b, const double* const* psi, double* const* sigma, bool use_graph);
+// Autotuner of the tensor-core plans (engine_mixed.cu): for every candidate (split_tps,
+// chunk budget) the plans of the prepared problems are rebuilt and H_eff.psi is timed
+// with CUDA events (one context: its own plan; several: one batched launch per stage
+// over all of them, replayed from a CUDA graph).  ms[i * budgets.size() + j] receives
+// the time per call of (splits[i], budgets[j]); the plans are left built with the
+// fastest candidate, which is returned.
+struct TuneChoice {
+  double split_tps;
+  int budget_mb;
+};
+TuneChoice autotune_plans(const std::vector<Context*>& ctxs, const std::vector<double>& splits,
+                          const std::vector<int>& budgets, int reps, std::vector<double>& ms);
 void compute_diag(Context& c, Tilde& lt, Tilde& rt, int k, const PsiLayout& P, double* diag);
 
 void prepare_two_site(Context& c, int k);

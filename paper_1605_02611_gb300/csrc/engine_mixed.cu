@@ -16,6 +16,7 @@
 #include <mutex>
 #include <atomic>
 #include <cmath>
+#include <limits>
 #include <map>
 
 #include "engine.hpp"
@@ -463,14 +464,16 @@ void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, 
         g2all.end();
       }
     {
-      // k-steps per task and the split that gives about 4 tiles per resident CTA
+      // k-steps per task and the split that gives about split_tps tiles per SM
       long total = 0;
       std::vector<long> w(g2all.tasks.size(), 0);
       for (size_t i = 0; i < g2all.tasks.size(); ++i) {
         for (int t = g2all.tasks[i].t0; t < g2all.tasks[i].t1; ++t) w[i] += (g2all.terms[t].k + 63) / 64;
         total += w[i] * ((g2all.tasks[i].m + 127) / 128);
       }
-      const long target = std::max<long>(1, total / (4L * 2 * 152));
+      const long target = c.split_tps > 0
+                              ? std::max<long>(1, total / std::max<long>(1, std::lround(c.split_tps * 152)))
+                              : std::numeric_limits<long>::max();
       for (size_t i = 0; i < g2all.tasks.size(); ++i) {
         const TcTask& tk = g2all.tasks[i];
         long acc = 0;
@@ -760,6 +763,77 @@ float batch_sigma(BatchPlan& b, const double* const* psi, double* const* sigma, 
   if (h) throw Error(ST_ETIMEOUT, "tensor-core GEMM: a bounded wait ran out");
   cuda_check(cudaStreamSynchronize(s), "sync");
   return ms;
+}
+
+
+// ---------------------------------------------------------------- autotuner
+
+TuneChoice autotune_plans(const std::vector<Context*>& ctxs, const std::vector<double>& splits,
+                          const std::vector<int>& budgets, int reps, std::vector<double>& ms) {
+  if (ctxs.empty() || splits.empty() || budgets.empty() || reps <= 0)
+    throw Error(ST_EINVAL, "autotune: empty problem or candidate list");
+  for (int b : budgets)
+    if (b <= 0) throw Error(ST_EINVAL, "autotune: chunk budgets must be positive");
+  const bool batched = ctxs.size() > 1;
+  for (Context* c : ctxs) {
+    if (c->prepared < 0 || !c->plan.mx)
+      throw Error(ST_ESTATE, "autotune: every context must be prepared in a tensor-core precision");
+    if (batched && !c->keep_host_plans)
+      throw Error(ST_ESTATE, "autotune: tuning a batch needs host copies of the plans (keep_host_plans)");
+  }
+  // inputs and outputs of the timed calls: zero vectors (the time does not depend on
+  // the values), sized for the prepared problems, whose layouts no candidate changes
+  std::vector<DArr<double>> in(ctxs.size()), out(ctxs.size());
+  std::vector<const double*> pin(ctxs.size());
+  std::vector<double*> pout(ctxs.size());
+  for (size_t i = 0; i < ctxs.size(); ++i) {
+    Context& c = *ctxs[i];
+    const size_t n = std::max<size_t>(c.plan.psi.nnz, 1);
+    in[i].alloc(n, c.stream);
+    out[i].alloc(n, c.stream);
+    cuda_check(cudaMemsetAsync(in[i].p, 0, n * sizeof(double), c.stream), "memset");
+    cuda_check(cudaStreamSynchronize(c.stream), "sync");
+    pin[i] = in[i].p;
+    pout[i] = out[i].p;
+  }
+  auto rebuild = [&](double split, int budget) {
+    for (Context* c : ctxs) {
+      c->split_tps = split;
+      c->chunk_budget_mb = budget;
+      build_sigma_plan(*c, c->lt, c->rt, c->prepared, c->plan);
+      cuda_check(cudaStreamSynchronize(c->stream), "sync");
+    }
+  };
+  ms.assign(splits.size() * budgets.size(), 0.0);
+  size_t best = 0;
+  for (size_t i = 0; i < splits.size(); ++i)
+    for (size_t j = 0; j < budgets.size(); ++j) {
+      rebuild(splits[i], budgets[j]);
+      double t = 0;
+      if (batched) {
+        std::unique_ptr<BatchPlan, void (*)(BatchPlan*)> b(batch_create(ctxs), batch_free);
+        batch_sigma(*b, pin.data(), pout.data(), true);  // eager pass, then the graph capture
+        batch_sigma(*b, pin.data(), pout.data(), true);  // first replay
+        for (int r = 0; r < reps; ++r) t += batch_sigma(*b, pin.data(), pout.data(), true);
+      } else {
+        Context& c = *ctxs[0];
+        run_sigma(c, c.plan, pin[0], pout[0]);  // warm-up
+        cuda_check(cudaEventRecord(c.ev0, c.stream), "record");
+        for (int r = 0; r < reps; ++r) run_sigma(c, c.plan, pin[0], pout[0]);
+        cuda_check(cudaEventRecord(c.ev1, c.stream), "record");
+        cuda_check(cudaEventSynchronize(c.ev1), "sync");
+        if (mixed_error(c, c.plan)) throw Error(ST_ETIMEOUT, "tensor-core GEMM: a bounded wait ran out");
+        float e = 0;
+        cuda_check(cudaEventElapsedTime(&e, c.ev0, c.ev1), "elapsed");
+        t = e;
+      }
+      const size_t at = i * budgets.size() + j;
+      ms[at] = t / reps;
+      if (ms[at] < ms[best]) best = at;
+    }
+  const TuneChoice choice{splits[best / budgets.size()], budgets[best % budgets.size()]};
+  rebuild(choice.split_tps, choice.budget_mb);
+  return choice;
 }
 
 }  // namespace gbdmrg

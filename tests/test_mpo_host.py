@@ -73,3 +73,16 @@ def test_header_symbols_exported(lib):
     for n in names:
         assert hasattr(lib, n), n
     assert names <= set(G.SIGNATURES), names - set(G.SIGNATURES)
+
+
+def test_plan_knobs_reject_bad_arguments(lib):
+    """The split-K knob and the autotuner reject null contexts and empty lists on
+    the host, before any device work."""
+    import ctypes as C
+    EINVAL = 1
+    assert lib.gbdmrg_set_split(None, 4.0) == EINVAL
+    assert lib.gbdmrg_get_plan_params(None, None, None) == EINVAL
+    none = (C.c_void_p * 1)(None)
+    assert lib.gbdmrg_autotune(0, none, 3, None, 0, None, 0, None, None, None) == EINVAL
+    assert lib.gbdmrg_autotune(1, none, 3, None, 0, None, 0, None, None, None) == EINVAL
+    assert lib.gbdmrg_autotune(1, None, 3, None, 0, None, 0, None, None, None) == EINVAL
