@@ -307,15 +307,37 @@ def run_ours(args, rank, world, local_rank):
     nprod = {0: 1, 1: 1, 2: 6, 3: 3}[args.precision]
     fp64_cmp = None
     if args.precision > 0 and args.compare_fp64:
+        # full-size checks (outside the timed region): the tensor-core H_eff.psi of the
+        # bench's own work lists against the FP64 one on the same vector, and the
+        # Hermiticity <x2|H x> = <H x2|x> of the FP64 operator
+        checks = {}
+        x = torch.randn(nnz, device="cuda", dtype=torch.float64)
+        x2 = torch.randn(nnz, device="cuda", dtype=torch.float64)
+        y, y2, y_tc = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x)
+        torch.cuda.synchronize()
+        try:
+            ctx.plan(k)
+            ctx.sigma_device(x.data_ptr(), y_tc.data_ptr())
+        except Exception as exc:  # reported in the line, never fatal for the bench
+            checks["error"] = f"tensor-core sigma: {exc}"
         # the same H_eff.psi on the FP64 units (one call), for the mixed/FP64 speed-up
         ctx.set_precision(0)
         ctx.plan(k)
-        x = torch.randn(nnz, device="cuda", dtype=torch.float64)
-        y = torch.empty_like(x)
         fl64 = ctx.sigma_device(x.data_ptr(), y.data_ptr())
         ms64 = ctx.sigma_timing(1, x.data_ptr(), y.data_ptr())
         fp64_cmp = {"sigma_ms": ms64, "sigma_tflops": fl64 / ms64 / 1e9,
                     "speedup_mixed_over_fp64": (fl64 / ms64 / 1e9) and (achieved_alg / (fl64 / ms64 / 1e9))}
+        try:
+            ctx.sigma_device(x2.data_ptr(), y2.data_ptr())
+            ny = float(torch.linalg.vector_norm(y))
+            if "error" not in checks:
+                checks["sigma_rel_err_vs_fp64"] = float(torch.linalg.vector_norm(y_tc - y)) / ny
+                checks["sigma_max_rel_err_vs_fp64"] = float((y_tc - y).abs().max()) / float(y.abs().max())
+            x2_hx, hx2_x = float(torch.dot(x2, y)), float(torch.dot(y2, x))
+            checks["fp64_hermiticity"] = abs(x2_hx - hx2_x) / (float(torch.linalg.vector_norm(x2)) * ny)
+        except Exception as exc:
+            checks["error"] = f"fp64 checks: {exc}"
+        fp64_cmp["fullsize_checks"] = checks
     if args.precision == 0:
         peak = peaks["bf16_tflops_sustained"] * 1.25 / 2250.0
         roof = {"bound": "alu", "achieved": achieved_alg, "peak": peak, "unit": "TFLOP/s",
