@@ -1,4 +1,8 @@
 """Library MPO builder (host code, no GPU) against the brute-force Fock-space oracle."""
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
@@ -65,7 +69,6 @@ def test_invalid_problems_rejected(lib):
 
 def test_header_symbols_exported(lib):
     """Every function declared in include/gbdmrg.h is exported by the library."""
-    import os
     import re
     hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "gbdmrg.h")).read()
     names = set(re.findall(r"\b(gbdmrg_[a-z_]+)\s*\(", hdr))
@@ -86,3 +89,21 @@ def test_plan_knobs_reject_bad_arguments(lib):
     assert lib.gbdmrg_autotune(0, none, 3, None, 0, None, 0, None, None, None) == EINVAL
     assert lib.gbdmrg_autotune(1, none, 3, None, 0, None, 0, None, None, None) == EINVAL
     assert lib.gbdmrg_autotune(1, None, 3, None, 0, None, 0, None, None, None) == EINVAL
+
+
+def test_context_without_gpu_fails_loudly(lib):
+    """No CPU fallback: without a CUDA device creating a context is an error."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h, eri = synth.integrals(4, 1)
+    with pytest.raises(G.GbdmrgError):
+        G.Context(h, eri, 4, 0)
+
+
+def test_missing_library_is_an_error(tmp_path):
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import paper_1605_02611_gb300 as G\n"
+            f"G.load({str(tmp_path / 'libgbdmrg.so')!r})\n")
+    p = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=120)
+    assert p.returncode != 0 and "missing" in p.stderr
