@@ -10,6 +10,7 @@
 #include <cstring>
 #include <map>
 #include <numeric>
+#include <tuple>
 
 #include "engine.hpp"
 #include "mlp.hpp"
@@ -1513,29 +1514,36 @@ double two_site_step(Context& c, int k, int dir, int M, const DavidsonOpts& o, b
 double count_sigma_flops(const MPO& mpo, int k, const Bond& Lb, const Bond& Rb) {
   const auto& mid = mpo.bonds[k + 1];
   // which (n, n') site-operator slots of the W-contracted operators are non-zero
-  std::vector<std::array<char, 16>> lref(mid.size()), rref(mid.size());
-  for (auto& a : lref) a.fill(0);
-  for (auto& a : rref) a.fill(0);
+  std::vector<uint16_t> lmask(mid.size(), 0), rmask(mid.size(), 0);
   for (const auto& e : mpo.W[k])
     for (int nn = 0; nn < 16; ++nn)
-      if (e.m[nn] != 0.0) lref[e.col][nn] = 1;
+      if (e.m[nn] != 0.0) lmask[e.col] |= (uint16_t)(1u << nn);
   for (const auto& e : mpo.W[k + 1])
     for (int nn = 0; nn < 16; ++nn)
-      if (e.m[nn] != 0.0) rref[e.row][nn] = 1;
+      if (e.m[nn] != 0.0) rmask[e.row] |= (uint16_t)(1u << nn);
+  // The count of one bond state depends only on its quantum-number change and its two
+  // slot patterns, so states are grouped by that key.  Every term is an integer and all
+  // sums stay far below 2^53, so the total is exact in any order.
+  std::map<std::tuple<int, int, uint16_t, uint16_t>, long> mult;
+  for (size_t beta = 0; beta < mid.size(); ++beta)
+    mult[std::make_tuple(mid[beta].dna, mid[beta].dnb, rmask[beta], lmask[beta])]++;
   double fl = 0;
-  for (size_t beta = 0; beta < mid.size(); ++beta) {
-    const int da = mid[beta].dna, db = mid[beta].dnb;
-    std::vector<char> xhas((size_t)Lb.nsec() * 16, 0);
+  std::vector<char> xhas((size_t)Lb.nsec() * 16);
+  for (const auto& km : mult) {
+    const int da = std::get<0>(km.first), db = std::get<1>(km.first);
+    const uint16_t rm = std::get<2>(km.first), lm = std::get<3>(km.first);
+    double f = 0;
+    std::fill(xhas.begin(), xhas.end(), 0);
     for (int qlp = 0; qlp < Lb.nsec(); ++qlp)
       for (int n1p = 0; n1p < 4; ++n1p)
         for (int n2 = 0; n2 < 4; ++n2) {
           int qr = Rb.find(Lb.qa[qlp] + LQA[n1p] + LQA[n2] + da, Lb.qb[qlp] + LQB[n1p] + LQB[n2] + db);
           if (qr < 0) continue;
           for (int n2p = 0; n2p < 4; ++n2p) {
-            if (!rref[beta][n2 * 4 + n2p]) continue;
+            if (!((rm >> (n2 * 4 + n2p)) & 1)) continue;
             int qrp = Rb.find(Lb.qa[qlp] + LQA[n1p] + LQA[n2p], Lb.qb[qlp] + LQB[n1p] + LQB[n2p]);
             if (qrp < 0) continue;
-            fl += 2.0 * Rb.dim[qr] * Lb.dim[qlp] * Rb.dim[qrp];
+            f += 2.0 * Rb.dim[qr] * Lb.dim[qlp] * Rb.dim[qrp];
             xhas[(qlp * 4 + n1p) * 4 + n2] = 1;
           }
         }
@@ -1545,13 +1553,14 @@ double count_sigma_flops(const MPO& mpo, int k, const Bond& Lb, const Bond& Rb) 
           int qr = Rb.find(Lb.qa[ql] + LQA[n1] + LQA[n2], Lb.qb[ql] + LQB[n1] + LQB[n2]);
           if (qr < 0) continue;
           for (int n1p = 0; n1p < 4; ++n1p) {
-            if (!lref[beta][n1 * 4 + n1p]) continue;
+            if (!((lm >> (n1 * 4 + n1p)) & 1)) continue;
             // the W-contracted operator changes the quantum number by dQ_beta - q(n1) + q(n1')
             int qlp = Lb.find(Lb.qa[ql] - (da - LQA[n1] + LQA[n1p]), Lb.qb[ql] - (db - LQB[n1] + LQB[n1p]));
             if (qlp < 0 || !xhas[(qlp * 4 + n1p) * 4 + n2]) continue;
-            fl += 2.0 * Lb.dim[ql] * Rb.dim[qr] * Lb.dim[qlp];
+            f += 2.0 * Lb.dim[ql] * Rb.dim[qr] * Lb.dim[qlp];
           }
         }
+    fl += f * (double)km.second;
   }
   return fl;
 }
