@@ -459,20 +459,50 @@ void env_boundary_right(Context& c, Env& e) {
   cuda_check(cudaStreamSynchronize(c.stream), "sync");
 }
 
-// lists[beta*16 + nn] = (env state, coefficient) pairs -> references / combinations
-static void finish_tilde(Context& c, Env& env, std::vector<std::vector<std::pair<int, double>>>& lists,
-                         Tilde& t) {
+// The blocking sums of one side: for every (bond state beta, site slot nn) the list
+// of (environment state, W coefficient) terms, in the order of the W entries, stored
+// as one array with offsets (slot i = beta * 16 + nn owns [start[i], start[i + 1])).
+struct TildeLists {
+  std::vector<long> start;
+  std::vector<std::pair<int, double>> items;
+  size_t size() const { return start.size() - 1; }
+  size_t len(size_t i) const { return (size_t)(start[i + 1] - start[i]); }
+  const std::pair<int, double>* at(size_t i) const { return items.data() + start[i]; }
+};
+
+// lists of W[site]: by_col = the blocking sums over rows (left side) or over columns
+static TildeLists tilde_lists(const MPO& mpo, int site, int nmid, bool by_col) {
+  TildeLists tl;
+  const size_t n = (size_t)nmid * 16;
+  tl.start.assign(n + 1, 0);
+  for (const auto& e : mpo.W[site])
+    for (int nn = 0; nn < 16; ++nn)
+      if (e.m[nn] != 0.0) tl.start[(size_t)(by_col ? e.col : e.row) * 16 + nn + 1]++;
+  for (size_t i = 0; i < n; ++i) tl.start[i + 1] += tl.start[i];
+  tl.items.resize((size_t)tl.start[n]);
+  std::vector<long> fill(tl.start.begin(), tl.start.end() - 1);
+  for (const auto& e : mpo.W[site])
+    for (int nn = 0; nn < 16; ++nn)
+      if (e.m[nn] != 0.0) {
+        const size_t i = (size_t)(by_col ? e.col : e.row) * 16 + nn;
+        tl.items[(size_t)fill[i]++] = {by_col ? e.row : e.col, e.m[nn]};
+      }
+  return tl;
+}
+
+static void finish_tilde(Context& c, Env& env, const TildeLists& lists, Tilde& t) {
   t.env = &env;
   t.ref.assign(t.nmid, {});
   size_t total = 0;
   std::vector<long> off(lists.size(), -1);
   for (size_t i = 0; i < lists.size(); ++i) {
-    auto& L = lists[i];
-    if (L.empty()) continue;
+    const size_t len = lists.len(i);
+    if (!len) continue;
+    const auto* L = lists.at(i);
     int cls = env.st_cls[L[0].first];
-    for (auto& pr : L)
-      if (env.st_cls[pr.first] != cls) throw Error(ST_ECUDA, "internal: mixed operator classes in a blocking sum");
-    if (L.size() > 1) {
+    for (size_t j = 0; j < len; ++j)
+      if (env.st_cls[L[j].first] != cls) throw Error(ST_ECUDA, "internal: mixed operator classes in a blocking sum");
+    if (len > 1) {
       off[i] = (long)total;
       total += env.cls[cls].nnz;
     }
@@ -480,26 +510,28 @@ static void finish_tilde(Context& c, Env& env, std::vector<std::vector<std::pair
   t.combo.alloc(total, c.stream);
   std::vector<ComboOut> outs;
   std::vector<ComboTerm> terms;
+  terms.reserve(lists.items.size());
   long mx = 0;
   t.combo_flops = 0;
   for (size_t i = 0; i < lists.size(); ++i) {
-    auto& L = lists[i];
-    if (L.empty()) continue;
+    const size_t len = lists.len(i);
+    if (!len) continue;
+    const auto* L = lists.at(i);
     int cls = env.st_cls[L[0].first];
     TRef& r = t.ref[i / 16][i % 16];
     r.cls = cls;
-    if (L.size() == 1) {
+    if (len == 1) {
       r.p = env.op(L[0].first);
       r.coef = L[0].second;
     } else {
       r.p = t.combo.p + off[i];
       r.coef = 1.0;
       ComboOut o{t.combo.p + off[i], env.cls[cls].nnz, (int)terms.size(), 0};
-      for (auto& pr : L) terms.push_back({env.op(pr.first), pr.second});
+      for (size_t j = 0; j < len; ++j) terms.push_back({env.op(L[j].first), L[j].second});
       o.t1 = (int)terms.size();
       outs.push_back(o);
       mx = std::max(mx, o.nnz);
-      t.combo_flops += 2L * (long)L.size() * o.nnz;
+      t.combo_flops += 2L * (long)len * o.nnz;
     }
   }
   c.other_flops_total += (double)t.combo_flops;
@@ -516,20 +548,12 @@ static void finish_tilde(Context& c, Env& env, std::vector<std::vector<std::pair
 
 void build_tilde_left(Context& c, Env& L, int site, Tilde& t) {
   t.nmid = (int)c.mpo.bonds[site + 1].size();
-  std::vector<std::vector<std::pair<int, double>>> lists((size_t)t.nmid * 16);
-  for (const auto& e : c.mpo.W[site])
-    for (int nn = 0; nn < 16; ++nn)
-      if (e.m[nn] != 0.0) lists[(size_t)e.col * 16 + nn].push_back({e.row, e.m[nn]});
-  finish_tilde(c, L, lists, t);
+  finish_tilde(c, L, tilde_lists(c.mpo, site, t.nmid, true), t);
 }
 
 void build_tilde_right(Context& c, Env& R, int site, Tilde& t) {
   t.nmid = (int)c.mpo.bonds[site].size();
-  std::vector<std::vector<std::pair<int, double>>> lists((size_t)t.nmid * 16);
-  for (const auto& e : c.mpo.W[site])
-    for (int nn = 0; nn < 16; ++nn)
-      if (e.m[nn] != 0.0) lists[(size_t)e.row * 16 + nn].push_back({e.col, e.m[nn]});
-  finish_tilde(c, R, lists, t);
+  finish_tilde(c, R, tilde_lists(c.mpo, site, t.nmid, false), t);
 }
 
 // column sector of a W-contracted operator block whose row sector is `row`

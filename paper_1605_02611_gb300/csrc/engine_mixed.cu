@@ -16,8 +16,11 @@
 #include <mutex>
 #include <atomic>
 #include <cmath>
+#include <cstdint>
+#include <cstring>
 #include <limits>
 #include <map>
+#include <unordered_map>
 
 #include "engine.hpp"
 #include "kernels_tc.hpp"
@@ -219,9 +222,24 @@ void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, 
   std::vector<long> lsz(Lenv.cls.size()), rsz(Renv.cls.size());
   for (size_t i = 0; i < Lenv.cls.size(); ++i) loff[i] = padded_offsets(Lenv.cls[i], &lsz[i]);
   for (size_t i = 0; i < Renv.cls.size(); ++i) roff[i] = padded_offsets(Renv.cls[i], &rsz[i]);
-  std::map<std::pair<const double*, double>, MirrorRef> mref;
+  struct MirrorKeyHash {
+    size_t operator()(const std::pair<const double*, double>& k) const {
+      uint64_t b;
+      std::memcpy(&b, &k.second, sizeof b);
+      return std::hash<uint64_t>()((uint64_t)(uintptr_t)k.first * 0x9e3779b97f4a7c15ULL ^ b);
+    }
+  };
+  std::unordered_map<std::pair<const double*, double>, MirrorRef, MirrorKeyHash> mref;
   long mtot = 0;
-  std::vector<ConvJob> conv;
+  // mirrors in the order of their first reference: (operator, scale, class, side, offset)
+  struct NewMirror {
+    const double* p;
+    double scale;
+    int cls;
+    bool left;
+    long off;
+  };
+  std::vector<NewMirror> created;
   std::vector<std::array<MirrorRef, 16>> lm(mid.size()), rm(mid.size());
   auto mirror_of = [&](const TRef& r, bool left) -> MirrorRef {
     const double a = std::fabs(r.coef);
@@ -230,19 +248,13 @@ void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, 
     auto it = mref.find(key);
     MirrorRef m;
     if (it == mref.end()) {
-      const OpLayout& L = left ? Lenv.cls[r.cls] : Renv.cls[r.cls];
       const long sz = left ? lsz[r.cls] : rsz[r.cls];
       m.off = mtot;
       m.stride = sz;
       m.boff = left ? &loff[r.cls] : &roff[r.cls];
       mtot += sz * nsl;
-      mref[key] = m;
-      for (size_t b = 0; b < L.blocks.size(); ++b) {
-        const Block& B = L.blocks[b];
-        conv.push_back(
-            {r.p + B.off, nullptr /*patched*/, sz, B.rows, B.cols, B.cols, pad8(B.cols), nsl, scale, pad8(B.cols)});
-        conv.back().dst = (__nv_bfloat16*)(intptr_t)(m.off + (*m.boff)[b]);  // offset, patched below
-      }
+      mref.emplace(key, m);
+      created.push_back({r.p, scale, r.cls, left, m.off});
     } else m = it->second;
     m.neg = (a == 1.0 && r.coef < 0);
     return m;
@@ -252,6 +264,24 @@ void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, 
       if (lt.ref[beta][nn].p) lm[beta][nn] = mirror_of(lt.ref[beta][nn], true);
       if (rt.ref[beta][nn].p) rm[beta][nn] = mirror_of(rt.ref[beta][nn], false);
     }
+  // one conversion job per block of every mirror (dst holds the element offset until
+  // the mirror buffer exists)
+  std::vector<ConvJob> conv;
+  {
+    size_t njobs = 0;
+    for (const NewMirror& nm : created) njobs += (nm.left ? Lenv.cls[nm.cls] : Renv.cls[nm.cls]).blocks.size();
+    conv.reserve(njobs);
+  }
+  for (const NewMirror& nm : created) {
+    const OpLayout& L = nm.left ? Lenv.cls[nm.cls] : Renv.cls[nm.cls];
+    const long sz = nm.left ? lsz[nm.cls] : rsz[nm.cls];
+    const std::vector<long>& boff = nm.left ? loff[nm.cls] : roff[nm.cls];
+    for (size_t b = 0; b < L.blocks.size(); ++b) {
+      const Block& B = L.blocks[b];
+      conv.push_back({nm.p + B.off, (__nv_bfloat16*)(intptr_t)(nm.off + boff[b]), sz, B.rows, B.cols, B.cols,
+                      pad8(B.cols), nsl, nm.scale, pad8(B.cols)});
+    }
+  }
   mx->mirror.alloc(std::max<long>(mtot, 8), c.stream);
   for (auto& j : conv) j.dst = mx->mirror.p + (intptr_t)j.dst;
   {
