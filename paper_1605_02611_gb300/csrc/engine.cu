@@ -8,8 +8,11 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <map>
+#include <mutex>
 #include <numeric>
+#include <thread>
 #include <tuple>
 
 #include "engine.hpp"
@@ -459,6 +462,29 @@ void env_boundary_right(Context& c, Env& e) {
   cuda_check(cudaStreamSynchronize(c.stream), "sync");
 }
 
+// f(lo, hi) over contiguous parts of [0, n) on up to 16 host threads (the calling
+// thread takes the first part); the first exception of any part is rethrown
+template <class F>
+static void parallel_ranges(size_t n, F&& f) {
+  const size_t hw = std::max(1u, std::thread::hardware_concurrency());
+  const size_t nt = std::max<size_t>(1, std::min<size_t>({hw, 16, n / 1024 + 1}));
+  std::exception_ptr fail;
+  std::mutex mu;
+  auto part = [&](size_t t) {
+    try {
+      f(n * t / nt, n * (t + 1) / nt);
+    } catch (...) {
+      std::lock_guard<std::mutex> lk(mu);
+      if (!fail) fail = std::current_exception();
+    }
+  };
+  std::vector<std::thread> pool;
+  for (size_t t = 1; t < nt; ++t) pool.emplace_back(part, t);
+  part(0);
+  for (auto& th : pool) th.join();
+  if (fail) std::rethrow_exception(fail);
+}
+
 // The blocking sums of one side: for every (bond state beta, site slot nn) the list
 // of (environment state, W coefficient) terms, in the order of the W entries, stored
 // as one array with offsets (slot i = beta * 16 + nn owns [start[i], start[i + 1])).
@@ -470,70 +496,100 @@ struct TildeLists {
   const std::pair<int, double>* at(size_t i) const { return items.data() + start[i]; }
 };
 
-// lists of W[site]: by_col = the blocking sums over rows (left side) or over columns
+// lists of W[site]: by_col = the blocking sums over rows (left side) or over columns.
+// Each thread owns a range of bond states and scans all entries for them.
 static TildeLists tilde_lists(const MPO& mpo, int site, int nmid, bool by_col) {
   TildeLists tl;
   const size_t n = (size_t)nmid * 16;
+  const auto& W = mpo.W[site];
   tl.start.assign(n + 1, 0);
-  for (const auto& e : mpo.W[site])
-    for (int nn = 0; nn < 16; ++nn)
-      if (e.m[nn] != 0.0) tl.start[(size_t)(by_col ? e.col : e.row) * 16 + nn + 1]++;
+  parallel_ranges((size_t)nmid, [&](size_t lo, size_t hi) {
+    for (const auto& e : W) {
+      const size_t b = (size_t)(by_col ? e.col : e.row);
+      if (b < lo || b >= hi) continue;
+      for (int nn = 0; nn < 16; ++nn)
+        if (e.m[nn] != 0.0) tl.start[b * 16 + nn + 1]++;
+    }
+  });
   for (size_t i = 0; i < n; ++i) tl.start[i + 1] += tl.start[i];
   tl.items.resize((size_t)tl.start[n]);
-  std::vector<long> fill(tl.start.begin(), tl.start.end() - 1);
-  for (const auto& e : mpo.W[site])
-    for (int nn = 0; nn < 16; ++nn)
-      if (e.m[nn] != 0.0) {
-        const size_t i = (size_t)(by_col ? e.col : e.row) * 16 + nn;
-        tl.items[(size_t)fill[i]++] = {by_col ? e.row : e.col, e.m[nn]};
-      }
+  parallel_ranges((size_t)nmid, [&](size_t lo, size_t hi) {
+    std::vector<long> fill(tl.start.begin() + lo * 16, tl.start.begin() + hi * 16);
+    for (const auto& e : W) {
+      const size_t b = (size_t)(by_col ? e.col : e.row);
+      if (b < lo || b >= hi) continue;
+      for (int nn = 0; nn < 16; ++nn)
+        if (e.m[nn] != 0.0) tl.items[(size_t)fill[(b - lo) * 16 + nn]++] = {by_col ? e.row : e.col, e.m[nn]};
+    }
+  });
   return tl;
 }
 
 static void finish_tilde(Context& c, Env& env, const TildeLists& lists, Tilde& t) {
   t.env = &env;
   t.ref.assign(t.nmid, {});
-  size_t total = 0;
-  std::vector<long> off(lists.size(), -1);
-  for (size_t i = 0; i < lists.size(); ++i) {
+  const size_t n = lists.size();
+  // operator class of every slot (-1: empty), checked to be the same for all terms
+  std::vector<int> cls_of(n, -1);
+  parallel_ranges(n, [&](size_t lo, size_t hi) {
+    for (size_t i = lo; i < hi; ++i) {
+      const size_t len = lists.len(i);
+      if (!len) continue;
+      const auto* L = lists.at(i);
+      const int cls = env.st_cls[L[0].first];
+      for (size_t j = 0; j < len; ++j)
+        if (env.st_cls[L[j].first] != cls) throw Error(ST_ECUDA, "internal: mixed operator classes in a blocking sum");
+      cls_of[i] = cls;
+    }
+  });
+  // slots with several terms become materialised sums: their output offsets, output
+  // index and term range, in slot order
+  std::vector<long> off(n, -1), tstart(n, 0);
+  std::vector<int> oidx(n, -1);
+  size_t total = 0, nterms = 0;
+  int nouts = 0;
+  for (size_t i = 0; i < n; ++i) {
     const size_t len = lists.len(i);
-    if (!len) continue;
-    const auto* L = lists.at(i);
-    int cls = env.st_cls[L[0].first];
-    for (size_t j = 0; j < len; ++j)
-      if (env.st_cls[L[j].first] != cls) throw Error(ST_ECUDA, "internal: mixed operator classes in a blocking sum");
     if (len > 1) {
       off[i] = (long)total;
-      total += env.cls[cls].nnz;
+      total += env.cls[cls_of[i]].nnz;
+      tstart[i] = (long)nterms;
+      nterms += len;
+      oidx[i] = nouts++;
     }
   }
   t.combo.alloc(total, c.stream);
-  std::vector<ComboOut> outs;
-  std::vector<ComboTerm> terms;
-  terms.reserve(lists.items.size());
-  long mx = 0;
-  t.combo_flops = 0;
-  for (size_t i = 0; i < lists.size(); ++i) {
-    const size_t len = lists.len(i);
-    if (!len) continue;
-    const auto* L = lists.at(i);
-    int cls = env.st_cls[L[0].first];
-    TRef& r = t.ref[i / 16][i % 16];
-    r.cls = cls;
-    if (len == 1) {
-      r.p = env.op(L[0].first);
-      r.coef = L[0].second;
-    } else {
-      r.p = t.combo.p + off[i];
-      r.coef = 1.0;
-      ComboOut o{t.combo.p + off[i], env.cls[cls].nnz, (int)terms.size(), 0};
-      for (size_t j = 0; j < len; ++j) terms.push_back({env.op(L[j].first), L[j].second});
-      o.t1 = (int)terms.size();
-      outs.push_back(o);
-      mx = std::max(mx, o.nnz);
-      t.combo_flops += 2L * (long)len * o.nnz;
+  std::vector<ComboOut> outs((size_t)nouts);
+  std::vector<ComboTerm> terms(nterms);
+  std::mutex mu;
+  long mx = 0, flops = 0;
+  parallel_ranges(n, [&](size_t lo, size_t hi) {
+    long my_mx = 0, my_flops = 0;
+    for (size_t i = lo; i < hi; ++i) {
+      const size_t len = lists.len(i);
+      if (!len) continue;
+      const auto* L = lists.at(i);
+      const int cls = cls_of[i];
+      TRef& r = t.ref[i / 16][i % 16];
+      r.cls = cls;
+      if (len == 1) {
+        r.p = env.op(L[0].first);
+        r.coef = L[0].second;
+      } else {
+        r.p = t.combo.p + off[i];
+        r.coef = 1.0;
+        const long nnz = env.cls[cls].nnz;
+        for (size_t j = 0; j < len; ++j) terms[(size_t)tstart[i] + j] = {env.op(L[j].first), L[j].second};
+        outs[(size_t)oidx[i]] = ComboOut{t.combo.p + off[i], nnz, (int)tstart[i], (int)(tstart[i] + (long)len)};
+        my_mx = std::max(my_mx, nnz);
+        my_flops += 2L * (long)len * nnz;
+      }
     }
-  }
+    std::lock_guard<std::mutex> lk(mu);
+    mx = std::max(mx, my_mx);
+    flops += my_flops;
+  });
+  t.combo_flops = flops;
   c.other_flops_total += (double)t.combo_flops;
   if (!outs.empty()) {
     DArr<ComboOut> d_o;
