@@ -264,29 +264,41 @@ void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, 
       if (lt.ref[beta][nn].p) lm[beta][nn] = mirror_of(lt.ref[beta][nn], true);
       if (rt.ref[beta][nn].p) rm[beta][nn] = mirror_of(rt.ref[beta][nn], false);
     }
-  // one conversion job per block of every mirror (dst holds the element offset until
-  // the mirror buffer exists)
-  std::vector<ConvJob> conv;
-  {
-    size_t njobs = 0;
-    for (const NewMirror& nm : created) njobs += (nm.left ? Lenv.cls[nm.cls] : Renv.cls[nm.cls]).blocks.size();
-    conv.reserve(njobs);
-  }
-  for (const NewMirror& nm : created) {
-    const OpLayout& L = nm.left ? Lenv.cls[nm.cls] : Renv.cls[nm.cls];
-    const long sz = nm.left ? lsz[nm.cls] : rsz[nm.cls];
-    const std::vector<long>& boff = nm.left ? loff[nm.cls] : roff[nm.cls];
-    for (size_t b = 0; b < L.blocks.size(); ++b) {
-      const Block& B = L.blocks[b];
-      conv.push_back({nm.p + B.off, (__nv_bfloat16*)(intptr_t)(nm.off + boff[b]), sz, B.rows, B.cols, B.cols,
-                      pad8(B.cols), nsl, nm.scale, pad8(B.cols)});
-    }
-  }
+  // one conversion job per block of every mirror, filled on host threads (each mirror's
+  // jobs are contiguous, in the order the mirrors were first referenced)
   mx->mirror.alloc(std::max<long>(mtot, 8), c.stream);
-  for (auto& j : conv) j.dst = mx->mirror.p + (intptr_t)j.dst;
+  std::vector<size_t> jstart(created.size() + 1, 0);
+  for (size_t i = 0; i < created.size(); ++i)
+    jstart[i + 1] = jstart[i] + (created[i].left ? Lenv.cls[created[i].cls] : Renv.cls[created[i].cls]).blocks.size();
+  std::vector<ConvJob> conv(jstart.back());
+  long maxel = 0;
   {
-    long maxel = 0;
-    for (auto& j : conv) maxel = std::max<long>(maxel, (long)j.rows * j.wcols);
+    std::mutex mu;
+    auto fill = [&](size_t lo, size_t hi) {
+      long mymax = 0;
+      for (size_t i = lo; i < hi; ++i) {
+        const NewMirror& nm = created[i];
+        const OpLayout& L = nm.left ? Lenv.cls[nm.cls] : Renv.cls[nm.cls];
+        const long sz = nm.left ? lsz[nm.cls] : rsz[nm.cls];
+        const std::vector<long>& boff = nm.left ? loff[nm.cls] : roff[nm.cls];
+        for (size_t b = 0; b < L.blocks.size(); ++b) {
+          const Block& B = L.blocks[b];
+          conv[jstart[i] + b] = ConvJob{nm.p + B.off, mx->mirror.p + nm.off + boff[b], sz, B.rows, B.cols, B.cols,
+                                        pad8(B.cols), nsl, nm.scale, pad8(B.cols)};
+          mymax = std::max<long>(mymax, (long)B.rows * pad8(B.cols));
+        }
+      }
+      std::lock_guard<std::mutex> lk(mu);
+      maxel = std::max(maxel, mymax);
+    };
+    const size_t nt = std::max<size_t>(1, std::min<size_t>({std::max(1u, std::thread::hardware_concurrency()), 16,
+                                                             created.size() / 256 + 1}));
+    std::vector<std::thread> pool;
+    for (size_t t = 1; t < nt; ++t) pool.emplace_back(fill, created.size() * t / nt, created.size() * (t + 1) / nt);
+    fill(0, created.size() / nt);
+    for (auto& th : pool) th.join();
+  }
+  {
     DArr<ConvJob> dj;
     dj.upload(conv, c.stream);
     if (!conv.empty()) launch_conv(dj, (int)conv.size(), maxel, c.stream);
