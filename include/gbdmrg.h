@@ -149,7 +149,9 @@ gbdmrg_status gbdmrg_get_plan_params(gbdmrg_ctx* ctx, double* tiles_per_sm, int3
  * again).  splits == NULL: {32, 8, 2, 0.5, 0.125, 0.03125, 0}; budgets_mb ==
  * NULL: the current budget of ctxs[0].  EINVAL for empty lists, non-positive
  * budgets or reps; ESTATE if a context is not prepared in a tensor-core
- * precision.  Errors are reported through gbdmrg_last_error(ctxs[0]). */
+ * precision.  Errors are reported through gbdmrg_last_error(ctxs[0]); after an
+ * error during timing the contexts keep their previous parameters and must be
+ * prepared again. */
 gbdmrg_status gbdmrg_autotune(int32_t n, gbdmrg_ctx* const* ctxs, int32_t reps, const double* splits,
                               int32_t nsplits, const int32_t* budgets_mb, int32_t nbudgets, double* ms,
                               double* best_split, int32_t* best_budget_mb);

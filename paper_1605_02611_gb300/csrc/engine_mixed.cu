@@ -848,6 +848,10 @@ TuneChoice autotune_plans(const std::vector<Context*>& ctxs, const std::vector<d
   };
   ms.assign(splits.size() * budgets.size(), 0.0);
   size_t best = 0;
+  // on an error the contexts get their parameters back and must be prepared again
+  std::vector<std::pair<double, int>> saved;
+  for (Context* c : ctxs) saved.emplace_back(c->split_tps, c->chunk_budget_mb);
+  try {
   for (size_t i = 0; i < splits.size(); ++i)
     for (size_t j = 0; j < budgets.size(); ++j) {
       rebuild(splits[i], budgets[j]);
@@ -876,6 +880,14 @@ TuneChoice autotune_plans(const std::vector<Context*>& ctxs, const std::vector<d
   const TuneChoice choice{splits[best / budgets.size()], budgets[best % budgets.size()]};
   rebuild(choice.split_tps, choice.budget_mb);
   return choice;
+  } catch (...) {
+    for (size_t i = 0; i < ctxs.size(); ++i) {
+      ctxs[i]->split_tps = saved[i].first;
+      ctxs[i]->chunk_budget_mb = saved[i].second;
+      ctxs[i]->prepared = -1;
+    }
+    throw;
+  }
 }
 
 }  // namespace gbdmrg
