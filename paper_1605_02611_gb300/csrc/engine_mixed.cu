@@ -852,34 +852,34 @@ TuneChoice autotune_plans(const std::vector<Context*>& ctxs, const std::vector<d
   std::vector<std::pair<double, int>> saved;
   for (Context* c : ctxs) saved.emplace_back(c->split_tps, c->chunk_budget_mb);
   try {
-  for (size_t i = 0; i < splits.size(); ++i)
-    for (size_t j = 0; j < budgets.size(); ++j) {
-      rebuild(splits[i], budgets[j]);
-      double t = 0;
-      if (batched) {
-        std::unique_ptr<BatchPlan, void (*)(BatchPlan*)> b(batch_create(ctxs), batch_free);
-        batch_sigma(*b, pin.data(), pout.data(), true);  // eager pass, then the graph capture
-        batch_sigma(*b, pin.data(), pout.data(), true);  // first replay
-        for (int r = 0; r < reps; ++r) t += batch_sigma(*b, pin.data(), pout.data(), true);
-      } else {
-        Context& c = *ctxs[0];
-        run_sigma(c, c.plan, pin[0], pout[0]);  // warm-up
-        cuda_check(cudaEventRecord(c.ev0, c.stream), "record");
-        for (int r = 0; r < reps; ++r) run_sigma(c, c.plan, pin[0], pout[0]);
-        cuda_check(cudaEventRecord(c.ev1, c.stream), "record");
-        cuda_check(cudaEventSynchronize(c.ev1), "sync");
-        if (mixed_error(c, c.plan)) throw Error(ST_ETIMEOUT, "tensor-core GEMM: a bounded wait ran out");
-        float e = 0;
-        cuda_check(cudaEventElapsedTime(&e, c.ev0, c.ev1), "elapsed");
-        t = e;
+    for (size_t i = 0; i < splits.size(); ++i)
+      for (size_t j = 0; j < budgets.size(); ++j) {
+        rebuild(splits[i], budgets[j]);
+        double t = 0;
+        if (batched) {
+          std::unique_ptr<BatchPlan, void (*)(BatchPlan*)> b(batch_create(ctxs), batch_free);
+          batch_sigma(*b, pin.data(), pout.data(), true);  // eager pass, then the graph capture
+          batch_sigma(*b, pin.data(), pout.data(), true);  // first replay
+          for (int r = 0; r < reps; ++r) t += batch_sigma(*b, pin.data(), pout.data(), true);
+        } else {
+          Context& c = *ctxs[0];
+          run_sigma(c, c.plan, pin[0], pout[0]);  // warm-up
+          cuda_check(cudaEventRecord(c.ev0, c.stream), "record");
+          for (int r = 0; r < reps; ++r) run_sigma(c, c.plan, pin[0], pout[0]);
+          cuda_check(cudaEventRecord(c.ev1, c.stream), "record");
+          cuda_check(cudaEventSynchronize(c.ev1), "sync");
+          if (mixed_error(c, c.plan)) throw Error(ST_ETIMEOUT, "tensor-core GEMM: a bounded wait ran out");
+          float e = 0;
+          cuda_check(cudaEventElapsedTime(&e, c.ev0, c.ev1), "elapsed");
+          t = e;
+        }
+        const size_t at = i * budgets.size() + j;
+        ms[at] = t / reps;
+        if (ms[at] < ms[best]) best = at;
       }
-      const size_t at = i * budgets.size() + j;
-      ms[at] = t / reps;
-      if (ms[at] < ms[best]) best = at;
-    }
-  const TuneChoice choice{splits[best / budgets.size()], budgets[best % budgets.size()]};
-  rebuild(choice.split_tps, choice.budget_mb);
-  return choice;
+    const TuneChoice choice{splits[best / budgets.size()], budgets[best % budgets.size()]};
+    rebuild(choice.split_tps, choice.budget_mb);
+    return choice;
   } catch (...) {
     for (size_t i = 0; i < ctxs.size(); ++i) {
       ctxs[i]->split_tps = saved[i].first;
