@@ -132,6 +132,15 @@ void gbdmrg_batch_destroy(gbdmrg_batch* b);
  * Default 8.  Every value gives the same sigma up to the order of the FP32
  * additions.  EINVAL for a null context or a non-finite value. */
 gbdmrg_status gbdmrg_set_split(gbdmrg_ctx* ctx, double tiles_per_sm);
+/* Stage-1 decomposition of the tensor-core H_eff.psi for work lists built by
+ * later gbdmrg_prepare / gbdmrg_plan calls.  stacked = 0 (default): one task per
+ * (bond state, group of psi columns, output sector) with up to four site-block
+ * terms.  stacked = 1: one task per (bond state, group) whose operand is the
+ * W-contracted right operator over all four x four site blocks of the two groups,
+ * built once per work list in BF16 slices with absent blocks zero (fewer, deeper
+ * tiles; more memory and more padded products).  Same sigma up to the order of
+ * the FP32 additions.  EINVAL for a null context. */
+gbdmrg_status gbdmrg_set_stage1_stacked(gbdmrg_ctx* ctx, int32_t stacked);
 /* Current plan parameters (either pointer may be NULL). */
 gbdmrg_status gbdmrg_get_plan_params(gbdmrg_ctx* ctx, double* tiles_per_sm, int32_t* chunk_budget_mb);
 

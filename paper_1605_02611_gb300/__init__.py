@@ -56,6 +56,7 @@ SIGNATURES = {
     "gbdmrg_batch_destroy": (None, [_P]),
     "gbdmrg_set_split": (C.c_int, [_P, C.c_double]),
     "gbdmrg_get_plan_params": (C.c_int, [_P, _PD, _PI32]),
+    "gbdmrg_set_stage1_stacked": (C.c_int, [_P, _I32]),
     "gbdmrg_autotune": (C.c_int, [_I32, C.POINTER(_P), _I32, _PD, _I32, _PI32, _I32, _PD, _PD, _PI32]),
     "gbdmrg_plan": (C.c_int, [_P, _I32]),
     "gbdmrg_psi_layout": (C.c_int, [_P, _PI64, _PI64, _PI64]),
@@ -371,6 +372,10 @@ class Context:
     def set_split(self, tiles_per_sm: float):
         """Split-K granularity of later tensor-core work lists (tiles per SM; <= 0: none)."""
         self._check(self.lib.gbdmrg_set_split(self.h, float(tiles_per_sm)), "set_split")
+
+    def set_stage1_stacked(self, stacked: bool = True):
+        """Stage 1 of later tensor-core work lists over stacked right operands."""
+        self._check(self.lib.gbdmrg_set_stage1_stacked(self.h, int(stacked)), "set_stage1_stacked")
 
     def plan_params(self):
         """(split tiles per SM, chunk budget MB) of the work lists built next."""

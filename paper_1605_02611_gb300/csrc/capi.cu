@@ -308,6 +308,11 @@ gbdmrg_status gbdmrg_set_split(gbdmrg_ctx* ctx, double tiles_per_sm) {
   return guard(ctx, [&] { ctx->c.split_tps = tiles_per_sm; });
 }
 
+gbdmrg_status gbdmrg_set_stage1_stacked(gbdmrg_ctx* ctx, int32_t stacked) {
+  if (!ctx) return GBDMRG_EINVAL;
+  return guard(ctx, [&] { ctx->c.stage1_stacked = stacked != 0; });
+}
+
 gbdmrg_status gbdmrg_get_plan_params(gbdmrg_ctx* ctx, double* tiles_per_sm, int32_t* chunk_budget_mb) {
   if (!ctx) return GBDMRG_EINVAL;
   return guard(ctx, [&] {

@@ -240,6 +240,10 @@ struct Context {
   // is cut into parts of about (k-steps of the whole stage) / (split_tps x 152), i.e.
   // about split_tps tiles per SM; <= 0: no split
   double split_tps = 8.0;
+  // stage 1 of the tensor-core sigma with stacked right operands: one task per
+  // (bond state, group) whose operand is the W-contracted right operator over all
+  // four x four site blocks of the two groups (absent blocks zero)
+  bool stage1_stacked = false;
   // 0: FP64 grouped GEMMs; 1: tensor cores, one BF16 pass; 2: tensor cores,
   // three BF16 slices (six products, about FP32 accuracy); 3: two BF16 slices
   // (three products)

@@ -178,6 +178,9 @@ struct MixedPlan {
   long sig_total = 0;
   std::vector<TcPlan> stage1, stage2;
   DArr<int> err;
+  // stacked right operands of stage 1 (stage1_stacked): nsl slices of rs_total elements
+  DArr<__nv_bfloat16> rstack;
+  long rs_total = 0;
 };
 
 void mixed_plan_free(MixedPlan* p) { delete p; }
@@ -259,10 +262,11 @@ void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, 
     m.neg = (a == 1.0 && r.coef < 0);
     return m;
   };
+  const bool stacked = c.stage1_stacked;
   for (size_t beta = 0; beta < mid.size(); ++beta)
     for (int nn = 0; nn < 16; ++nn) {
       if (lt.ref[beta][nn].p) lm[beta][nn] = mirror_of(lt.ref[beta][nn], true);
-      if (rt.ref[beta][nn].p) rm[beta][nn] = mirror_of(rt.ref[beta][nn], false);
+      if (rt.ref[beta][nn].p && !stacked) rm[beta][nn] = mirror_of(rt.ref[beta][nn], false);
     }
   // one conversion job per block of every mirror, filled on host threads (each mirror's
   // jobs are contiguous, in the order the mirrors were first referenced)
@@ -381,6 +385,56 @@ void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, 
   }
   mx->err.alloc(1, c.stream);
   cuda_check(cudaMemsetAsync(mx->err.p, 0, sizeof(int), c.stream), "memset");
+  // ---- stacked right operands (stage1_stacked): for every (beta, g') with g = g' + dQ_beta
+  // the matrix Rt_beta[(n2, qr) blocks of g, (n2', qr') blocks of g'] (C_g x C_g', the
+  // column layout of Psi_g'), absent site blocks and padding zero, scaled by the W
+  // coefficient of each block
+  std::vector<long> soff;
+  if (stacked) {
+    soff.assign(mid.size() * (size_t)ng, -1);
+    std::vector<ConvJob> sj;
+    long stot = 0, smax = 0;
+    for (size_t beta = 0; beta < mid.size(); ++beta)
+      for (int gp = 0; gp < ng; ++gp) {
+        const int g = group_of(gq[gp].first + mid[beta].dna, gq[gp].second + mid[beta].dnb);
+        if (g < 0) continue;
+        const size_t j0 = sj.size();
+        for (const auto& cb : gcol[g]) {
+          const int n2 = cb[0], qr = cb[1];
+          for (int n2p = 0; n2p < 4; ++n2p) {
+            const TRef& r = rt.ref[beta][n2 * 4 + n2p];
+            if (!r.p) continue;
+            const int qrp = Rb.find(gq[gp].first + LQA[n2p], gq[gp].second + LQB[n2p]);
+            if (qrp < 0) continue;
+            const auto cpp = cpos[qrp * 4 + n2p];
+            if (cpp[0] != gp) continue;
+            const OpLayout& Lay = Renv.cls[r.cls];
+            const int bl = Lay.blk_of_col[qrp];
+            if (bl < 0 || Lay.blocks[bl].rs != qr) continue;
+            const Block& B = Lay.blocks[bl];
+            // dst holds the element offset until the buffer exists
+            sj.push_back({r.p + B.off, (__nv_bfloat16*)(intptr_t)(stot + (long)cb[2] * gC[gp] + cpp[1]), 0, B.rows,
+                          B.cols, B.cols, gC[gp], nsl, r.coef, pad8(B.cols)});
+            smax = std::max<long>(smax, (long)B.rows * pad8(B.cols));
+          }
+        }
+        if (sj.size() > j0) {
+          soff[beta * ng + gp] = stot;
+          stot += (long)gC[g] * gC[gp];
+        }
+      }
+    mx->rs_total = std::max<long>(stot, 8);
+    mx->rstack.alloc((size_t)mx->rs_total * nsl, c.stream);
+    cuda_check(cudaMemsetAsync(mx->rstack.p, 0, mx->rstack.n * sizeof(__nv_bfloat16), c.stream), "memset");
+    for (auto& j : sj) {
+      j.dst = mx->rstack.p + (intptr_t)j.dst;
+      j.slice_stride = mx->rs_total;
+    }
+    DArr<ConvJob> dj;
+    dj.upload(sj, c.stream);
+    if (!sj.empty()) launch_conv(dj, (int)sj.size(), smax, c.stream);
+    cuda_check(cudaStreamSynchronize(c.stream), "sync");
+  }
   // ---- X_beta^T per (beta, g'): C_g x R_g' with g = g' + dQ_beta; chunking over beta
   std::vector<size_t> xsz(mid.size(), 0);
   for (size_t beta = 0; beta < mid.size(); ++beta)
@@ -424,6 +478,25 @@ void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, 
         const int g = group_of(gq[gp].first + mid[beta].dna, gq[gp].second + mid[beta].dnb);
         if (g < 0) continue;
         const long base = (long)xoff;
+        if (stacked) {
+          // one task: X_beta^T (C_g x R_g') = (Psi_g' Rt_beta^T)^T over the whole group
+          const long so = soff[beta * ng + gp];
+          if (so < 0) continue;
+          TcTask t{};
+          t.Cb = mx->X_b.p + base;
+          t.slice_stride = xstride;
+          t.ldcb = gR[gp];
+          t.m = gR[gp];
+          t.n = gC[g];
+          t.nslices = nsl;
+          t.trans = 1;
+          g1.begin(t);
+          g1.term(mx->psi_b.p + goff[gp], ptot, gC[gp], mx->rstack.p + so, mx->rs_total, gC[gp], gC[gp], false, nsl);
+          g1.end();
+          xp[gp] = base;
+          xoff += (size_t)gC[g] * gR[gp];
+          continue;
+        }
         bool any = false;
         std::vector<ZeroJob> empty_cb;  // column blocks of X^T without a term
         // stage 1: X_beta[rows of g', (n2, qr) block of g] = sum_{n2'} Psi_g'[:, (n2', qr')] Rt^{n2 n2'}[qr, qr']^T,
