@@ -231,6 +231,8 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream()
     ctx = G.Context(h, eri, N, w["two_sz"], stream=stream.cuda_stream)
     ctx.set_precision(args.precision)
+    if args.stage1_stacked:
+        ctx.set_stage1_stacked(True)
     ctx.set_mps(T, [b.labels() for b in bonds])
     del T
     ctx.prepare(k)
@@ -360,7 +362,8 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": dtype, "data": "synthetic",
         "config": {"workload": workload_name(args),
                    "psi_nnz": nnz, "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (no flush)",
-                   "setup_s": round(setup_s, 1), "setup_launches": int(setup_launches)},
+                   "setup_s": round(setup_s, 1), "setup_launches": int(setup_launches),
+                   "stage1": "stacked" if args.stage1_stacked else "per-sector"},
         "sigma_tflops": achieved_alg, "sigma_calls": sig_calls, "fp64_comparison": fp64_cmp,
         "step_phase_s": phases,
         "step_phase_tflops": phase_tf,
@@ -521,6 +524,8 @@ def main():
     ap.add_argument("--max-iter", type=int, default=40)
     ap.add_argument("--batched", type=int, default=0,
                     help="> 0: batched H_eff.psi over this many independent problems instead of the step bench")
+    ap.add_argument("--stage1-stacked", action="store_true",
+                    help="tensor-core sigma with stacked right operands in stage 1")
     ap.add_argument("--autotune", action="store_true",
                     help="with --batched: choose the split-K granularity of the fused work lists by timing")
     ap.add_argument("--profile-sigma", type=int, default=0,
