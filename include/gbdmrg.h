@@ -141,6 +141,15 @@ gbdmrg_status gbdmrg_set_split(gbdmrg_ctx* ctx, double tiles_per_sm);
  * tiles; more memory and more padded products).  Same sigma up to the order of
  * the FP32 additions.  EINVAL for a null context. */
 gbdmrg_status gbdmrg_set_stage1_stacked(gbdmrg_ctx* ctx, int32_t stacked);
+/* W-contracted operator sums on the tensor cores.  on != 0: a blocking sum of
+ * Eq. prenormrule type with at least min_terms terms in total, built for later
+ * gbdmrg_prepare / gbdmrg_plan / gbdmrg_step calls in a tensor-core precision,
+ * whose results feed only the tensor-core H_eff.psi and the H_eff diagonal (the
+ * side that the environment update of the step does not use), is formed as one
+ * GEMM per operator class in three BF16 slices with FP32 accumulation (about
+ * FP32 accuracy) instead of on the FP64 units.  Default off, min_terms 100000.
+ * EINVAL for a null context or a negative min_terms. */
+gbdmrg_status gbdmrg_set_tc_combos(gbdmrg_ctx* ctx, int32_t on, int64_t min_terms);
 /* Current plan parameters (either pointer may be NULL). */
 gbdmrg_status gbdmrg_get_plan_params(gbdmrg_ctx* ctx, double* tiles_per_sm, int32_t* chunk_budget_mb);
 

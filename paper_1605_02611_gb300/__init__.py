@@ -57,6 +57,7 @@ SIGNATURES = {
     "gbdmrg_set_split": (C.c_int, [_P, C.c_double]),
     "gbdmrg_get_plan_params": (C.c_int, [_P, _PD, _PI32]),
     "gbdmrg_set_stage1_stacked": (C.c_int, [_P, _I32]),
+    "gbdmrg_set_tc_combos": (C.c_int, [_P, _I32, C.c_int64]),
     "gbdmrg_autotune": (C.c_int, [_I32, C.POINTER(_P), _I32, _PD, _I32, _PI32, _I32, _PD, _PD, _PI32]),
     "gbdmrg_plan": (C.c_int, [_P, _I32]),
     "gbdmrg_psi_layout": (C.c_int, [_P, _PI64, _PI64, _PI64]),
@@ -376,6 +377,10 @@ class Context:
     def set_stage1_stacked(self, stacked: bool = True):
         """Stage 1 of later tensor-core work lists over stacked right operands."""
         self._check(self.lib.gbdmrg_set_stage1_stacked(self.h, int(stacked)), "set_stage1_stacked")
+
+    def set_tc_combos(self, on: bool = True, min_terms: int = 100000):
+        """W-contracted sums that feed only the tensor-core sigma and the diagonal on the tensor cores."""
+        self._check(self.lib.gbdmrg_set_tc_combos(self.h, int(on), int(min_terms)), "set_tc_combos")
 
     def plan_params(self):
         """(split tiles per SM, chunk budget MB) of the work lists built next."""

@@ -313,6 +313,14 @@ gbdmrg_status gbdmrg_set_stage1_stacked(gbdmrg_ctx* ctx, int32_t stacked) {
   return guard(ctx, [&] { ctx->c.stage1_stacked = stacked != 0; });
 }
 
+gbdmrg_status gbdmrg_set_tc_combos(gbdmrg_ctx* ctx, int32_t on, int64_t min_terms) {
+  if (!ctx || min_terms < 0) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    ctx->c.tc_combos = on != 0;
+    ctx->c.tc_combo_min_terms = (long)min_terms;
+  });
+}
+
 gbdmrg_status gbdmrg_get_plan_params(gbdmrg_ctx* ctx, double* tiles_per_sm, int32_t* chunk_budget_mb) {
   if (!ctx) return GBDMRG_EINVAL;
   return guard(ctx, [&] {
@@ -352,8 +360,8 @@ gbdmrg_status gbdmrg_plan(gbdmrg_ctx* ctx, int32_t k) {
     if (k < 0 || k + 1 >= c.K) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "two-site position out of range");
     if (!c.left[k].valid || !c.right[k + 2].valid)
       throw gbdmrg::Error(gbdmrg::ST_ESTATE, "environments of bonds k and k+2 are not built");
-    gbdmrg::build_tilde_left(c, c.left[k], k, c.lt);
-    gbdmrg::build_tilde_right(c, c.right[k + 2], k + 1, c.rt);
+    gbdmrg::build_tilde_left(c, c.left[k], k, c.lt, true);
+    gbdmrg::build_tilde_right(c, c.right[k + 2], k + 1, c.rt, true);
     gbdmrg::build_sigma_plan(c, c.lt, c.rt, k, c.plan);
     gbdmrg::cuda_check(cudaStreamSynchronize(c.stream), "sync");
     c.prepared = k;

@@ -525,7 +525,7 @@ static TildeLists tilde_lists(const MPO& mpo, int site, int nmid, bool by_col) {
   return tl;
 }
 
-static void finish_tilde(Context& c, Env& env, const TildeLists& lists, Tilde& t) {
+static void finish_tilde(Context& c, Env& env, const TildeLists& lists, Tilde& t, bool approx) {
   t.env = &env;
   t.ref.assign(t.nmid, {});
   const size_t n = lists.size();
@@ -591,7 +591,12 @@ static void finish_tilde(Context& c, Env& env, const TildeLists& lists, Tilde& t
   });
   t.combo_flops = flops;
   c.other_flops_total += (double)t.combo_flops;
-  if (!outs.empty()) {
+  if (!outs.empty() && approx && c.tc_combos && c.precision > 0 && (long)terms.size() >= c.tc_combo_min_terms) {
+    std::vector<int> out_cls(outs.size());
+    for (size_t i = 0; i < n; ++i)
+      if (oidx[i] >= 0) out_cls[(size_t)oidx[i]] = cls_of[i];
+    combos_tc(c, env, outs, terms, out_cls);
+  } else if (!outs.empty()) {
     DArr<ComboOut> d_o;
     DArr<ComboTerm> d_t;
     d_o.upload(outs, c.stream);
@@ -602,14 +607,14 @@ static void finish_tilde(Context& c, Env& env, const TildeLists& lists, Tilde& t
   }
 }
 
-void build_tilde_left(Context& c, Env& L, int site, Tilde& t) {
+void build_tilde_left(Context& c, Env& L, int site, Tilde& t, bool approx) {
   t.nmid = (int)c.mpo.bonds[site + 1].size();
-  finish_tilde(c, L, tilde_lists(c.mpo, site, t.nmid, true), t);
+  finish_tilde(c, L, tilde_lists(c.mpo, site, t.nmid, true), t, approx);
 }
 
-void build_tilde_right(Context& c, Env& R, int site, Tilde& t) {
+void build_tilde_right(Context& c, Env& R, int site, Tilde& t, bool approx) {
   t.nmid = (int)c.mpo.bonds[site].size();
-  finish_tilde(c, R, tilde_lists(c.mpo, site, t.nmid, false), t);
+  finish_tilde(c, R, tilde_lists(c.mpo, site, t.nmid, false), t, approx);
 }
 
 // column sector of a W-contracted operator block whose row sector is `row`
@@ -991,8 +996,9 @@ void prepare_two_site(Context& c, int k) {
     build_tilde_right(c, c.right[j + 1], j, t);
     env_update_right(c, t, c.sites[j], j, c.right[j]);
   }
-  build_tilde_left(c, c.left[k], k, c.lt);
-  build_tilde_right(c, c.right[k + 2], k + 1, c.rt);
+  // these sums feed only the sigma and the diagonal
+  build_tilde_left(c, c.left[k], k, c.lt, true);
+  build_tilde_right(c, c.right[k + 2], k + 1, c.rt, true);
   build_sigma_plan(c, c.lt, c.rt, k, c.plan);
   cuda_check(cudaStreamSynchronize(c.stream), "sync");
   c.prepared = k;
@@ -1549,9 +1555,10 @@ double two_site_step(Context& c, int k, int dir, int M, const DavidsonOpts& o, b
     t0 = t1;
     f0 = f1;
   };
+  // the side that the environment update does not use feeds only the sigma and the diagonal
   Tilde lt, rt;
-  build_tilde_left(c, c.left[k], k, lt);
-  build_tilde_right(c, c.right[k + 2], k + 1, rt);
+  build_tilde_left(c, c.left[k], k, lt, dir == 1);
+  build_tilde_right(c, c.right[k + 2], k + 1, rt, dir == 0);
   lap(0);
   SigmaPlan plan;
   build_sigma_plan(c, lt, rt, k, plan);

@@ -244,6 +244,11 @@ struct Context {
   // (bond state, group) whose operand is the W-contracted right operator over all
   // four x four site blocks of the two groups (absent blocks zero)
   bool stage1_stacked = false;
+  // blocking sums with at least tc_combo_min_terms terms that feed only the
+  // tensor-core sigma and the H_eff diagonal are formed on the tensor cores
+  // (three BF16 slices, FP32 accumulation) instead of the FP64 units
+  bool tc_combos = false;
+  long tc_combo_min_terms = 100000;
   // 0: FP64 grouped GEMMs; 1: tensor cores, one BF16 pass; 2: tensor cores,
   // three BF16 slices (six products, about FP32 accuracy); 3: two BF16 slices
   // (three products)
@@ -270,8 +275,14 @@ void load_mps(Context& c, const char* path);
 
 void env_boundary_left(Context& c, Env& e);
 void env_boundary_right(Context& c, Env& e);
-void build_tilde_left(Context& c, Env& L, int site, Tilde& t);
-void build_tilde_right(Context& c, Env& R, int site, Tilde& t);
+// approx: the sums feed only the tensor-core sigma and the H_eff diagonal, so with
+// tc_combos they may be formed on the tensor cores (about FP32 accuracy)
+void build_tilde_left(Context& c, Env& L, int site, Tilde& t, bool approx = false);
+void build_tilde_right(Context& c, Env& R, int site, Tilde& t, bool approx = false);
+// blocking sums out_i = sum_j coef_ij Op_j of one environment on the tensor cores
+// (engine_mixed.cu); out_cls[i] is the operator class of output i
+void combos_tc(Context& c, Env& env, const std::vector<ComboOut>& outs, const std::vector<ComboTerm>& terms,
+               const std::vector<int>& out_cls);
 void env_update_left(Context& c, Tilde& lt, const SiteT& A, int site, Env& out);
 void env_update_right(Context& c, Tilde& rt, const SiteT& B, int site, Env& out);
 

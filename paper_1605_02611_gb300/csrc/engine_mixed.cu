@@ -881,6 +881,98 @@ float batch_sigma(BatchPlan& b, const double* const* psi, double* const* sigma, 
 }
 
 
+// ---------------------------------------------------------------- blocking sums on the tensor cores
+
+// out_i = sum_j coef_ij Op_j for the operators Op_j of one class (Sec. "Efficient
+// implementation of expectation values": the W contraction with the renormalised
+// operators) as one GEMM per class: A = the class's operators transposed into BF16
+// slices (element-major, operator index contiguous), B = the coefficient matrix in BF16
+// slices, FP32 accumulation, the result gathered into the FP64 outputs.  Three slices
+// carry ~24 significant bits, so the sums have about FP32 accuracy.
+void combos_tc(Context& c, Env& env, const std::vector<ComboOut>& outs, const std::vector<ComboTerm>& terms,
+               const std::vector<int>& out_cls) {
+  const int nsl = 3;
+  DArr<int> err;
+  err.alloc(1, c.stream);
+  cuda_check(cudaMemsetAsync(err.p, 0, sizeof(int), c.stream), "memset");
+  std::vector<std::vector<size_t>> by_cls(env.cls.size());
+  for (size_t i = 0; i < outs.size(); ++i) by_cls[(size_t)out_cls[i]].push_back(i);
+  for (size_t cls = 0; cls < env.cls.size(); ++cls) {
+    const std::vector<size_t>& mine = by_cls[cls];
+    if (mine.empty()) continue;
+    const long nnz = env.cls[cls].nnz;
+    const int K = env.nslot[cls];
+    const int Kp = pad8(K);
+    const int S = (int)mine.size();
+    if (nnz <= 0 || K <= 0) continue;
+    if (nnz > (long)std::numeric_limits<int>::max())
+      throw Error(ST_EINVAL, "tensor-core blocking sums: operator class too large");
+    const double* base = env.data[cls].p;
+    // A: operators transposed, [nnz x Kp] per slice (padding columns zero)
+    DArr<__nv_bfloat16> at, bt;
+    at.alloc((size_t)nnz * Kp * nsl, c.stream);
+    cuda_check(cudaMemsetAsync(at.p, 0, at.n * sizeof(__nv_bfloat16), c.stream), "memset");
+    std::vector<ConvJob> jobs;
+    jobs.reserve((size_t)K + 1);
+    for (int j = 0; j < K; ++j)
+      jobs.push_back({base + (long)j * nnz, at.p + j, nnz * Kp, (int)nnz, 1, 1, Kp, nsl, 1.0, 1});
+    // B: coefficients [S x Kp] (a repeated operator in one sum adds up)
+    std::vector<double> coef((size_t)S * Kp, 0.0);
+    for (int sidx = 0; sidx < S; ++sidx) {
+      const ComboOut& o = outs[mine[(size_t)sidx]];
+      for (int t = o.t0; t < o.t1; ++t) {
+        const long d = (long)(terms[(size_t)t].in - base);
+        if (d < 0 || d % nnz != 0 || d / nnz >= K)
+          throw Error(ST_ECUDA, "internal: blocking-sum term outside its operator class");
+        coef[(size_t)sidx * Kp + (size_t)(d / nnz)] += terms[(size_t)t].coef;
+      }
+    }
+    DArr<double> coef_d;
+    coef_d.upload(coef, c.stream);
+    bt.alloc((size_t)S * Kp * nsl, c.stream);
+    jobs.push_back({coef_d.p, bt.p, (long)S * Kp, S, Kp, Kp, Kp, nsl, 1.0, Kp});
+    {
+      DArr<ConvJob> dj;
+      dj.upload(jobs, c.stream);
+      launch_conv(dj, (int)jobs.size(), std::max<long>(nnz, (long)S * Kp), c.stream);
+    }
+    // C^T [S x nnz] in FP32: element (e, i) of the product goes to ct[i * nnz + e]
+    DArr<float> ct;
+    ct.alloc((size_t)S * nnz, c.stream);
+    TcBuilder g;
+    TcTask task{};
+    task.C = ct.p;
+    task.ldc = (int)nnz;
+    task.m = (int)nnz;
+    task.n = S;
+    task.beta = 0;
+    task.trans = 1;
+    g.begin(task);
+    g.term(at.p, nnz * Kp, Kp, bt.p, (long)S * Kp, Kp, K, false, nsl);
+    g.end();
+    DArr<TcTile> d_tiles;
+    DArr<TcTask> d_tasks;
+    DArr<TcTerm> d_terms;
+    d_tiles.upload(g.tiles, c.stream);
+    d_tasks.upload(g.tasks, c.stream);
+    d_terms.upload(g.terms, c.stream);
+    cuda_check(launch_gemm_bf16_tc(d_tiles.p, (int)g.tiles.size(), d_tasks.p, d_terms.p, err.p, c.stream, nsl),
+               "tc blocking sums");
+    // gather into the FP64 outputs (a plain copy: one column per job)
+    std::vector<UnconvJob> uj;
+    uj.reserve((size_t)S);
+    for (int sidx = 0; sidx < S; ++sidx)
+      uj.push_back({ct.p + (long)sidx * nnz, outs[mine[(size_t)sidx]].out, (int)nnz, 1, 1});
+    DArr<UnconvJob> du;
+    du.upload(uj, c.stream);
+    launch_unconv(du.p, (int)uj.size(), nnz, c.stream);
+    cuda_check(cudaStreamSynchronize(c.stream), "sync");
+  }
+  int h = 0;
+  cuda_check(cudaMemcpy(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost), "d2h");
+  if (h) throw Error(ST_ETIMEOUT, "tensor-core GEMM: a bounded wait ran out");
+}
+
 // ---------------------------------------------------------------- autotuner
 
 TuneChoice autotune_plans(const std::vector<Context*>& ctxs, const std::vector<double>& splits,
