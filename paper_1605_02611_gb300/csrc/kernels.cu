@@ -105,7 +105,13 @@ __global__ void fill_kernel(double* p, long n, double v) {
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) p[e] = v;
 }
 
+// y = a x + b y; with b == 0 y is not read (it may be uninitialised, and 0 * NaN is NaN)
 __global__ void axpby_kernel(long n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+  if (b == 0.0) {
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+      y[e] = a * x[e];
+    return;
+  }
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
     y[e] = a * x[e] + b * y[e];
 }

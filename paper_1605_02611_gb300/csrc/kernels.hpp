@@ -62,7 +62,8 @@ void launch_copy(const CopyJob* d_jobs, int njobs, int max_elems, cudaStream_t s
 void launch_fill(double* p, long n, double v, cudaStream_t s);
 
 // vector ops (FP64, length n)
-void launch_axpby(long n, double a, const double* x, double b, double* y, cudaStream_t s);  // y = a x + b y
+// y = a x + b y (b == 0: y is only written)
+void launch_axpby(long n, double a, const double* x, double b, double* y, cudaStream_t s);
 // dots[j] = <V_j, x> for j < m, V row-major [m][n]; result written to d_out[m] (deterministic)
 void launch_multidot(const double* V, long ldv, int m, const double* x, long n, double* d_part,
                      int nblk, double* d_out, cudaStream_t s);
