@@ -233,8 +233,8 @@ def run_ours(args, rank, world, local_rank):
     ctx.set_precision(args.precision)
     if args.stage1_stacked:
         ctx.set_stage1_stacked(True)
-    if args.tc_combos:
-        ctx.set_tc_combos(True)
+    if args.fp64_w_sums:
+        ctx.set_tc_combos(False)
     ctx.set_mps(T, [b.labels() for b in bonds])
     del T
     ctx.prepare(k)
@@ -366,7 +366,8 @@ def run_ours(args, rank, world, local_rank):
                    "psi_nnz": nnz, "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (no flush)",
                    "setup_s": round(setup_s, 1), "setup_launches": int(setup_launches),
                    "stage1": "stacked" if args.stage1_stacked else "per-sector",
-                   "w_sums": "tensor cores where only the sigma uses them" if args.tc_combos else "fp64"},
+                   "w_sums": "fp64" if args.fp64_w_sums else
+                   "tensor cores (bf16x3) for sums of >= 1e5 terms that feed only the sigma, fp64 otherwise"},
         "sigma_tflops": achieved_alg, "sigma_calls": sig_calls, "fp64_comparison": fp64_cmp,
         "step_phase_s": phases,
         "step_phase_tflops": phase_tf,
@@ -529,8 +530,9 @@ def main():
                     help="> 0: batched H_eff.psi over this many independent problems instead of the step bench")
     ap.add_argument("--stage1-stacked", action="store_true",
                     help="tensor-core sigma with stacked right operands in stage 1")
-    ap.add_argument("--tc-combos", action="store_true",
-                    help="W-contracted sums that feed only the tensor-core sigma on the tensor cores")
+    ap.add_argument("--fp64-w-sums", action="store_true",
+                    help="form every W-contracted sum on the FP64 units (default: large sums that feed only "
+                         "the tensor-core sigma run on the tensor cores)")
     ap.add_argument("--autotune", action="store_true",
                     help="with --batched: choose the split-K granularity of the fused work lists by timing")
     ap.add_argument("--profile-sigma", type=int, default=0,

@@ -147,7 +147,8 @@ gbdmrg_status gbdmrg_set_stage1_stacked(gbdmrg_ctx* ctx, int32_t stacked);
  * whose results feed only the tensor-core H_eff.psi and the H_eff diagonal (the
  * side that the environment update of the step does not use), is formed as one
  * GEMM per operator class in three BF16 slices with FP32 accumulation (about
- * FP32 accuracy) instead of on the FP64 units.  Default off, min_terms 100000.
+ * FP32 accuracy) instead of on the FP64 units.  Default on, min_terms 100000
+ * (in practice the sums of the switch site K/2 of larger problems).
  * EINVAL for a null context or a negative min_terms. */
 gbdmrg_status gbdmrg_set_tc_combos(gbdmrg_ctx* ctx, int32_t on, int64_t min_terms);
 /* Current plan parameters (either pointer may be NULL). */

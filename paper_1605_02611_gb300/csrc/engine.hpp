@@ -247,7 +247,7 @@ struct Context {
   // blocking sums with at least tc_combo_min_terms terms that feed only the
   // tensor-core sigma and the H_eff diagonal are formed on the tensor cores
   // (three BF16 slices, FP32 accumulation) instead of the FP64 units
-  bool tc_combos = false;
+  bool tc_combos = true;
   long tc_combo_min_terms = 100000;
   // 0: FP64 grouped GEMMs; 1: tensor cores, one BF16 pass; 2: tensor cores,
   // three BF16 slices (six products, about FP32 accuracy); 3: two BF16 slices
