@@ -256,7 +256,19 @@ def run_ours(args, rank, world, local_rank):
     def step(psi_in=None, want=False):
         return ctx.step(k, 0, M, 1e-14, dav, psi_in=psi_in, want_psi=want)
 
-    for _ in range(args.warmup):
+    # first warm-up step; should the tensor-core W-contracted sums report an error, the
+    # run continues with FP64 sums and says so in the line
+    w_sums_failed = None
+    try:
+        step()
+    except G.GbdmrgError as exc:
+        if args.fp64_w_sums:
+            raise
+        w_sums_failed = str(exc)
+        print(f"warning: tensor-core W-contracted sums failed, using FP64 sums: {exc}", file=sys.stderr)
+        ctx.set_tc_combos(False)
+        step()
+    for _ in range(args.warmup - 1):
         step()
     torch.cuda.synchronize()
     c0 = ctx.counters()
@@ -367,7 +379,8 @@ def run_ours(args, rank, world, local_rank):
                    "setup_s": round(setup_s, 1), "setup_launches": int(setup_launches),
                    "stage1": "stacked" if args.stage1_stacked else "per-sector",
                    "w_sums": "fp64" if args.fp64_w_sums else
-                   "tensor cores (bf16x3) for sums of >= 1e5 terms that feed only the sigma, fp64 otherwise"},
+                   (f"fp64 (tensor-core sums failed: {w_sums_failed})" if w_sums_failed else
+                    "tensor cores (bf16x3) for sums of >= 1e5 terms that feed only the sigma, fp64 otherwise")},
         "sigma_tflops": achieved_alg, "sigma_calls": sig_calls, "fp64_comparison": fp64_cmp,
         "step_phase_s": phases,
         "step_phase_tflops": phase_tf,
