@@ -113,3 +113,21 @@ def test_prenormrule_cross_term_uses_w(system):
             assert np.abs(with_w - full).max() < 1e-13, (k, p, q)
             bad = max(bad, np.abs(with_v - full).max())
     assert bad > 1e-3
+
+
+def test_unique_two_electron_integrals(system):
+    """Appendix form of the two-body part: (1/2) sum v_pqrs a+_p a+_q a_r a_s equals
+    sum g_pqrs a+_p a+_q a_r a_s with g_pqrs = w_pqrs for p < q, r < s and 0 otherwise."""
+    s = system
+    v, w, cd, c = s["v"], s["w"], s["cd"], s["c"]
+    h2 = np.zeros_like(s["H"])
+    g2 = np.zeros_like(s["H"])
+    for p, q, r, u in itertools.product(range(N_SO), repeat=4):
+        op = None
+        if v[p, q, r, u]:
+            op = cd[p] @ cd[q] @ c[r] @ c[u]
+            h2 += 0.5 * v[p, q, r, u] * op
+        if p < q and r < u and w[p, q, r, u]:
+            g2 += w[p, q, r, u] * (op if op is not None else cd[p] @ cd[q] @ c[r] @ c[u])
+    assert np.abs(h2).max() > 1e-3
+    assert np.abs(h2 - g2).max() < 1e-12
