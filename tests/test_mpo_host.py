@@ -79,8 +79,8 @@ def test_header_symbols_exported(lib):
 
 
 def test_plan_knobs_reject_bad_arguments(lib):
-    """The split-K knob and the autotuner reject null contexts and empty lists on
-    the host, before any device work."""
+    """The plan knobs and the autotuner reject null contexts and empty lists on the
+    host, before any device work."""
     import ctypes as C
     EINVAL = 1
     assert lib.gbdmrg_set_split(None, 4.0) == EINVAL
@@ -89,6 +89,8 @@ def test_plan_knobs_reject_bad_arguments(lib):
     assert lib.gbdmrg_autotune(0, none, 3, None, 0, None, 0, None, None, None) == EINVAL
     assert lib.gbdmrg_autotune(1, none, 3, None, 0, None, 0, None, None, None) == EINVAL
     assert lib.gbdmrg_autotune(1, None, 3, None, 0, None, 0, None, None, None) == EINVAL
+    assert lib.gbdmrg_set_stage1_stacked(None, 1) == EINVAL
+    assert lib.gbdmrg_set_tc_combos(None, 1, 0) == EINVAL
 
 
 def test_context_without_gpu_fails_loudly(lib):
