@@ -539,7 +539,9 @@ static void finish_tilde(Context& c, Env& env, const TildeLists& lists, Tilde& t
       const int cls = env.st_cls[L[0].first];
       for (size_t j = 0; j < len; ++j)
         if (env.st_cls[L[j].first] != cls) throw Error(ST_ECUDA, "internal: mixed operator classes in a blocking sum");
-      cls_of[i] = cls;
+      // a class without elements (no sector pair at this bond) contributes nothing: the
+      // slot stays empty, so that no zero-size sum shares an address with another one
+      if (env.cls[cls].nnz > 0) cls_of[i] = cls;
     }
   });
   // slots with several terms become materialised sums: their output offsets, output
@@ -550,7 +552,7 @@ static void finish_tilde(Context& c, Env& env, const TildeLists& lists, Tilde& t
   int nouts = 0;
   for (size_t i = 0; i < n; ++i) {
     const size_t len = lists.len(i);
-    if (len > 1) {
+    if (len > 1 && cls_of[i] >= 0) {
       off[i] = (long)total;
       total += env.cls[cls_of[i]].nnz;
       tstart[i] = (long)nterms;
@@ -567,7 +569,7 @@ static void finish_tilde(Context& c, Env& env, const TildeLists& lists, Tilde& t
     long my_mx = 0, my_flops = 0;
     for (size_t i = lo; i < hi; ++i) {
       const size_t len = lists.len(i);
-      if (!len) continue;
+      if (!len || cls_of[i] < 0) continue;
       const auto* L = lists.at(i);
       const int cls = cls_of[i];
       TRef& r = t.ref[i / 16][i % 16];
