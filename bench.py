@@ -237,7 +237,24 @@ def run_ours(args, rank, world, local_rank):
         ctx.set_tc_combos(False)
     ctx.set_mps(T, [b.labels() for b in bonds])
     del T
-    ctx.prepare(k)
+    # should the tensor-core W-contracted sums report an error (here or in the first
+    # warm-up step), the run continues with FP64 sums and says so in the line
+    w_sums_failed = None
+
+    def with_fp64_fallback(fn):
+        nonlocal w_sums_failed
+        try:
+            return fn()
+        except G.GbdmrgError as exc:
+            if args.fp64_w_sums or w_sums_failed is not None:
+                raise
+            w_sums_failed = str(exc)
+            print(f"warning: tensor-core W-contracted sums failed, using FP64 sums: {exc}", file=sys.stderr)
+            ctx.set_tc_combos(False)
+            ctx.prepare(k)
+            return fn()
+
+    with_fp64_fallback(lambda: ctx.prepare(k))
     nnz = ctx.nnz
     setup_s = time.perf_counter() - t_setup
     setup_launches = G.kernel_launches()
@@ -256,18 +273,7 @@ def run_ours(args, rank, world, local_rank):
     def step(psi_in=None, want=False):
         return ctx.step(k, 0, M, 1e-14, dav, psi_in=psi_in, want_psi=want)
 
-    # first warm-up step; should the tensor-core W-contracted sums report an error, the
-    # run continues with FP64 sums and says so in the line
-    w_sums_failed = None
-    try:
-        step()
-    except G.GbdmrgError as exc:
-        if args.fp64_w_sums:
-            raise
-        w_sums_failed = str(exc)
-        print(f"warning: tensor-core W-contracted sums failed, using FP64 sums: {exc}", file=sys.stderr)
-        ctx.set_tc_combos(False)
-        step()
+    with_fp64_fallback(step)
     for _ in range(args.warmup - 1):
         step()
     torch.cuda.synchronize()
