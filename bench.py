@@ -48,6 +48,12 @@ WORKLOADS = {
 # full Fock space, so it can only take K <= 10; this is the largest sample of
 # the same kind of step (central two-site sigma) it finishes in seconds
 ORACLE_SAMPLE = dict(K=10, N=10, two_sz=0, M=1000, k=3, seed=1607, spread=0.5)
+# Algorithmic flops of one H_eff.psi of that sample: the sum of 2mnk over the non-zero
+# quantum-number blocks of the MPO contraction (the count every TFLOP/s figure here
+# uses).  The oracle builds no MPO, so it cannot count them itself; the value is
+# stored so that the oracle arm runs without the CUDA library, and
+# tests/test_bench_contract.py checks it against the library's host-side count.
+ORACLE_SAMPLE_FLOPS = 2928679808.0
 
 
 def _measured_peaks():
@@ -114,7 +120,6 @@ class ClockSampler:
 def oracle_sample(seconds: float = 12.0):
     """Time the CPU oracle's sigma (P^T H P psi) on the bounded sample; returns
     (sigma flops of the sample, seconds per sigma, calls)."""
-    import paper_1605_02611_gb300 as G
     from oracle import mps as omps
     from paper_1605_02611_gb300 import synth
     s = ORACLE_SAMPLE
@@ -123,7 +128,7 @@ def oracle_sample(seconds: float = 12.0):
     k = s["k"]
     psi = synth.random_psi(bonds[k], bonds[k + 2], s["seed"] + 2)
     Na = Nb = s["N"] // 2
-    flops = G.sigma_flops_host(h, eri, s["N"], s["two_sz"], k, bonds[k].labels(), bonds[k + 2].labels())
+    flops = ORACLE_SAMPLE_FLOPS
     P = omps.TwoSiteProjector(T, k, Na, Nb)
     omps.sigma(T, k, psi, h, eri, Na, Nb, P)  # warm-up (string tables)
     t0 = time.perf_counter()
@@ -191,7 +196,6 @@ def run_reference(args, rank, world):
     """Oracle arm: the CPU oracle on a bounded sample of the workload (rank 0 only)."""
     if rank != 0:
         return
-    import paper_1605_02611_gb300 as G  # noqa: F401  (host-only flop count of the sample)
     times = []
     flops = None
     for i in range(args.warmup + args.steps):
@@ -246,7 +250,10 @@ def run_ours(args, rank, world, local_rank):
         try:
             return fn()
         except G.GbdmrgError as exc:
-            if args.fp64_w_sums or w_sums_failed is not None:
+            # only the errors the tensor-core sums report on purpose (an operator class
+            # too large for them, a bounded wait that ran out, no memory for their
+            # operands); a CUDA fault or anything else ends the run
+            if args.fp64_w_sums or w_sums_failed is not None or exc.status not in ("EINVAL", "ETIMEOUT", "ENOMEM"):
                 raise
             w_sums_failed = str(exc)
             print(f"warning: tensor-core W-contracted sums failed, using FP64 sums: {exc}", file=sys.stderr)
@@ -342,8 +349,11 @@ def run_ours(args, rank, world, local_rank):
             ctx.sigma_device(x.data_ptr(), y_tc.data_ptr())
         except Exception as exc:  # reported in the line, never fatal for the bench
             checks["error"] = f"tensor-core sigma: {exc}"
-        # the same H_eff.psi on the FP64 units (one call), for the mixed/FP64 speed-up
+        # the same H_eff.psi on the FP64 units (one call), for the mixed/FP64 speed-up;
+        # the W-contracted sums are rebuilt on the FP64 units too, so the comparison is
+        # against an operator formed entirely in FP64
         ctx.set_precision(0)
+        ctx.set_tc_combos(False)
         ctx.plan(k)
         fl64 = ctx.sigma_device(x.data_ptr(), y.data_ptr())
         ms64 = ctx.sigma_timing(1, x.data_ptr(), y.data_ptr())
@@ -369,12 +379,16 @@ def run_ours(args, rank, world, local_rank):
         dtype = "f64"
     else:
         peak = peaks["bf16_tflops_sustained"]
-        ach = achieved_alg * nprod if achieved_alg else None
-        roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": (ach / peak) if ach else None, "traffic": None,
+        # achieved = ALGORITHMIC flops (2mnk over non-zero blocks, no padding, no extra
+        # split-precision products) / event-timed sigma time; the products the tensor
+        # cores actually execute for the slices are reported beside it, not in frac
+        roof = {"bound": "tensor", "achieved": achieved_alg, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved_alg / peak) if achieved_alg else None, "traffic": None,
                 "kernel": "gemm_bf16_tc_kernel (sigma stages 1+2)",
-                "peak_note": f"{src} bf16 dense, sustained (kernel timed inside a long step); achieved counts the "
-                             f"{nprod} tensor-core product(s) per algorithmic multiply-add"}
+                "executed_tflops": achieved_alg * nprod if achieved_alg else None,
+                "products_per_multiply_add": nprod,
+                "peak_note": f"{src} bf16 dense, sustained (kernel timed inside a long step); achieved and frac "
+                             f"count algorithmic flops only"}
         dtype = {1: "bf16", 2: "bf16x3", 3: "bf16x2"}[args.precision]
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -518,8 +532,10 @@ def run_batched(args):
             "flops_per_batch": fl, "sequential_ms": seq_ms, "batched_eager_ms": eager_ms, "batched_graph_ms": graph_ms,
             "sequential_tflops": fl / seq_ms / 1e9, "batched_tflops": fl / graph_ms / 1e9,
             "speedup_over_sequential": seq_ms / graph_ms,
-            "tensor_frac": fl * nprod / graph_ms / 1e9 / peaks["bf16_tflops_sustained"],
-            "peak_note": f"{src} bf16 sustained; {nprod} tensor-core products per algorithmic multiply-add",
+            "tensor_frac": fl / graph_ms / 1e9 / peaks["bf16_tflops_sustained"],
+            "executed_tensor_frac": fl * nprod / graph_ms / 1e9 / peaks["bf16_tflops_sustained"],
+            "peak_note": f"{src} bf16 sustained; tensor_frac counts algorithmic flops, executed_tensor_frac the "
+                         f"{nprod} tensor-core products per algorithmic multiply-add",
             "gpu_launches_per_batch": launches / max(1, args.warmup + args.steps), "setup_s": setup_s,
             "autotune": tune, "clocks": clk}
     print(json.dumps(line), flush=True)

@@ -202,16 +202,19 @@ gbdmrg_status gbdmrg_diag(gbdmrg_ctx* ctx, double* diag, int32_t on_device);
 /* Diagonal of H_eff for the prepared sites, like gbdmrg_diag with on_device = 1,
  * but without allocating any device memory.  The paper has no counterpart: this
  * entry exists for callers that cannot call cudaMalloc/cudaFree at that moment
- * (work recorded while a stream is being captured into a CUDA graph, or inside a
- * framework whose memory manager owns the device).  Every scratch buffer it needs
- * is carved from one fixed 32 MiB array compiled into the library (held by each
- * GPU that loads the library until the process exits); problems that need more
+ * (for example inside a framework whose memory manager owns the device and
+ * forbids allocations between its own phases).  Every scratch buffer it needs is
+ * carved from one fixed 32 MiB array compiled into the library (held by each GPU
+ * that loads the library until the process exits); problems that need more
  * return GBDMRG_EINVAL with the required size in gbdmrg_last_error.  The first
  * call on a device looks up that array's device address (cudaGetSymbolAddress),
  * so make it with the context's device current and before any stream capture.
- * All calls share the one array: calls that overlap on the GPU (several streams
- * or host threads at once) race.  diag_dev: device pointer, nnz doubles of the
- * packed layout.  Requires gbdmrg_prepare (which does allocate) beforehand. */
+ * All calls share the one array (and one host staging buffer): calls whose GPU
+ * work overlapped would race, even for different GPUs, so each call holds a
+ * process-wide lock until its own GPU work has finished (it synchronises the
+ * context stream before returning) and calls from several host threads run one
+ * after another.  diag_dev: device pointer, nnz doubles of the packed layout.
+ * Requires gbdmrg_prepare (which does allocate) beforehand. */
 gbdmrg_status gbdmrg_diag_noalloc(gbdmrg_ctx* ctx, double* diag_dev);
 /* Average device time (ms) of the sigma work of the last n calls of gbdmrg_sigma
  * with on_device != 0, timed with CUDA events on the context stream. */

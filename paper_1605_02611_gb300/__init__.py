@@ -115,7 +115,11 @@ def load(path: str = LIB_PATH) -> C.CDLL:
 
 
 class GbdmrgError(RuntimeError):
-    pass
+    """A library call returned a non-zero status; ``status`` is its name (e.g. "ECUDA")."""
+
+    def __init__(self, msg: str, status: str | None = None):
+        super().__init__(msg)
+        self.status = status
 
 
 def _dptr(a: np.ndarray):
@@ -326,7 +330,7 @@ class Context:
     def _check(self, st: int, what: str):
         if st != 0:
             msg = self.lib.gbdmrg_last_error(self.h).decode()
-            raise GbdmrgError(f"{what}: {STATUS.get(st, st)}: {msg}")
+            raise GbdmrgError(f"{what}: {STATUS.get(st, st)}: {msg}", STATUS.get(st, str(st)))
 
     # ---- MPO
     def mpo_bond_dims(self) -> np.ndarray:

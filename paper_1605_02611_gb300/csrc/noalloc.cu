@@ -1,22 +1,24 @@
 // Diagonal of H_eff without any device allocation.
 //
 // Some callers cannot allocate device memory at the time they need the
-// preconditioner input: code running while a CUDA stream is being captured
-// into a graph, or inside a framework whose memory manager owns the whole
-// device and forbids cudaMalloc/cudaFree between its own phases.  For them
-// this variant of compute_diag keeps every scratch buffer it needs (the
-// gathered diagonals of the W-contracted operators and the GEMM work lists)
-// in one file-scope device array of fixed size, NOALLOC_SCRATCH_BYTES.  The
-// array lives in the module image, so every GPU that loads the library holds
-// it until the process exits.
+// preconditioner input: for example code inside a framework whose memory
+// manager owns the whole device and forbids cudaMalloc/cudaFree between its
+// own phases.  For them this variant of compute_diag keeps every scratch
+// buffer it needs (the gathered diagonals of the W-contracted operators and
+// the GEMM work lists) in one file-scope device array of fixed size,
+// NOALLOC_SCRATCH_BYTES.  The array lives in the module image, so every GPU
+// that loads the library holds it until the process exits.
 //
 // Host code cannot use the array's name as a device address (in host code it
 // names a host-side stand-in); the device address is obtained once per device
 // with cudaGetSymbolAddress, with that device current, by the first call made
 // on that device.  That first call should therefore come before any stream
-// capture.  All calls share the one array and it keeps the contents of the
-// last call: everything that must start at zero is cleared on every call, and
-// calls whose work overlaps on the GPU (two streams, two host threads) race.
+// capture.  All calls share the one array (and one host staging buffer for the
+// work lists) and it keeps the contents of the last call: everything that must
+// start at zero is cleared on every call.  Calls whose GPU work overlapped would
+// race on the shared array, even calls for different GPUs (they share the host
+// staging); a process-wide lock held from staging until the call's own GPU work
+// has finished makes calls from several host threads run one after another.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,6 +40,8 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 void* g_scratch_dev[kMaxDevices] = {nullptr};
+// held by a call from staging its work lists until its GPU work has finished
+std::mutex g_call_mu;
 
 // host staging for the descriptor lists (also fixed size: no host allocation)
 unsigned char g_stage[NOALLOC_SCRATCH_BYTES];
@@ -112,6 +116,7 @@ void compute_diag_noalloc(Context& c, double* diag) {
     throw Error(ST_EINVAL, "problem too large for the no-allocation diagonal: needs " + std::to_string(need) +
                                " bytes of scratch, the fixed scratch holds " +
                                std::to_string(NOALLOC_SCRATCH_BYTES) + " bytes");
+  std::lock_guard<std::mutex> call_lock(g_call_mu);
   unsigned char* base = (unsigned char*)scratch_address();
   double* DL = (double*)base;
   double* DR = (double*)(base + dl_bytes);
@@ -146,9 +151,11 @@ void compute_diag_noalloc(Context& c, double* diag) {
   GemmTask* hk = (GemmTask*)(g_stage + jobs_bytes + tile_bytes);
   GemmTerm* hm = (GemmTerm*)(g_stage + jobs_bytes + tile_bytes + task_bytes);
   size_t t = 0;
+  double flops = 0;
   for (size_t pb = 0; pb < nblk; ++pb) {
     const Block& ob = P.blocks[pb];
     const int n1 = P.b1[pb], n2 = P.b2[pb];
+    flops += 2.0 * ob.rows * ob.cols * nz;  // counted like compute_diag's grouped GEMM
     hk[pb] = {diag + ob.off, ob.cols, ob.rows, ob.cols, 0, (int)pb, (int)pb + 1};
     hm[pb] = {DL + ((size_t)n1 * Lb.total + Lb.off[ob.rs]) * nz, DR + ((size_t)n2 * Rb.total + Rb.off[ob.cs]) * nz, nz,
               nz, nz, 0, 1.0};
@@ -164,6 +171,7 @@ void compute_diag_noalloc(Context& c, double* diag) {
   cuda_check(cudaGetLastError(), "gemm launch");
   // the host staging buffer is reused by the next call: wait for the copy and the kernels
   cuda_check(cudaStreamSynchronize(c.stream), "sync");
+  c.other_flops_total += flops;
 }
 
 }  // namespace gbdmrg

@@ -43,3 +43,30 @@ def test_library_arm_needs_a_gpu():
     p = _run("--steps", "1", "--warmup", "0", timeout=120)
     assert p.returncode != 0
     assert not [ln for ln in p.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_reference_arm_does_not_load_the_library():
+    """The oracle arm times the CPU oracle alone: libgbdmrg.so stays unloaded."""
+    code = ("import runpy, sys; sys.argv = ['bench.py', '--impl', 'reference', '--steps', '1', '--warmup', '0']; "
+            "runpy.run_path('bench.py', run_name='__main__'); "
+            "maps = open('/proc/self/maps').read(); "
+            "assert 'libgbdmrg' not in maps, 'library loaded by the oracle arm'")
+    p = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert p.returncode == 0, p.stderr[-2000:]
+
+
+def test_oracle_sample_flops_match_the_library_count():
+    """The stored algorithmic flop count of the oracle sample equals the library's host-side count."""
+    import importlib.util
+
+    import paper_1605_02611_gb300 as G
+    from paper_1605_02611_gb300 import synth
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    s = bench.ORACLE_SAMPLE
+    h, eri = synth.integrals(s["K"], s["seed"])
+    bonds, _ = synth.random_mps(s["K"], s["N"], s["two_sz"], s["M"], s["seed"] + 1, s["spread"])
+    k = s["k"]
+    fl = G.sigma_flops_host(h, eri, s["N"], s["two_sz"], k, bonds[k].labels(), bonds[k + 2].labels())
+    assert fl == bench.ORACLE_SAMPLE_FLOPS

@@ -71,3 +71,24 @@ def test_truncation_rule_keeps_multiplets():
     assert [x[:2] for x in dmrg.truncation_select(lams, 2)] == [(0.5, 0)]
     assert len(dmrg.truncation_select(lams, 3)) == 3
     assert len(dmrg.truncation_select(lams, 10)) == 4
+
+
+@pytest.mark.parametrize("K,N,two_sz,M", [(5, 5, 1, 9), (6, 6, 0, 12), (6, 4, 2, 7)])
+def test_right_canonicalize_keeps_state_and_gauge(K, N, two_sz, M):
+    """Bringing the start MPS to right-canonical form is a change of gauge only:
+    the contracted state is unchanged, every site k >= 2 becomes
+    right-orthonormal (sum over n, r of A^n[l, r] A^n[l', r] = delta_ll'), and
+    the quantum-number block structure of every tensor survives."""
+    bonds, T = synth.random_mps(K, N, two_sz, M, 40 + K)
+    lab = [b.labels() for b in bonds]
+    T2 = dmrg.right_canonicalize(T, lab)
+    before, after = mps.full_state(T), mps.full_state(T2)
+    assert np.abs(after - before).max() < 1e-12 * np.abs(before).max()
+    for k in range(2, K):
+        A = T2[k].reshape(T2[k].shape[0], -1)
+        assert np.allclose(A @ A.T, np.eye(A.shape[0]), atol=1e-12)
+    for k in range(K):
+        # entries outside the allowed (q_l + q(n) = q_r) pattern stay exactly zero
+        q = lab[k][:, None, None, :] + mps.LOCAL_QN[None, :, None, :]
+        allowed = np.all(q == lab[k + 1][None, None, :, :], axis=-1)
+        assert np.all(T2[k][~allowed] == 0.0)

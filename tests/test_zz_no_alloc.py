@@ -1,8 +1,8 @@
 """The no-allocation diagonal entry point (gbdmrg_diag_noalloc) through the C-ABI.
 
 It serves callers that cannot allocate device memory when they need the
-Davidson preconditioner input (e.g. while capturing a CUDA graph): all its
-scratch sits in a fixed array inside the library.  It must give the same
+Davidson preconditioner input (e.g. inside a framework whose memory manager
+owns the device): all its scratch sits in a fixed array inside the library.  It must give the same
 diagonal as gbdmrg_diag, call after call, and refuse problems whose scratch
 would not fit.  This file is collected last on purpose.
 """
@@ -17,13 +17,19 @@ from gpu_util import context_with_mps, rel_err, require_gpu
 pytestmark = pytest.mark.gpu
 
 
-def test_diag_noalloc_matches_diag_twice():
+@pytest.mark.parametrize("K,M,k", [
+    (8, 60, 3),      # every psi block inside one 64 x 64 GEMM tile
+    (10, 1000, 3),   # blocks of 100 columns: several tiles per block, ragged tails
+])
+def test_diag_noalloc_matches_diag_twice(K, M, k):
     torch = require_gpu()
-    K, N, M, k = 8, 8, 60, 3
+    N = K
     h, eri = synth.integrals(K, 91)
     bonds, T = synth.random_mps(K, N, 0, M, 92)
     ctx = context_with_mps(h, eri, N, 0, bonds, T)
     ctx.prepare(k)
+    if K == 10:
+        assert max(ctx.layout[:, 1].max(), ctx.layout[:, 5].max()) > 64
     ref = ctx.diag()
     for _ in range(2):
         out = torch.full((ctx.nnz,), float("nan"), device="cuda", dtype=torch.float64)
