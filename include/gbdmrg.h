@@ -91,9 +91,26 @@ gbdmrg_status gbdmrg_get_bond(gbdmrg_ctx* ctx, int32_t bond, int32_t* D, int32_t
  * BF16 pass with FP32 accumulation; 2 = tensor cores, every operand split in
  * three BF16 slices and the six leading slice products accumulated in FP32
  * (about FP32 accuracy); 3 = tensor cores, two BF16 slices per operand and the
- * three leading products (operands to ~2^-16 relative).  Environments,
+ * three leading products (operands to ~2^-16 relative); 4 = tensor cores, one
+ * BF16 pass with FP32 accumulation on the TMA-staged work lists (stage 1 of
+ * H_eff.psi, X_beta = psi Rt_beta^T of Eq. Hpartition's right factor, as one
+ * dense GEMM per quantum-number group of the cut over all bond states, its
+ * operands copied by the Tensor Memory Accelerator from a few large matrices;
+ * stage 2 as long contractions over the operator terms).  Environments,
  * Davidson, decimation stay FP64. */
 gbdmrg_status gbdmrg_set_precision(gbdmrg_ctx* ctx, int32_t precision);
+
+/* Device memory (MB) for the X intermediates of the precision-4 work lists
+ * (default 65536): the bond states are processed in chunks whose intermediates
+ * fit this budget (each chunk one stage-1 and one stage-2 launch).  Takes effect
+ * at the next gbdmrg_prepare / gbdmrg_plan.  EINVAL for megabytes <= 0. */
+gbdmrg_status gbdmrg_set_tma_budget(gbdmrg_ctx* ctx, int64_t megabytes);
+/* Work-list statistics of the prepared precision-4 H_eff.psi (zeros for other
+ * precisions): out[0] stage-1 tiles, [1] stage-1 64-wide K steps, [2] stage-2
+ * tiles, [3] stage-2 K steps, [4] stage-1 and [5] stage-2 tensor-core flops as
+ * executed (128-row tiles, blocks padded to 16), [6] bytes of the X
+ * intermediates per chunk, [7] bytes of the stacked right operators, [8] chunks. */
+gbdmrg_status gbdmrg_plan_stats(gbdmrg_ctx* ctx, double* out);
 
 /* Device memory (MB) for the per-chunk intermediates X_beta of one H_eff.psi
  * (default 2048): the operator terms are processed in chunks whose
@@ -282,7 +299,8 @@ typedef struct {
   const int32_t* M;
   const double* dav_tol;
   int32_t dav_max_iter;
-  int32_t precision; /* as gbdmrg_set_precision: 0 FP64, 1 BF16 pass, 2 BF16 x3, 3 BF16 x2 slices */
+  int32_t precision; /* as gbdmrg_set_precision: 0 FP64, 1 BF16 pass, 2 BF16 x3, 3 BF16 x2 slices,
+                        4 BF16 pass on the TMA-staged work lists */
 } gbdmrg_schedule;
 
 /* Run the sweeps from the current MPS (brought to right-canonical form first).

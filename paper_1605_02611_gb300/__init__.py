@@ -57,6 +57,8 @@ SIGNATURES = {
     "gbdmrg_set_split": (C.c_int, [_P, C.c_double]),
     "gbdmrg_get_plan_params": (C.c_int, [_P, _PD, _PI32]),
     "gbdmrg_set_stage1_stacked": (C.c_int, [_P, _I32]),
+    "gbdmrg_set_tma_budget": (C.c_int, [_P, C.c_int64]),
+    "gbdmrg_plan_stats": (C.c_int, [_P, _PD]),
     "gbdmrg_set_tc_combos": (C.c_int, [_P, _I32, C.c_int64]),
     "gbdmrg_autotune": (C.c_int, [_I32, C.POINTER(_P), _I32, _PD, _I32, _PI32, _I32, _PD, _PD, _PI32]),
     "gbdmrg_plan": (C.c_int, [_P, _I32]),
@@ -382,6 +384,18 @@ class Context:
         """Stage 1 of later tensor-core work lists over stacked right operands."""
         self._check(self.lib.gbdmrg_set_stage1_stacked(self.h, int(stacked)), "set_stage1_stacked")
 
+    def set_tma_budget(self, megabytes: int):
+        """Device memory (MB) for the X intermediates of one precision-4 H_eff.psi chunk."""
+        self._check(self.lib.gbdmrg_set_tma_budget(self.h, int(megabytes)), "set_tma_budget")
+
+    def plan_stats(self) -> dict:
+        """Work-list statistics of the prepared precision-4 H_eff.psi (see gbdmrg_plan_stats)."""
+        out = np.zeros(9)
+        self._check(self.lib.gbdmrg_plan_stats(self.h, _dptr(out)), "plan_stats")
+        keys = ["stage1_tiles", "stage1_ksteps", "stage2_tiles", "stage2_ksteps", "stage1_exec_flops",
+                "stage2_exec_flops", "x_bytes", "rstack_bytes", "chunks"]
+        return dict(zip(keys, out.tolist()))
+
     def set_tc_combos(self, on: bool = True, min_terms: int = 100000):
         """W-contracted sums that feed only the tensor-core sigma and the diagonal on the tensor cores."""
         self._check(self.lib.gbdmrg_set_tc_combos(self.h, int(on), int(min_terms)), "set_tc_combos")
@@ -393,7 +407,8 @@ class Context:
         return t.value, b.value
 
     def set_precision(self, mode: int):
-        """0 FP64, 1 tensor-core BF16 single pass, 2 BF16 x3 slices, 3 BF16 x2 slices."""
+        """0 FP64, 1 tensor-core BF16 single pass, 2 BF16 x3 slices, 3 BF16 x2 slices,
+        4 BF16 single pass on the TMA-staged work lists."""
         self._check(self.lib.gbdmrg_set_precision(self.h, mode), "set_precision")
 
     def prepare(self, k: int):

@@ -226,7 +226,7 @@ gbdmrg_status gbdmrg_get_bond(gbdmrg_ctx* ctx, int32_t bond, int32_t* D, int32_t
 }
 
 gbdmrg_status gbdmrg_set_precision(gbdmrg_ctx* ctx, int32_t precision) {
-  if (!ctx || precision < 0 || precision > 3) return GBDMRG_EINVAL;
+  if (!ctx || precision < 0 || precision > 4) return GBDMRG_EINVAL;
   return guard(ctx, [&] {
     ctx->c.precision = precision;
     ctx->c.prepared = -1;
@@ -306,6 +306,22 @@ void gbdmrg_batch_destroy(gbdmrg_batch* b) { delete b; }
 gbdmrg_status gbdmrg_set_split(gbdmrg_ctx* ctx, double tiles_per_sm) {
   if (!ctx || !std::isfinite(tiles_per_sm)) return GBDMRG_EINVAL;
   return guard(ctx, [&] { ctx->c.split_tps = tiles_per_sm; });
+}
+
+gbdmrg_status gbdmrg_set_tma_budget(gbdmrg_ctx* ctx, int64_t megabytes) {
+  if (!ctx || megabytes <= 0) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    ctx->c.tma_budget_mb = (long)megabytes;
+    ctx->c.prepared = -1;
+  });
+}
+
+gbdmrg_status gbdmrg_plan_stats(gbdmrg_ctx* ctx, double* out) {
+  if (!ctx || !out) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    if (ctx->c.prepared < 0) throw gbdmrg::Error(gbdmrg::ST_ESTATE, "call gbdmrg_prepare first");
+    gbdmrg::tma_plan_stats(ctx->c.plan, out);
+  });
 }
 
 gbdmrg_status gbdmrg_set_stage1_stacked(gbdmrg_ctx* ctx, int32_t stacked) {
@@ -411,7 +427,7 @@ gbdmrg_status gbdmrg_sigma(gbdmrg_ctx* ctx, const double* psi, double* sigma, in
       gbdmrg::cuda_check(cudaMemcpyAsync(sigma, plan.out.p, bytes, cudaMemcpyDeviceToHost, c.stream), "d2h");
     }
     gbdmrg::cuda_check(cudaStreamSynchronize(c.stream), "sync");
-    if (plan.mx && gbdmrg::mixed_error(c, plan))
+    if (plan.tensor() && gbdmrg::plan_error(c, plan))
       throw gbdmrg::Error(gbdmrg::ST_ETIMEOUT, "tensor-core GEMM: a bounded wait ran out");
     if (flops) *flops = plan.flops;
   });
@@ -453,7 +469,7 @@ gbdmrg_status gbdmrg_sigma_timing(gbdmrg_ctx* ctx, int32_t reps, const double* p
     for (int r = 0; r < reps; ++r) gbdmrg::run_sigma(c, c.plan, psi_dev, sigma_dev);
     gbdmrg::cuda_check(cudaEventRecord(e1, c.stream), "record");
     gbdmrg::cuda_check(cudaEventSynchronize(e1), "sync");
-    if (c.plan.mx && gbdmrg::mixed_error(c, c.plan))
+    if (c.plan.tensor() && gbdmrg::plan_error(c, c.plan))
       throw gbdmrg::Error(gbdmrg::ST_ETIMEOUT, "tensor-core GEMM: a bounded wait ran out");
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
@@ -609,7 +625,7 @@ gbdmrg_status gbdmrg_run(gbdmrg_ctx* ctx, const gbdmrg_schedule* s, double* ener
       if (s->M[i] <= 0) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "M must be positive");
       if (!(s->dav_tol[i] > 0)) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "dav_tol must be positive");
     }
-    if (s->precision < 0 || s->precision > 3) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "precision must be 0 to 3");
+    if (s->precision < 0 || s->precision > 4) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "precision must be 0 to 4");
     ctx->c.precision = s->precision;
     ctx->stats = gbdmrg::SweepStats();
     gbdmrg::run_sweeps(ctx->c, s->nsweeps, s->M, s->dav_tol, s->dav_max_iter > 0 ? s->dav_max_iter : 200,

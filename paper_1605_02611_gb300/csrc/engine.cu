@@ -790,6 +790,10 @@ void build_sigma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) 
   P.build(Lb, Rb);
   plan.in.alloc(P.nnz, c.stream);
   plan.out.alloc(P.nnz, c.stream);
+  if (c.precision == 4) {
+    build_tma_plan(c, lt, rt, k, plan);
+    return;
+  }
   if (c.precision > 0) {
     build_mixed_plan(c, lt, rt, k, plan, c.precision == 1 ? 1 : c.precision == 2 ? 3 : 2);
     return;
@@ -886,6 +890,10 @@ void build_sigma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) 
 }
 
 void run_sigma(Context& c, SigmaPlan& plan, const double* x, double* y) {
+  if (plan.tm) {
+    run_tma_sigma(c, plan, x, y);
+    return;
+  }
   if (plan.mx) {
     run_mixed_sigma(c, plan, x, y);
     return;
@@ -1097,7 +1105,7 @@ double davidson(Context& c, SigmaPlan& plan, const double* diag, double* psi, co
     cuda_check(cudaEventSynchronize(c.ev1), "sync");
     float ms = 0;
     cuda_check(cudaEventElapsedTime(&ms, c.ev0, c.ev1), "elapsed");
-    if (plan.mx && mixed_error(c, plan)) throw Error(ST_ETIMEOUT, "tensor-core GEMM: a bounded wait ran out");
+    if (plan.tensor() && plan_error(c, plan)) throw Error(ST_ETIMEOUT, "tensor-core GEMM: a bounded wait ran out");
     c.sigma_time_total += 1e-3 * ms;
     c.sigma_flops_total += plan.flops;
     c.sigma_calls++;
@@ -1227,7 +1235,7 @@ double expectation(Context& c) {
   sig.alloc(n, c.stream);
   make_psi(c, c.sites[k], c.sites[k + 1], plan.psi, psi.p);
   run_sigma(c, plan, psi.p, sig.p);
-  if (plan.mx && mixed_error(c, plan)) throw Error(ST_ETIMEOUT, "tensor-core GEMM: a bounded wait ran out");
+  if (plan.tensor() && plan_error(c, plan)) throw Error(ST_ETIMEOUT, "tensor-core GEMM: a bounded wait ran out");
   DotHelper dh;
   dh.init(1, c.stream);
   const double num = dh.dots(c, psi.p, 0, 1, sig.p, n)[0];
@@ -1575,7 +1583,7 @@ double two_site_step(Context& c, int k, int dir, int M, const DavidsonOpts& o, b
   compute_diag(c, lt, rt, k, plan.psi, diag.p);
   lap(2);
   DavidsonOpts od = o;
-  if (plan.mx && od.stagnation == 0) od.stagnation = 6;
+  if (plan.tensor() && od.stagnation == 0) od.stagnation = 6;
   double e = davidson(c, plan, diag.p, psi.p, od, iters);
   if (psi_out)
     cuda_check(cudaMemcpyAsync(psi_out, psi.p, plan.psi.nnz * sizeof(double), cudaMemcpyDeviceToDevice, c.stream),

@@ -167,6 +167,11 @@ void mixed_plan_free(MixedPlan* p);
 struct MixedDeleter {
   void operator()(MixedPlan* p) const { mixed_plan_free(p); }
 };
+struct TmaPlan;
+void tma_plan_free(TmaPlan* p);
+struct TmaDeleter {
+  void operator()(TmaPlan* p) const { tma_plan_free(p); }
+};
 
 // Work lists of H_eff.psi for one two-site problem: FP64 grouped GEMMs, or
 // (mx set) the tensor-core mixed-precision plan of engine_mixed.cu.
@@ -175,7 +180,10 @@ struct SigmaPlan {
   DArr<double> in, out, X;
   std::vector<GemmPlan> stage1, stage2;
   std::unique_ptr<MixedPlan, MixedDeleter> mx;
+  // single-pass tensor-core plan with TMA-staged operands (precision 4)
+  std::unique_ptr<TmaPlan, TmaDeleter> tm;
   double flops = 0;
+  bool tensor() const { return mx != nullptr || tm != nullptr; }
 };
 
 struct Context;
@@ -251,8 +259,15 @@ struct Context {
   long tc_combo_min_terms = 100000;
   // 0: FP64 grouped GEMMs; 1: tensor cores, one BF16 pass; 2: tensor cores,
   // three BF16 slices (six products, about FP32 accuracy); 3: two BF16 slices
-  // (three products)
+  // (three products); 4: tensor cores, one BF16 pass on the TMA-staged plan
+  // (stage 1 as one dense GEMM per group over the stacked right operators)
   int precision = 0;
+  // precision of the Davidson refinement phase for the single-pass modes (1, 4):
+  // after the inner solve with the single-pass operator, the Ritz vector is
+  // refined with this operator (0 FP64, 2 three BF16 slices; -1: no refinement)
+  int refine_precision = -1;
+  // X intermediates of the TMA-staged plan per chunk of bond states (MB)
+  long tma_budget_mb = 65536;
   // keep host copies of tensor-core work lists (needed to fuse problems into batches)
   bool keep_host_plans = false;
   // learned Davidson preconditioner (not owned; null: diagonal) and its scratch
@@ -291,6 +306,15 @@ void run_sigma(Context& c, SigmaPlan& plan, const double* x, double* y);
 void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, int nslices);
 void run_mixed_sigma(Context& c, SigmaPlan& plan, const double* x, double* y);
 int mixed_error(Context& c, SigmaPlan& plan);
+void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan);
+void run_tma_sigma(Context& c, SigmaPlan& plan, const double* x, double* y);
+// non-zero if a tensor-core launch of the plan reported a bounded wait that ran out
+// (reads and clears nothing; synchronises the context stream)
+int plan_error(Context& c, SigmaPlan& plan);
+// host statistics of a TMA-staged plan: [0] stage-1 tiles, [1] stage-1 K steps,
+// [2] stage-2 tiles, [3] stage-2 K steps, [4] executed stage-1 flops, [5] executed
+// stage-2 flops, [6] X intermediate bytes, [7] stacked right-operand bytes, [8] chunks
+void tma_plan_stats(const SigmaPlan& plan, double* out);
 
 // batched tensor-core sigma over several prepared contexts (engine_mixed.cu)
 struct BatchPlan;

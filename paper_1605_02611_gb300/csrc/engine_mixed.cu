@@ -21,9 +21,11 @@
 #include <limits>
 #include <map>
 #include <unordered_map>
+#include <unordered_set>
 
 #include "engine.hpp"
 #include "kernels_tc.hpp"
+#include "kernels_tma.hpp"
 
 namespace gbdmrg {
 
@@ -698,6 +700,635 @@ int mixed_error(Context& c, SigmaPlan& plan) {
   return h;
 }
 
+// ---------------------------------------------------------------- TMA-staged single-pass plan
+
+// H_eff.psi in one BF16 pass with both stages as TMA-staged grouped GEMMs over a few
+// large matrices (one tensor map each):
+//   stage 1, per input group g': X_g'^T = A1_g' Psi_g'^T, where A1_g' stacks, for every
+//     bond state beta and every (n2, qr) column block of the output group g = g' + dQ_beta,
+//     the row block [Rt_beta^{n2 n2'}[qr, qr'] over the column blocks (n2', qr') of g'];
+//     row blocks with the same pattern of non-zero site blocks n2' are stacked together,
+//     and a tile multiplies only the K blocks of its pattern (no product with an absent
+//     site block).  Each output row goes through a row map to its place in X_g'^T, whose
+//     rows are, per beta, the column blocks of g in the row order of sigma^T_g.
+//   stage 2, per output block: sigma^T_g[rows, (ql, n1)] += sum_{beta, n1'}
+//     X_g'^T[beta rows, (ql', n1')] Lt_beta^{n1 n1'}[ql, ql']^T, a long contraction over
+//     the operator terms (the paper's sum over left-right terms, Eq. Hpartition), cut
+//     into parts that add with FP32 vector reductions.
+// Every block is padded to 16 rows and columns with zeros, so a K step of 16 never
+// mixes two blocks and padding contributes exact zeros.
+struct TmaPlan {
+  DArr<__nv_bfloat16> psi_b, a1, xt, lmir;
+  DArr<float> sig_t;
+  long sig_total = 0;
+  DArr<ConvJob> psi_jobs, a1_jobs, l_jobs;
+  int n_psi_jobs = 0, n_a1_jobs = 0, n_l_jobs = 0;
+  long psi_maxel = 0, a1_maxel = 0, l_maxel = 0;
+  DArr<UnconvJob> sig_jobs;
+  int n_sig_jobs = 0;
+  long sig_maxel = 0;
+  DArr<CUtensorMap> maps;
+  DArr<long> rowmap;
+  struct Chunk {
+    DArr<TmTile> t1, t2;
+    DArr<TmTerm> m1, m2;
+    int n1 = 0, n2 = 0;
+    DArr<ZeroJob> z;
+    int nz = 0;
+    long zmax = 0;
+  };
+  std::vector<Chunk> chunks;
+  DArr<int> err;
+  double stats[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+void tma_plan_free(TmaPlan* p) { delete p; }
+
+void tma_plan_stats(const SigmaPlan& plan, double* out) {
+  for (int i = 0; i < 9; ++i) out[i] = plan.tm ? plan.tm->stats[i] : 0.0;
+}
+
+namespace {
+inline int pad16(int x) { return (x + 15) & ~15; }
+}  // namespace
+
+// conversion jobs must write inside their destination buffer
+static void check_conv_jobs(const std::vector<ConvJob>& jobs, const DArr<__nv_bfloat16>& buf) {
+  for (const ConvJob& j : jobs)
+    if (j.rows < 1 || j.wcols < j.cols || j.ldd < j.wcols || j.dst < buf.p ||
+        j.dst + (long)(j.rows - 1) * j.ldd + j.wcols > buf.p + buf.n)
+      throw Error(ST_ECUDA, "internal: conversion job outside its buffer");
+}
+
+void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) {
+  const auto& mid = c.mpo.bonds[k + 1];
+  Env& Lenv = *lt.env;
+  Env& Renv = *rt.env;
+  const Bond& Lb = Lenv.bond;
+  const Bond& Rb = Renv.bond;
+  const PsiLayout& P = plan.psi;
+  auto* tp = new TmaPlan();
+  plan.tm.reset(tp);
+  const int nL = Lb.nsec(), nR = Rb.nsec();
+  const int nmid = (int)mid.size();
+  // ---- groups of the cut: rows (ql, n1) and columns (n2, qr), blocks padded to 16
+  std::map<std::pair<int, int>, int> gidx;
+  std::vector<std::pair<int, int>> gq;
+  std::vector<std::vector<std::array<int, 3>>> grow, gcol;  // (ql, n1, off), (n2, qr, off)
+  std::vector<int> gR, gC;
+  {
+    std::map<std::pair<int, int>, std::pair<std::vector<std::array<int, 3>>, std::vector<std::array<int, 3>>>> tmp;
+    for (int ql = 0; ql < nL; ++ql)
+      for (int n1 = 0; n1 < 4; ++n1) tmp[{Lb.qa[ql] + LQA[n1], Lb.qb[ql] + LQB[n1]}].first.push_back({ql, n1, 0});
+    for (int qr = 0; qr < nR; ++qr)
+      for (int n2 = 0; n2 < 4; ++n2) tmp[{Rb.qa[qr] - LQA[n2], Rb.qb[qr] - LQB[n2]}].second.push_back({n2, qr, 0});
+    for (auto& kv : tmp) {
+      if (kv.second.first.empty() || kv.second.second.empty()) continue;
+      gidx[kv.first] = (int)gq.size();
+      gq.push_back(kv.first);
+      auto rows = kv.second.first, cols = kv.second.second;
+      int R = 0, C = 0;
+      for (auto& r : rows) { r[2] = R; R += pad16(Lb.dim[r[0]]); }
+      for (auto& cc : cols) { cc[2] = C; C += pad16(Rb.dim[cc[1]]); }
+      grow.push_back(rows);
+      gcol.push_back(cols);
+      gR.push_back(R);
+      gC.push_back(C);
+    }
+  }
+  const int ng = (int)gq.size();
+  std::vector<std::array<int, 2>> rpos((size_t)nL * 4, {-1, 0}), cpos((size_t)nR * 4, {-1, 0});
+  for (int g = 0; g < ng; ++g) {
+    for (auto& r : grow[g]) rpos[r[0] * 4 + r[1]] = {g, r[2]};
+    for (auto& cc : gcol[g]) cpos[cc[1] * 4 + cc[0]] = {g, cc[2]};
+  }
+  auto group_of = [&](int a, int b) {
+    auto it = gidx.find({a, b});
+    return it == gidx.end() ? -1 : it->second;
+  };
+  // output group of bond state beta for input group g' (-1: none)
+  std::vector<int> gout((size_t)nmid * ng, -1);
+  for (int beta = 0; beta < nmid; ++beta)
+    for (int gp = 0; gp < ng; ++gp)
+      gout[(size_t)beta * ng + gp] = group_of(gq[gp].first + mid[beta].dna, gq[gp].second + mid[beta].dnb);
+  // input group g' = g - dQ_beta of bond state beta for output group g (-1: none)
+  std::vector<int> gin((size_t)nmid * ng, -1);
+  for (int beta = 0; beta < nmid; ++beta)
+    for (int g = 0; g < ng; ++g)
+      gin[(size_t)beta * ng + g] = group_of(gq[g].first - mid[beta].dna, gq[g].second - mid[beta].dnb);
+  // ---- Psi_g (BF16, R_g x C_g) and sigma^T_g (FP32, C_g x R_g)
+  std::vector<long> goff(ng), sgoff(ng);
+  long ptot = 0, stot = 0;
+  for (int g = 0; g < ng; ++g) {
+    goff[g] = ptot;
+    ptot += (long)gR[g] * gC[g];
+    sgoff[g] = stot;
+    stot += (long)gC[g] * gR[g];
+  }
+  tp->psi_b.alloc(std::max<long>(ptot, 8), c.stream);
+  cuda_check(cudaMemsetAsync(tp->psi_b.p, 0, tp->psi_b.n * sizeof(__nv_bfloat16), c.stream), "memset");
+  tp->sig_total = std::max<long>(stot, 4);
+  tp->sig_t.alloc(tp->sig_total, c.stream);
+  {
+    std::vector<ConvJob> pj;
+    std::vector<UnconvJob> sj;
+    for (size_t b = 0; b < P.blocks.size(); ++b) {
+      const Block& B = P.blocks[b];
+      const auto rp = rpos[B.rs * 4 + P.b1[b]];
+      const auto cp = cpos[B.cs * 4 + P.b2[b]];
+      if (rp[0] < 0 || rp[0] != cp[0]) throw Error(ST_ECUDA, "internal: psi block outside its group");
+      const int g = rp[0];
+      pj.push_back({plan.in.p + B.off, tp->psi_b.p + goff[g] + (long)rp[1] * gC[g] + cp[1], 0, B.rows, B.cols,
+                    B.cols, gC[g], 1, 1.0, pad16(B.cols)});
+      tp->psi_maxel = std::max<long>(tp->psi_maxel, (long)B.rows * pad16(B.cols));
+      sj.push_back({tp->sig_t.p + sgoff[g] + (long)cp[1] * gR[g] + rp[1], plan.out.p + B.off, B.rows, B.cols, gR[g]});
+      tp->sig_maxel = std::max<long>(tp->sig_maxel, (long)B.rows * B.cols);
+    }
+    check_conv_jobs(pj, tp->psi_b);
+    for (const UnconvJob& u : sj)
+      if (u.src < tp->sig_t.p || u.src + (long)(u.cols - 1) * u.lds + u.rows > tp->sig_t.p + tp->sig_total)
+        throw Error(ST_ECUDA, "internal: gather job outside sigma^T");
+    tp->psi_jobs.upload(pj, c.stream);
+    tp->n_psi_jobs = (int)pj.size();
+    tp->sig_jobs.upload(sj, c.stream);
+    tp->n_sig_jobs = (int)sj.size();
+    cuda_check(cudaStreamSynchronize(c.stream), "sync");
+  }
+  // ---- stage-1 row blocks: per input group g', every (beta, n2) with at least one
+  // non-zero site block n2' of Rt_beta towards the column blocks of g'
+  struct RowBlk {
+    int beta, n2, qr, rows, mask;
+    int bl[4];  // per n2' in the mask: the operator block of Rt_beta^{n2 n2'}
+  };
+  std::vector<std::vector<RowBlk>> rb(ng);
+  for (int gp = 0; gp < ng; ++gp)
+    for (int beta = 0; beta < nmid; ++beta) {
+      const int g = gout[(size_t)beta * ng + gp];
+      if (g < 0) continue;
+      for (const auto& cb : gcol[g]) {
+        const int n2 = cb[0], qr = cb[1];
+        RowBlk x{beta, n2, qr, Rb.dim[qr], 0, {-1, -1, -1, -1}};
+        for (int n2p = 0; n2p < 4; ++n2p) {
+          const TRef& r = rt.ref[beta][n2 * 4 + n2p];
+          if (!r.p) continue;
+          const int qrp = Rb.find(gq[gp].first + LQA[n2p], gq[gp].second + LQB[n2p]);
+          if (qrp < 0 || cpos[qrp * 4 + n2p][0] != gp) continue;
+          const OpLayout& Lay = Renv.cls[r.cls];
+          const int bl = Lay.blk_of_col[qrp];
+          if (bl < 0 || Lay.blocks[bl].rs != qr) continue;
+          x.mask |= 1 << n2p;
+          x.bl[n2p] = bl;
+        }
+        if (x.mask) rb[gp].push_back(x);
+      }
+    }
+  std::vector<char> xhas((size_t)nmid * ng, 0);  // [beta][g'] has X^T rows
+  for (int gp = 0; gp < ng; ++gp)
+    for (const RowBlk& x : rb[gp]) xhas[(size_t)x.beta * ng + gp] = 1;
+  // chunks of bond states whose X^T fit the budget (one chunk unless the budget is small)
+  std::vector<size_t> xsz(nmid, 0);
+  for (int beta = 0; beta < nmid; ++beta)
+    for (int gp = 0; gp < ng; ++gp)
+      if (xhas[(size_t)beta * ng + gp]) xsz[beta] += (size_t)gC[gout[(size_t)beta * ng + gp]] * gR[gp];
+  const size_t budget = (size_t)std::max<long>(1, c.tma_budget_mb) * (1u << 20) / sizeof(__nv_bfloat16);
+  std::vector<std::pair<int, int>> chunks;
+  for (int b0 = 0; b0 < nmid;) {
+    int b1 = b0;
+    size_t tot = 0;
+    while (b1 < nmid && (b1 == b0 || tot + xsz[b1] <= budget)) tot += xsz[b1++];
+    chunks.push_back({b0, b1});
+    b0 = b1;
+  }
+  const int nch = (int)chunks.size();
+  std::vector<int> chunk_of(nmid, 0);
+  for (int ci = 0; ci < nch; ++ci)
+    for (int b = chunks[ci].first; b < chunks[ci].second; ++b) chunk_of[b] = ci;
+  // X^T layout per chunk: regions per g' (Sum_beta C_g(beta) rows x R_g' columns);
+  // xrow[beta][g'] = first row of beta's block in its region
+  std::vector<std::vector<long>> xreg(nch, std::vector<long>(ng, 0)), xregrows(nch, std::vector<long>(ng, 0));
+  std::vector<long> xrow((size_t)nmid * ng, -1);
+  size_t maxchunk = 0;
+  for (int ci = 0; ci < nch; ++ci) {
+    long off = 0;
+    for (int gp = 0; gp < ng; ++gp) {
+      xreg[ci][gp] = off;
+      long rows = 0;
+      for (int beta = chunks[ci].first; beta < chunks[ci].second; ++beta)
+        if (xhas[(size_t)beta * ng + gp]) {
+          xrow[(size_t)beta * ng + gp] = rows;
+          rows += gC[gout[(size_t)beta * ng + gp]];
+        }
+      xregrows[ci][gp] = rows;
+      off += rows * gR[gp];
+    }
+    maxchunk = std::max(maxchunk, (size_t)off);
+  }
+  tp->xt.alloc(std::max<size_t>(maxchunk, 8), c.stream);
+  cuda_check(cudaMemsetAsync(tp->xt.p, 0, tp->xt.n * sizeof(__nv_bfloat16), c.stream), "memset");
+  // ---- A1 per g': row blocks sorted by (chunk, mask), beta order kept inside a run
+  for (int gp = 0; gp < ng; ++gp)
+    std::stable_sort(rb[gp].begin(), rb[gp].end(), [&](const RowBlk& a, const RowBlk& b) {
+      if (chunk_of[a.beta] != chunk_of[b.beta]) return chunk_of[a.beta] < chunk_of[b.beta];
+      return a.mask < b.mask;
+    });
+  std::vector<long> a1off(ng), a1rows(ng);
+  long a1tot = 0;
+  for (int gp = 0; gp < ng; ++gp) {
+    long rows = 0;
+    for (const RowBlk& x : rb[gp]) rows += x.rows;
+    a1off[gp] = a1tot;
+    a1rows[gp] = rows;
+    a1tot += rows * gC[gp];
+  }
+  tp->a1.alloc(std::max<long>(a1tot, 8), c.stream);
+  cuda_check(cudaMemsetAsync(tp->a1.p, 0, tp->a1.n * sizeof(__nv_bfloat16), c.stream), "memset");
+  struct Run {
+    int chunk, mask;
+    long r0, r1;
+  };
+  std::vector<std::vector<Run>> runs(ng);
+  std::vector<std::vector<long>> rowdst(ng);  // per A1 row: element offset of its X^T row
+  std::vector<ConvJob> aconv;
+  for (int gp = 0; gp < ng; ++gp) {
+    long row = 0;
+    rowdst[gp].assign((size_t)a1rows[gp], -1);
+    for (const RowBlk& x : rb[gp]) {
+      const int ci = chunk_of[x.beta];
+      if (runs[gp].empty() || runs[gp].back().chunk != ci || runs[gp].back().mask != x.mask)
+        runs[gp].push_back({ci, x.mask, row, row});
+      runs[gp].back().r1 = row + x.rows;
+      const long xbase =
+          xreg[ci][gp] + (xrow[(size_t)x.beta * ng + gp] + (long)cpos[x.qr * 4 + x.n2][1]) * (long)gR[gp];
+      for (int i = 0; i < x.rows; ++i) rowdst[gp][(size_t)(row + i)] = xbase + (long)i * gR[gp];
+      for (int n2p = 0; n2p < 4; ++n2p) {
+        if (!((x.mask >> n2p) & 1)) continue;
+        const TRef& r = rt.ref[x.beta][x.n2 * 4 + n2p];
+        const Block& B = Renv.cls[r.cls].blocks[x.bl[n2p]];
+        const int coff = cpos[B.cs * 4 + n2p][1];
+        aconv.push_back({r.p + B.off, tp->a1.p + a1off[gp] + row * gC[gp] + coff, 0, B.rows, B.cols, B.cols, gC[gp],
+                         1, r.coef, pad16(B.cols)});
+        tp->a1_maxel = std::max<long>(tp->a1_maxel, (long)B.rows * pad16(B.cols));
+      }
+      row += x.rows;
+    }
+  }
+  check_conv_jobs(aconv, tp->a1);
+  tp->a1_jobs.upload(aconv, c.stream);
+  tp->n_a1_jobs = (int)aconv.size();
+  // ---- left mirror: every distinct (operator, scale) referenced by Lt, all its blocks,
+  // each padded to 16 rows and columns, in one matrix of WL columns
+  int WL = 16;
+  for (const OpLayout& L : Lenv.cls)
+    for (const Block& B : L.blocks) WL = std::max(WL, pad16(B.cols));
+  struct MirKeyHash {
+    size_t operator()(const std::pair<const double*, double>& kk) const {
+      uint64_t b;
+      std::memcpy(&b, &kk.second, sizeof b);
+      return std::hash<uint64_t>()((uint64_t)(uintptr_t)kk.first * 0x9e3779b97f4a7c15ULL ^ b);
+    }
+  };
+  std::unordered_map<std::pair<const double*, double>, long, MirKeyHash> lm_row;
+  std::vector<std::vector<long>> lblk_row(Lenv.cls.size());
+  std::vector<long> lop_rows(Lenv.cls.size(), 0);
+  for (size_t ci = 0; ci < Lenv.cls.size(); ++ci) {
+    long r = 0;
+    for (const Block& B : Lenv.cls[ci].blocks) {
+      lblk_row[ci].push_back(r);
+      r += pad16(B.rows);
+    }
+    lop_rows[ci] = r;
+  }
+  long lrows = 0;
+  std::vector<ConvJob> lconv;
+  std::vector<std::array<long, 16>> lrow0((size_t)nmid);
+  std::vector<std::array<char, 16>> lneg((size_t)nmid);
+  for (int beta = 0; beta < nmid; ++beta)
+    for (int nn = 0; nn < 16; ++nn) {
+      lrow0[beta][nn] = -1;
+      lneg[beta][nn] = 0;
+      const TRef& r = lt.ref[beta][nn];
+      if (!r.p) continue;
+      const double a = std::fabs(r.coef);
+      const double scale = a == 1.0 ? 1.0 : r.coef;
+      auto key = std::make_pair(r.p, scale);
+      auto it = lm_row.find(key);
+      long row0;
+      if (it == lm_row.end()) {
+        row0 = lrows;
+        lm_row.emplace(key, row0);
+        const OpLayout& L = Lenv.cls[r.cls];
+        for (size_t b = 0; b < L.blocks.size(); ++b) {
+          const Block& B = L.blocks[b];
+          // dst holds the row until the buffer exists
+          lconv.push_back({r.p + B.off, (__nv_bfloat16*)(intptr_t)(row0 + lblk_row[r.cls][b]), 0, B.rows, B.cols,
+                           B.cols, WL, 1, scale, pad16(B.cols)});
+          tp->l_maxel = std::max<long>(tp->l_maxel, (long)B.rows * pad16(B.cols));
+        }
+        lrows += lop_rows[r.cls];
+      } else {
+        row0 = it->second;
+      }
+      lrow0[beta][nn] = row0;
+      lneg[beta][nn] = (a == 1.0 && r.coef < 0) ? 1 : 0;
+    }
+  tp->lmir.alloc(std::max<long>(lrows * WL, 8), c.stream);
+  cuda_check(cudaMemsetAsync(tp->lmir.p, 0, tp->lmir.n * sizeof(__nv_bfloat16), c.stream), "memset");
+  for (ConvJob& j : lconv) j.dst = tp->lmir.p + (intptr_t)j.dst * WL;
+  check_conv_jobs(lconv, tp->lmir);
+  tp->l_jobs.upload(lconv, c.stream);
+  tp->n_l_jobs = (int)lconv.size();
+  // ---- tensor maps
+  std::vector<CUtensorMap> maps;
+  // every map must lie inside its buffer (a box outside the map's extent reads zeros,
+  // but the extent itself is trusted by the hardware)
+  struct MapInfo {
+    long rows, cols;
+    int box;
+  };
+  std::vector<MapInfo> minfo;
+  auto add_map = [&](const DArr<__nv_bfloat16>& buf, long off, long rows, long cols, long ld, int box_rows) {
+    if (off < 0 || rows < 1 || cols < 1 || ld < cols || ld % 8 != 0 || off % 8 != 0 ||
+        (size_t)(off + (rows - 1) * ld + cols) > buf.n)
+      throw Error(ST_ECUDA, "internal: tensor map outside its buffer");
+    CUtensorMap m;
+    if (!encode_bf16_map(&m, buf.p + off, (uint64_t)rows, (uint64_t)cols, (uint64_t)ld, (uint32_t)box_rows))
+      throw Error(ST_ECUDA, "cuTensorMapEncodeTiled failed");
+    maps.push_back(m);
+    minfo.push_back({rows, cols, box_rows});
+    return (int)maps.size() - 1;
+  };
+  const int n1max = tma_max_n(TM_MODE_STORE_BF16), n2max = tma_max_n(TM_MODE_REDUCE_F32);
+  std::vector<std::vector<std::array<int, 3>>> nt1(ng);  // per g': (row0, width, Psi map) of the stage-1 N tiles
+  std::vector<int> a1map(ng, -1);
+  for (int gp = 0; gp < ng; ++gp) {
+    if (a1rows[gp] == 0) continue;
+    const int parts = (gR[gp] + n1max - 1) / n1max;
+    int r0 = 0;
+    for (int p = 0; p < parts; ++p) {
+      const int w = std::min(gR[gp] - r0, pad16((gR[gp] - r0 + (parts - p) - 1) / (parts - p)));
+      nt1[gp].push_back({r0, w, add_map(tp->psi_b, goff[gp], gR[gp], gC[gp], gC[gp], w)});
+      r0 += w;
+    }
+    a1map[gp] = add_map(tp->a1, a1off[gp], a1rows[gp], gC[gp], gC[gp], 128);
+  }
+  std::vector<std::vector<int>> xtmap(nch, std::vector<int>(ng, -1));
+  for (int ci = 0; ci < nch; ++ci)
+    for (int gp = 0; gp < ng; ++gp)
+      if (xregrows[ci][gp] > 0) xtmap[ci][gp] = add_map(tp->xt, xreg[ci][gp], xregrows[ci][gp], gR[gp], gR[gp], 128);
+  std::vector<int> lmap(n2max / 16 + 1, -1);
+  if (lrows > 0)
+    for (int h = 16; h <= n2max; h += 16) lmap[h / 16] = add_map(tp->lmir, 0, lrows, WL, WL, h);
+  tp->maps.alloc(std::max<size_t>(maps.size(), 1), c.stream);
+  if (!maps.empty())
+    cuda_check(cudaMemcpyAsync(tp->maps.p, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
+                               c.stream),
+               "h2d");
+  // ---- work lists per chunk
+  std::vector<long> rowmap;
+  double st1_tiles = 0, st1_steps = 0, st2_tiles = 0, st2_steps = 0, st1_fl = 0, st2_fl = 0;
+  tp->chunks.resize(nch);
+  for (int ci = 0; ci < nch; ++ci) {
+    TmaPlan::Chunk& ch = tp->chunks[ci];
+    std::vector<TmTile> t1, t2;
+    std::vector<TmTerm> m1, m2;
+    std::vector<ZeroJob> zj;
+    // stage 1: per g', per (chunk, mask) run, 128-row tiles x N tiles
+    for (int gp = 0; gp < ng; ++gp)
+      for (const Run& run : runs[gp]) {
+        if (run.chunk != ci) continue;
+        for (long r0 = run.r0; r0 < run.r1; r0 += 128) {
+          const long moff = (long)rowmap.size();
+          for (long i = 0; i < 128; ++i)
+            rowmap.push_back(r0 + i < run.r1 ? rowdst[gp][(size_t)(r0 + i)] : -1);
+          for (const auto& nt : nt1[gp]) {
+            TmTile tl{};
+            tl.t0 = (int)m1.size();
+            int ksum = 0;
+            for (int n2p = 0; n2p < 4; ++n2p) {
+              if (!((run.mask >> n2p) & 1)) continue;
+              // the K block of n2': the column block (n2', qr') of g'
+              const int qrp = Rb.find(gq[gp].first + LQA[n2p], gq[gp].second + LQB[n2p]);
+              const int coff = cpos[qrp * 4 + n2p][1];
+              const int kk = pad16(Rb.dim[qrp]);
+              m1.push_back({a1map[gp], nt[2], coff, (int)r0, coff, nt[0], kk, 0});
+              ksum += kk;
+              st1_steps += (kk + 63) / 64;
+            }
+            tl.t1 = (int)m1.size();
+            tl.n = nt[1];
+            tl.m_valid = 128;
+            tl.ldo = gR[gp];
+            tl.out_off = nt[0];
+            tl.rowmap_off = moff;
+            t1.push_back(tl);
+            st1_fl += 2.0 * 128 * nt[1] * ksum;
+          }
+        }
+      }
+    // X^T rows of this chunk that stage 1 does not write: zero them before the chunk
+    // (with one chunk the buffer is zero from the start)
+    if (nch > 1) {
+      for (int gp = 0; gp < ng; ++gp) {
+        std::unordered_set<long> written;
+        for (const RowBlk& x : rb[gp])
+          if (chunk_of[x.beta] == ci) written.insert(((long)x.beta * 4 + x.n2) * nR + x.qr);
+        for (int beta = chunks[ci].first; beta < chunks[ci].second; ++beta) {
+          if (!xhas[(size_t)beta * ng + gp]) continue;
+          const int g = gout[(size_t)beta * ng + gp];
+          for (const auto& cb : gcol[g]) {
+            if (written.count(((long)beta * 4 + cb[0]) * nR + cb[1])) continue;
+            const long e0 = xreg[ci][gp] + (xrow[(size_t)beta * ng + gp] + cb[2]) * (long)gR[gp];
+            zj.push_back({tp->xt.p + e0, (long)pad16(Rb.dim[cb[1]]) * gR[gp], 0, 1});
+          }
+        }
+      }
+    }
+    // stage 2: per output block (g, (ql, n1) column block, N part), 128-row tiles, terms
+    // over the chunk's bond states; long term lists cut into parts (split-K)
+    struct Pending {
+      TmTile tl;
+      std::vector<TmTerm> terms;
+    };
+    std::vector<Pending> pend;
+    long total_steps = 0;
+    for (int g = 0; g < ng; ++g)
+      for (const auto& rbk : grow[g]) {
+        const int ql = rbk[0], n1 = rbk[1];
+        const int dql = Lb.dim[ql];
+        for (int c0 = 0; c0 < pad16(dql); c0 += n2max) {
+          const int nw = std::min(n2max, pad16(dql) - c0);
+          // the block's terms for the first row tile; other row tiles shift the X^T row
+          std::vector<TmTerm> base;
+          for (int beta = chunks[ci].first; beta < chunks[ci].second; ++beta) {
+            const int gp = gin[(size_t)beta * ng + g];
+            if (gp < 0 || !xhas[(size_t)beta * ng + gp]) continue;
+            for (int n1p = 0; n1p < 4; ++n1p) {
+              const TRef& r = lt.ref[beta][n1 * 4 + n1p];
+              if (!r.p) continue;
+              const OpLayout& Lay = Lenv.cls[r.cls];
+              const int qlp = Lb.find(Lb.qa[ql] - Lay.da, Lb.qb[ql] - Lay.db);
+              if (qlp < 0) continue;
+              const int bl = Lay.blk_of_col[qlp];
+              if (bl < 0 || Lay.blocks[bl].rs != ql) continue;
+              const auto rpp = rpos[qlp * 4 + n1p];
+              if (rpp[0] != gp) continue;
+              base.push_back({xtmap[ci][gp], lmap[nw / 16], rpp[1], (int)xrow[(size_t)beta * ng + gp], 0,
+                              (int)(lrow0[beta][n1 * 4 + n1p] + lblk_row[r.cls][bl] + c0), pad16(Lb.dim[qlp]),
+                              (int)lneg[beta][n1 * 4 + n1p]});
+            }
+          }
+          if (base.empty()) continue;
+          long steps = 0;
+          for (const TmTerm& t : base) steps += (t.k + 63) / 64;
+          for (int r0 = 0; r0 < gC[g]; r0 += 128) {
+            Pending pd;
+            pd.tl = TmTile{};
+            pd.tl.n = nw;
+            pd.tl.m_valid = std::min(128, gC[g] - r0);
+            pd.tl.ldo = gR[g];
+            pd.tl.out_off = sgoff[g] + (long)r0 * gR[g] + rbk[2] + c0;
+            pd.terms = base;
+            for (TmTerm& t : pd.terms) t.ay += r0;
+            total_steps += steps;
+            pend.push_back(std::move(pd));
+          }
+        }
+      }
+    const long target = c.split_tps > 0 ? std::max<long>(1, total_steps / std::max<long>(1, std::lround(c.split_tps * 152)))
+                                        : std::numeric_limits<long>::max();
+    for (Pending& pd : pend) {
+      long acc = 0;
+      size_t t0 = 0;
+      for (size_t t = 0; t < pd.terms.size(); ++t) {
+        acc += (pd.terms[t].k + 63) / 64;
+        if (acc >= target || t + 1 == pd.terms.size()) {
+          TmTile tl = pd.tl;
+          tl.t0 = (int)m2.size();
+          long ks = 0;
+          for (size_t u = t0; u <= t; ++u) {
+            m2.push_back(pd.terms[u]);
+            ks += pd.terms[u].k;
+          }
+          tl.t1 = (int)m2.size();
+          t2.push_back(tl);
+          st2_steps += acc;
+          st2_fl += 2.0 * 128 * tl.n * ks;
+          t0 = t + 1;
+          acc = 0;
+        }
+      }
+    }
+    // longest tiles first (static round-robin over the persistent CTAs); tiles of equal
+    // length keep their order, so the N tiles of one row tile stay adjacent
+    auto order = [](std::vector<TmTile>& t, const std::vector<TmTerm>& m) {
+      std::vector<std::pair<long, int>> key(t.size());
+      for (size_t i = 0; i < t.size(); ++i) {
+        long ks = 0;
+        for (int j = t[i].t0; j < t[i].t1; ++j) ks += (m[j].k + 63) / 64;
+        key[i] = {-ks, (int)i};
+      }
+      std::stable_sort(key.begin(), key.end(),
+                       [](const std::pair<long, int>& a, const std::pair<long, int>& b) { return a.first < b.first; });
+      std::vector<TmTile> out(t.size());
+      for (size_t i = 0; i < t.size(); ++i) out[i] = t[(size_t)key[i].second];
+      t.swap(out);
+    };
+    order(t1, m1);
+    order(t2, m2);
+    st1_tiles += (double)t1.size();
+    st2_tiles += (double)t2.size();
+    // every access of the kernels checked against its buffer before anything runs:
+    // operand boxes (their coordinates, alignment and widths), the rows stage 1 stores
+    // through the row map and the blocks stage 2 reduces into
+    auto check_terms = [&](const std::vector<TmTile>& tt, const std::vector<TmTerm>& mm, int nmax) {
+      for (const TmTile& tl : tt) {
+        if (tl.n < 16 || tl.n > nmax || tl.n % 16 || tl.t0 < 0 || tl.t1 <= tl.t0 || tl.t1 > (int)mm.size())
+          throw Error(ST_ECUDA, "internal: malformed TMA tile");
+        for (int t = tl.t0; t < tl.t1; ++t) {
+          const TmTerm& m = mm[t];
+          if (m.amap < 0 || m.amap >= (int)minfo.size() || m.bmap < 0 || m.bmap >= (int)minfo.size() ||
+              minfo[m.amap].box != 128 || minfo[m.bmap].box != tl.n || m.k < 16 || m.k % 16 || m.ax % 16 ||
+              m.bx % 16 || m.ax < 0 || m.bx < 0 || m.ay < 0 || m.by < 0 || m.ax + m.k > minfo[m.amap].cols + 63 ||
+              m.bx + m.k > minfo[m.bmap].cols + 63)
+            throw Error(ST_ECUDA, "internal: malformed TMA term");
+        }
+      }
+    };
+    check_terms(t1, m1, n1max);
+    check_terms(t2, m2, n2max);
+    for (const TmTile& tl : t1) {
+      if (tl.rowmap_off < 0 || tl.rowmap_off + 128 > (long)rowmap.size())
+        throw Error(ST_ECUDA, "internal: stage-1 row map out of range");
+      for (int r = 0; r < 128; ++r) {
+        const long d = rowmap[(size_t)(tl.rowmap_off + r)];
+        if (d < -1 || (d >= 0 && ((size_t)(d + tl.out_off + tl.n) > tp->xt.n || (d + tl.out_off) % 8)))
+          throw Error(ST_ECUDA, "internal: stage-1 store outside the X buffer");
+      }
+    }
+    for (const TmTile& tl : t2)
+      if (tl.m_valid < 1 || tl.m_valid > 128 || tl.out_off < 0 || tl.out_off % 4 || tl.ldo % 4 ||
+          tl.out_off + (long)(tl.m_valid - 1) * tl.ldo + tl.n > tp->sig_total)
+        throw Error(ST_ECUDA, "internal: stage-2 reduction outside sigma^T");
+    for (const ZeroJob& z : zj)
+      if (z.p < tp->xt.p || z.p + z.n > tp->xt.p + tp->xt.n) throw Error(ST_ECUDA, "internal: zero job outside X");
+    ch.t1.upload(t1, c.stream);
+    ch.m1.upload(m1, c.stream);
+    ch.n1 = (int)t1.size();
+    ch.t2.upload(t2, c.stream);
+    ch.m2.upload(m2, c.stream);
+    ch.n2 = (int)t2.size();
+    ch.nz = (int)zj.size();
+    for (const ZeroJob& z : zj) ch.zmax = std::max(ch.zmax, z.n);
+    ch.z.upload(zj, c.stream);
+    cuda_check(cudaStreamSynchronize(c.stream), "sync");
+  }
+  tp->rowmap.upload(rowmap, c.stream);
+  // the operator stacks depend only on the environments: filled once per plan
+  if (tp->n_a1_jobs) launch_conv(tp->a1_jobs, tp->n_a1_jobs, tp->a1_maxel, c.stream);
+  if (tp->n_l_jobs) launch_conv(tp->l_jobs, tp->n_l_jobs, tp->l_maxel, c.stream);
+  tp->err.alloc(1, c.stream);
+  cuda_check(cudaMemsetAsync(tp->err.p, 0, sizeof(int), c.stream), "memset");
+  cuda_check(cudaStreamSynchronize(c.stream), "sync");
+  tp->stats[0] = st1_tiles;
+  tp->stats[1] = st1_steps;
+  tp->stats[2] = st2_tiles;
+  tp->stats[3] = st2_steps;
+  tp->stats[4] = st1_fl;
+  tp->stats[5] = st2_fl;
+  tp->stats[6] = (double)maxchunk * 2;
+  tp->stats[7] = (double)a1tot * 2;
+  tp->stats[8] = nch;
+  plan.flops = count_sigma_flops(c.mpo, k, Lb, Rb);
+}
+
+void run_tma_sigma(Context& c, SigmaPlan& plan, const double* x, double* y) {
+  TmaPlan& tp = *plan.tm;
+  const size_t n = plan.psi.nnz;
+  if (x != plan.in.p) cuda_check(cudaMemcpyAsync(plan.in.p, x, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "d2d");
+  if (tp.n_psi_jobs) launch_conv(tp.psi_jobs, tp.n_psi_jobs, tp.psi_maxel, c.stream);
+  cuda_check(cudaMemsetAsync(tp.sig_t.p, 0, tp.sig_total * sizeof(float), c.stream), "memset");
+  for (auto& ch : tp.chunks) {
+    if (ch.nz) launch_zero(ch.z.p, ch.nz, ch.zmax, c.stream);
+    cuda_check(launch_gemm_tma(TM_MODE_STORE_BF16, ch.t1.p, ch.n1, ch.m1.p, tp.maps.p, tp.rowmap.p, tp.xt.p, tp.err.p,
+                               c.stream),
+               "tma stage 1");
+    cuda_check(launch_gemm_tma(TM_MODE_REDUCE_F32, ch.t2.p, ch.n2, ch.m2.p, tp.maps.p, tp.rowmap.p, tp.sig_t.p,
+                               tp.err.p, c.stream),
+               "tma stage 2");
+  }
+  if (tp.n_sig_jobs) launch_unconv(tp.sig_jobs.p, tp.n_sig_jobs, tp.sig_maxel, c.stream);
+  if (y != plan.out.p) cuda_check(cudaMemcpyAsync(y, plan.out.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "d2d");
+}
+
+int plan_error(Context& c, SigmaPlan& plan) {
+  int h = 0;
+  int* p = plan.mx ? plan.mx->err.p : plan.tm ? plan.tm->err.p : nullptr;
+  if (!p) return 0;
+  cuda_check(cudaMemcpyAsync(&h, p, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h");
+  cuda_check(cudaStreamSynchronize(c.stream), "sync");
+  return h;
+}
+
 // ---------------------------------------------------------------- batched sigma
 
 // Several independent two-site problems (each prepared in tensor-core precision
@@ -766,7 +1397,8 @@ BatchPlan* batch_create(const std::vector<Context*>& ctxs) {
   for (Context* c : ctxs) {
     if (c->prepared < 0 || !c->plan.mx) {
       delete b;
-      throw Error(ST_ESTATE, "batched sigma: every context must be prepared in a tensor-core precision");
+      throw Error(ST_ESTATE,
+                  "batched sigma: every context must be prepared in a tensor-core precision of the cp.async plan (1-3)");
     }
     MixedPlan& mx = *c->plan.mx;
     nch = std::max(nch, mx.stage1.size());

@@ -82,4 +82,24 @@ struct DiagJob {
 };
 void launch_diag_extract(const DiagJob* d_jobs, int njobs, int max_rows, cudaStream_t s);
 
+// Davidson on the device (FP64).  Rayleigh-Ritz: lowest eigenpair of the symmetric
+// part of the m x m projected matrix G (m <= 48) by parallel cyclic Jacobi in one
+// thread block; eigenvalue to scal[0], eigenvector to y[0..m).  false (nothing
+// launched) if m is outside [1, RR_MAX_SUB]
+constexpr int RR_MAX_SUB = 48;
+bool launch_rr(const double* G, int ldg, int m, double* y, double* scal, cudaStream_t s);
+// r = hx - theta x (theta on device)
+void launch_resid(long n, const double* hx, const double* x, const double* d_theta, double* r, cudaStream_t s);
+// t = r / (theta - diag), theta on device
+void launch_precond_dev(long n, const double* r, const double* diag, const double* d_theta, double eps, double* t,
+                        cudaStream_t s);
+// t -= sum_j c[j] V_j (c on device)
+void launch_sub_combine(const double* V, long ldv, int m, const double* d_c, long n, double* t, cudaStream_t s);
+// y = x / sqrt(*nrm2)
+void launch_scale_rsqrt(long n, const double* x, const double* d_nrm2, double* y, cudaStream_t s);
+// G[i][col] = G[col][i] = dots[i], i < m1
+void launch_gcol(const double* dots, int m1, double* G, int ld, int col, cudaStream_t s);
+// G[0] = theta / xn2
+void launch_restart_g(double* G, const double* d_theta, const double* d_xn2, cudaStream_t s);
+
 }  // namespace gbdmrg

@@ -1,0 +1,388 @@
+// TMA-staged tensor-core grouped GEMM (tcgen05, sm_103a): BF16 operands, FP32
+// accumulation in tensor memory.
+//
+// The operands of the single-pass sigma vector live in a few large row-major
+// BF16 matrices (per quantum-number group of the cut: the stacked two-site
+// wavefunction Psi_g, the stacked right operators, the X intermediates; one
+// matrix for all left-operator blocks), each described by one tensor map.  A
+// K step of a tile is then two TMA box copies (A: 128 rows x 64 columns, B: n
+// rows x 64 columns, 128-byte swizzle, zero fill outside the matrix) that
+// complete on the stage's mbarrier by transaction count: no producer threads
+// copy data, and a ragged edge costs nothing but the zero fill.
+//
+// Persistent and warp-specialised, one CTA per SM (192 KB shared memory ring,
+// all 512 tensor-memory columns):
+//   warp 0     one thread: waits for a free stage, posts the expected bytes and
+//              the stage's MMA parameters, issues the two box copies
+//   warp 1     one thread issues tcgen05.mma (M = 128, N = n, K = 16 per
+//              instruction; instructions past the term's K are skipped) and
+//              commits to the stage's empty barrier / the accumulator's full
+//              barrier
+//   warps 2-5  epilogue: tcgen05.ld of their 32 tensor-memory lanes; BF16 rows
+//              scattered through a row map (X intermediates) or FP32 vector
+//              reductions (sigma^T, several tiles may add into one block)
+// Two (store mode, N <= 256) or four (reduce mode, N <= 128) accumulators let
+// the epilogue of one tile overlap the MMAs of the next.  Every wait is
+// bounded: on timeout the CTA raises a shared abort flag, records an error,
+// waits (bounded) for the copies it issued, frees its tensor memory and returns.
+#include "kernels_tma.hpp"
+
+#include <cuda_bf16.h>
+
+#include <atomic>
+#include <cstdint>
+#include <mutex>
+
+namespace gbdmrg {
+
+long tc_launch_count();
+void count_tc_launches(long n);
+
+namespace {
+
+constexpr int TM_THREADS = 192;
+constexpr int TM_BOX_K = 64;                       // columns per box (128 bytes)
+constexpr int TM_A_BYTES = 128 * TM_BOX_K * 2;     // 16 KB
+constexpr long TM_WAIT_LIMIT = 1L << 24;
+
+template <int MODE>
+struct TmCfg {
+  static constexpr int NMAX = MODE == TM_MODE_STORE_BF16 ? 256 : 128;
+  static constexpr int NACC = 512 / NMAX;
+  static constexpr int B_BYTES = NMAX * TM_BOX_K * 2;
+  static constexpr int STAGE_BYTES = TM_A_BYTES + B_BYTES;
+  static constexpr int STAGES = (192 * 1024) / STAGE_BYTES;  // 4 (store) or 6 (reduce)
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+};
+constexpr int TM_MAX_STAGES = 6, TM_MAX_ACC = 4;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// instruction descriptor: D f32, A/B bf16, both K-major, M = 128, N = n
+__device__ __forceinline__ uint32_t idesc_bf16(int n, bool negA) {
+  uint32_t d = 0;
+  d |= 1u << 4;
+  d |= 1u << 7;
+  d |= 1u << 10;
+  if (negA) d |= 1u << 13;
+  d |= (uint32_t)(n >> 3) << 17;
+  d |= (uint32_t)(128 >> 4) << 24;
+  return d;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// bounded parity wait; gives up when the CTA-wide abort flag is raised
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+  for (long it = 0; it < TM_WAIT_LIMIT; ++it) {
+    if (mbar_test(b, parity)) return true;
+    if ((it & 1023) == 1023 && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+          dst),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void red_add_v4(float* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(p), "f"(__uint_as_float(a)),
+               "f"(__uint_as_float(b)), "f"(__uint_as_float(c)), "f"(__uint_as_float(d))
+               : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(uint32_t lo, uint32_t hi) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(__uint_as_float(lo), __uint_as_float(hi));
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(TM_THREADS, 1)
+    gemm_tma_kernel(const TmTile* __restrict__ tiles, int ntiles, const TmTerm* __restrict__ terms,
+                    const CUtensorMap* __restrict__ maps, const long* __restrict__ rowmap, void* __restrict__ out,
+                    int* __restrict__ err) {
+  constexpr int S = TmCfg<MODE>::STAGES;
+  constexpr int STAGE_BYTES = TmCfg<MODE>::STAGE_BYTES;
+  constexpr int NACC = TmCfg<MODE>::NACC;
+  constexpr int NMAX = TmCfg<MODE>::NMAX;
+  extern __shared__ uint8_t dsm[];
+  __shared__ __align__(8) uint64_t full_b[TM_MAX_STAGES], empty_b[TM_MAX_STAGES], tfull_b[TM_MAX_ACC],
+      tempty_b[TM_MAX_ACC];
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  // per stage: instruction descriptor, K=16 steps, first/last K step of the tile
+  __shared__ uint32_t meta_id[TM_MAX_STAGES];
+  __shared__ int meta_nk[TM_MAX_STAGES], meta_first[TM_MAX_STAGES], meta_last[TM_MAX_STAGES];
+  const uint32_t base = (smem_u32(dsm) + 1023u) & ~1023u;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (warp == 2) {  // an epilogue warp (all lanes take the same path) owns the tensor memory
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+  }
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full_b[s], 1);  // the producer's arrive (with the expected bytes)
+      mbar_init(&empty_b[s], 1);
+    }
+    for (int a = 0; a < NACC; ++a) {
+      mbar_init(&tfull_b[a], 1);
+      mbar_init(&tempty_b[a], 128);
+    }
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+  const uint32_t tmem = tmem_base_sh;
+  volatile int* abort_flag = &abort_sh;
+
+  if (warp == 0) {
+    // ---------------- TMA producer (one thread)
+    if (lane == 0) {
+      long j = 0;  // K steps issued
+      bool ok = true;
+      for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
+        const TmTile tl = tiles[ti];
+        const uint32_t bbytes = (uint32_t)tl.n * TM_BOX_K * 2;
+        for (int t = tl.t0; t < tl.t1 && ok; ++t) {
+          const TmTerm tm = terms[t];
+          const uint32_t id = idesc_bf16(tl.n, tm.neg != 0);
+          const CUtensorMap* ma = maps + tm.amap;
+          const CUtensorMap* mb = maps + tm.bmap;
+          for (int k0 = 0; k0 < tm.k; k0 += TM_BOX_K) {
+            const int s = (int)(j % S);
+            if (j >= S && !mbar_wait(&empty_b[s], (uint32_t)(((j / S) - 1) & 1), abort_flag)) {
+              ok = false;
+              break;
+            }
+            meta_id[s] = id;
+            meta_nk[s] = min(TM_BOX_K / 16, (tm.k - k0) / 16);
+            meta_first[s] = (t == tl.t0 && k0 == 0) ? 1 : 0;
+            meta_last[s] = (t + 1 == tl.t1 && k0 + TM_BOX_K >= tm.k) ? 1 : 0;
+            const uint32_t sa = base + s * STAGE_BYTES;
+            mbar_arrive_expect_tx(&full_b[s], TM_A_BYTES + bbytes);
+            tma_load_2d(sa, ma, tm.ax + k0, tm.ay, &full_b[s]);
+            tma_load_2d(sa + TM_A_BYTES, mb, tm.bx + k0, tm.by, &full_b[s]);
+            ++j;
+          }
+        }
+      }
+      // every issued copy must land before the CTA may exit: the last (up to S)
+      // issued stages complete their full phase when their bytes arrive
+      for (long q = j - 1; q >= 0 && q >= j - S; --q) {
+        const int s = (int)(q % S);
+        for (long it = 0; it < TM_WAIT_LIMIT && !mbar_test(&full_b[s], (uint32_t)((q / S) & 1)); ++it) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer (one thread)
+    if (lane == 0) {
+      long j = 0;
+      int it = 0;
+      bool ok = true;
+      for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x, ++it) {
+        const int acc = it % NACC;
+        if (it >= NACC && !mbar_wait(&tempty_b[acc], (uint32_t)(((it / NACC) - 1) & 1), abort_flag)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+        const uint32_t dacc = tmem + (uint32_t)(acc * NMAX);
+        for (;;) {
+          const int s = (int)(j % S);
+          if (!mbar_wait(&full_b[s], (uint32_t)((j / S) & 1), abort_flag)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+          const uint32_t id = meta_id[s];
+          const int nk = meta_nk[s], first = meta_first[s], last = meta_last[s];
+          const uint32_t sa = base + s * STAGE_BYTES;
+          for (int kk = 0; kk < nk; ++kk) {
+            const uint64_t ad = sdesc(sa + kk * 32), bd = sdesc(sa + TM_A_BYTES + kk * 32);
+            const uint32_t accum = (first && kk == 0) ? 0u : 1u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dacc),
+                "l"(ad), "l"(bd), "r"(id), "r"(accum));
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+              smem_u32(&empty_b[s])));
+          ++j;
+          if (last) break;
+        }
+        if (!ok) break;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+            smem_u32(&tfull_b[acc])));
+      }
+    }
+  } else {
+    // ---------------- epilogue (warps 2-5: tensor-memory lanes 32 * (warp % 4) ...)
+    const int sub = warp & 3;
+    const int r = sub * 32 + lane;  // row of the tile
+    int it = 0;
+    for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x, ++it) {
+      const TmTile tl = tiles[ti];
+      const int acc = it % NACC;
+      bool ok = mbar_wait(&tfull_b[acc], (uint32_t)((it / NACC) & 1), abort_flag);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+      long dst = -1;
+      if (MODE == TM_MODE_STORE_BF16) {
+        dst = rowmap[tl.rowmap_off + r];
+      } else if (r < tl.m_valid) {
+        dst = tl.out_off + (long)r * tl.ldo;
+      }
+      for (int c0 = 0; c0 < tl.n; c0 += 32) {
+        uint32_t v[32];
+        const uint32_t taddr = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(acc * NMAX + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+              "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+              "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+              "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (dst < 0) continue;
+        const int nv = min(32, tl.n - c0);  // a multiple of 16
+        if (MODE == TM_MODE_STORE_BF16) {
+          __nv_bfloat16* p = reinterpret_cast<__nv_bfloat16*>(out) + dst + tl.out_off + c0;
+#pragma unroll
+          for (int q = 0; q < 32; q += 8) {
+            if (q >= nv) break;
+            uint4 w;
+            w.x = pack_bf16x2(v[q], v[q + 1]);
+            w.y = pack_bf16x2(v[q + 2], v[q + 3]);
+            w.z = pack_bf16x2(v[q + 4], v[q + 5]);
+            w.w = pack_bf16x2(v[q + 6], v[q + 7]);
+            *reinterpret_cast<uint4*>(p + q) = w;
+          }
+        } else {
+          float* p = reinterpret_cast<float*>(out) + dst + c0;
+#pragma unroll
+          for (int q = 0; q < 32; q += 4) {
+            if (q >= nv) break;
+            red_add_v4(p + q, v[q], v[q + 1], v[q + 2], v[q + 3]);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+      mbar_arrive(&tempty_b[acc]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+  __syncthreads();
+  if (tid == 0 && abort_sh) atomicExch(err, 1);
+  if (warp == 2) {
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(512));
+  }
+}
+
+template <int MODE>
+cudaError_t launch_mode(const TmTile* d_tiles, int ntiles, const TmTerm* d_terms, const CUtensorMap* d_maps,
+                        const long* d_rowmap, void* out, int* d_err, cudaStream_t s) {
+  static const int nsm = [] {
+    if (cudaFuncSetAttribute(gemm_tma_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TmCfg<MODE>::SMEM) !=
+        cudaSuccess)
+      return -1;
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 148;
+  }();
+  if (nsm < 0) return cudaErrorInvalidValue;
+  const int grid = ntiles < nsm ? ntiles : nsm;
+  count_tc_launches(1);
+  gemm_tma_kernel<MODE><<<grid, TM_THREADS, TmCfg<MODE>::SMEM, s>>>(d_tiles, ntiles, d_terms, d_maps, d_rowmap, out,
+                                                                     d_err);
+  return cudaGetLastError();
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encoder() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return (EncodeTiledFn) nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+}  // namespace
+
+int tma_max_n(int mode) { return mode == TM_MODE_STORE_BF16 ? 256 : 128; }
+
+cudaError_t launch_gemm_tma(int mode, const TmTile* d_tiles, int ntiles, const TmTerm* d_terms,
+                            const CUtensorMap* d_maps, const long* d_rowmap, void* out, int* d_err, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (mode == TM_MODE_STORE_BF16)
+    return launch_mode<TM_MODE_STORE_BF16>(d_tiles, ntiles, d_terms, d_maps, d_rowmap, out, d_err, s);
+  if (mode == TM_MODE_REDUCE_F32)
+    return launch_mode<TM_MODE_REDUCE_F32>(d_tiles, ntiles, d_terms, d_maps, d_rowmap, out, d_err, s);
+  return cudaErrorInvalidValue;
+}
+
+bool encode_bf16_map(CUtensorMap* out, const void* base, uint64_t rows, uint64_t cols, uint64_t ld,
+                     uint32_t box_rows) {
+  EncodeTiledFn fn = encoder();
+  if (!fn || rows == 0 || cols == 0 || (ld * 2) % 16 != 0 || ((uintptr_t)base & 15) != 0 || box_rows == 0 ||
+      box_rows > 256)
+    return false;
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)TM_BOX_K, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace gbdmrg

@@ -1,0 +1,55 @@
+// TMA-staged tensor-core grouped GEMM (tcgen05, BF16 in, FP32 accumulate) for
+// the single-pass sigma vector of the group-stacked layout.
+#pragma once
+#include <cuda.h>  // CUtensorMap (type only; the encoder is reached through the runtime)
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace gbdmrg {
+
+// One term of an output tile: C[128 x n] (-)= A[128 x k] B[n x k]^T, where A is the
+// box of rows [ay, ay + 128) and columns [ax, ax + k) of tensor map amap and B the
+// rows [by, by + n) and columns [bx, bx + k) of tensor map bmap (both BF16,
+// row-major, 128-byte swizzled boxes of 64 columns; rows or columns outside a
+// map's extent read as zero).  k is a multiple of 16; columns of a 64-wide box
+// past k are loaded but never multiplied.  The B map's box height must be the
+// tile's n.
+struct TmTerm {
+  int amap, bmap;
+  int ax, ay, bx, by;
+  int k, neg;
+};
+
+// Output tile over the terms [t0, t1).  n: MMA width (multiple of 16, <= the
+// kernel's maximum).
+//   store mode (X intermediates, BF16): row r of the tile goes to out + rowmap[rowmap_off + r]
+//     + col0, columns [0, n); rowmap entries < 0 are skipped;
+//   reduce mode (sigma^T, FP32): rows r < m_valid are added (vector reductions) to
+//     out + out_off + r * ldo, columns [0, n).
+struct TmTile {
+  int t0, t1;
+  int n, m_valid;
+  int ldo, pad;
+  long out_off;
+  long rowmap_off;
+};
+
+constexpr int TM_MODE_STORE_BF16 = 1, TM_MODE_REDUCE_F32 = 2;
+
+// maps: device array of encoded tensor maps (64-byte aligned).  err: set to 1 if a
+// bounded wait ran out (the CTA then stops, lets its copies land and frees its
+// tensor memory).
+cudaError_t launch_gemm_tma(int mode, const TmTile* d_tiles, int ntiles, const TmTerm* d_terms,
+                            const CUtensorMap* d_maps, const long* d_rowmap, void* out, int* d_err,
+                            cudaStream_t s);
+// maximum MMA width of a mode (256 for the BF16 store mode, 128 for the reduce mode)
+int tma_max_n(int mode);
+
+// Host: encode a 2D BF16 tensor map over a row-major matrix (rows x cols, leading
+// dimension ld elements, ld * 2 a multiple of 16 bytes, base 16-byte aligned), box
+// of 64 columns x box_rows rows, 128-byte swizzle.  Returns false on failure.
+bool encode_bf16_map(CUtensorMap* out, const void* base, uint64_t rows, uint64_t cols, uint64_t ld,
+                     uint32_t box_rows);
+
+}  // namespace gbdmrg
