@@ -263,7 +263,7 @@ def run_ours(args, rank, world, local_rank):
 
     with_fp64_fallback(lambda: ctx.prepare(k))
     nnz = ctx.nnz
-    plan_stats = ctx.plan_stats() if args.precision == 4 else None
+    plan_stats = ctx.plan_stats() if args.precision >= 4 else None
     setup_s = time.perf_counter() - t_setup
     setup_launches = G.kernel_launches()
     dav = args.dav_iters
@@ -334,7 +334,7 @@ def run_ours(args, rank, world, local_rank):
     achieved_alg = sig_fl / sig_s / 1e12 if sig_s > 0 else None
     # products the tensor cores execute per algorithmic multiply-add: 1 (one BF16
     # pass) or 6 (three BF16 slices, products s_i t_j with i + j <= 2)
-    nprod = {0: 1, 1: 1, 2: 6, 3: 3, 4: 1}[args.precision]
+    nprod = {0: 1, 1: 1, 2: 6, 3: 3, 4: 1, 5: 6, 6: 3}[args.precision]
     fp64_cmp = None
     if args.precision > 0 and args.compare_fp64:
         # full-size checks (outside the timed region): the tensor-core H_eff.psi of the
@@ -390,7 +390,7 @@ def run_ours(args, rank, world, local_rank):
                 "products_per_multiply_add": nprod,
                 "peak_note": f"{src} bf16 dense, sustained (kernel timed inside a long step); achieved and frac "
                              f"count algorithmic flops only"}
-        dtype = {1: "bf16", 2: "bf16x3", 3: "bf16x2", 4: "bf16"}[args.precision]
+        dtype = {1: "bf16", 2: "bf16x3", 3: "bf16x2", 4: "bf16", 5: "bf16x3", 6: "bf16x2"}[args.precision]
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -555,9 +555,9 @@ def main():
     ap.add_argument("--workload", default="k40_m2000", choices=sorted(WORKLOADS))
     ap.add_argument("--dav-iters", type=int, default=16,
                     help="Davidson iterations per step (sweeps at K=24 averaged ~20 per site)")
-    ap.add_argument("--precision", type=int, default=2, choices=[0, 1, 2, 3, 4],
+    ap.add_argument("--precision", type=int, default=2, choices=[0, 1, 2, 3, 4, 5, 6],
                     help="0 FP64 units, 1 tensor cores one BF16 pass, 2 tensor cores three BF16 slices, 3 two slices, "
-                         "4 one BF16 pass on the TMA-staged work lists")
+                         "4, 5, 6 one pass, three and two slices on the TMA-staged work lists")
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -96,16 +96,26 @@ gbdmrg_status gbdmrg_get_bond(gbdmrg_ctx* ctx, int32_t bond, int32_t* D, int32_t
  * H_eff.psi, X_beta = psi Rt_beta^T of Eq. Hpartition's right factor, as one
  * dense GEMM per quantum-number group of the cut over all bond states, its
  * operands copied by the Tensor Memory Accelerator from a few large matrices;
- * stage 2 as long contractions over the operator terms).  Environments,
- * Davidson, decimation stay FP64. */
+ * stage 2 as long contractions over the operator terms); 5 and 6 = the same
+ * work lists with three and two BF16 slices per operand (as 2 and 3).
+ * Environments, Davidson, decimation stay FP64. */
 gbdmrg_status gbdmrg_set_precision(gbdmrg_ctx* ctx, int32_t precision);
 
-/* Device memory (MB) for the X intermediates of the precision-4 work lists
+/* Device memory (MB) for the X intermediates of the precision 4-6 work lists
  * (default 65536): the bond states are processed in chunks whose intermediates
  * fit this budget (each chunk one stage-1 and one stage-2 launch).  Takes effect
  * at the next gbdmrg_prepare / gbdmrg_plan.  EINVAL for megabytes <= 0. */
 gbdmrg_status gbdmrg_set_tma_budget(gbdmrg_ctx* ctx, int64_t megabytes);
-/* Work-list statistics of the prepared precision-4 H_eff.psi (zeros for other
+/* Refinement of the Davidson solve of every later tensor-core two-site step
+ * (gbdmrg_step, gbdmrg_run; not part of the paper, which names no eigensolver):
+ * after the solve with the operator of the context's precision, its Ritz vector
+ * starts a second Davidson solve with the operator of `precision` (0 FP64 with
+ * every W-contracted sum formed again on the FP64 units, or 1-6), whose residual
+ * decides convergence and whose eigenvalue the step reports; it takes at most
+ * max_iters iterations of the step's budget.  precision -1 turns it off (the
+ * default).  EINVAL for precision outside -1..6 or max_iters < 1. */
+gbdmrg_status gbdmrg_set_refinement(gbdmrg_ctx* ctx, int32_t precision, int32_t max_iters);
+/* Work-list statistics of the prepared precision 4-6 H_eff.psi (zeros for other
  * precisions): out[0] stage-1 tiles, [1] stage-1 64-wide K steps, [2] stage-2
  * tiles, [3] stage-2 K steps, [4] stage-1 and [5] stage-2 tensor-core flops as
  * executed (128-row tiles, blocks padded to 16), [6] bytes of the X
@@ -300,7 +310,8 @@ typedef struct {
   const double* dav_tol;
   int32_t dav_max_iter;
   int32_t precision; /* as gbdmrg_set_precision: 0 FP64, 1 BF16 pass, 2 BF16 x3, 3 BF16 x2 slices,
-                        4 BF16 pass on the TMA-staged work lists */
+                        4, 5, 6 one pass, three and two slices on the TMA-staged
+                        work lists */
 } gbdmrg_schedule;
 
 /* Run the sweeps from the current MPS (brought to right-canonical form first).

@@ -59,6 +59,7 @@ SIGNATURES = {
     "gbdmrg_set_stage1_stacked": (C.c_int, [_P, _I32]),
     "gbdmrg_set_tma_budget": (C.c_int, [_P, C.c_int64]),
     "gbdmrg_plan_stats": (C.c_int, [_P, _PD]),
+    "gbdmrg_set_refinement": (C.c_int, [_P, _I32, _I32]),
     "gbdmrg_set_tc_combos": (C.c_int, [_P, _I32, C.c_int64]),
     "gbdmrg_autotune": (C.c_int, [_I32, C.POINTER(_P), _I32, _PD, _I32, _PI32, _I32, _PD, _PD, _PI32]),
     "gbdmrg_plan": (C.c_int, [_P, _I32]),
@@ -385,11 +386,15 @@ class Context:
         self._check(self.lib.gbdmrg_set_stage1_stacked(self.h, int(stacked)), "set_stage1_stacked")
 
     def set_tma_budget(self, megabytes: int):
-        """Device memory (MB) for the X intermediates of one precision-4 H_eff.psi chunk."""
+        """Device memory (MB) for the X intermediates of one precision 4-6 H_eff.psi chunk."""
         self._check(self.lib.gbdmrg_set_tma_budget(self.h, int(megabytes)), "set_tma_budget")
 
+    def set_refinement(self, precision: int, max_iters: int = 8):
+        """Second Davidson solve of each tensor-core step with the operator of `precision` (-1: off)."""
+        self._check(self.lib.gbdmrg_set_refinement(self.h, int(precision), int(max_iters)), "set_refinement")
+
     def plan_stats(self) -> dict:
-        """Work-list statistics of the prepared precision-4 H_eff.psi (see gbdmrg_plan_stats)."""
+        """Work-list statistics of the prepared precision 4-6 H_eff.psi (see gbdmrg_plan_stats)."""
         out = np.zeros(9)
         self._check(self.lib.gbdmrg_plan_stats(self.h, _dptr(out)), "plan_stats")
         keys = ["stage1_tiles", "stage1_ksteps", "stage2_tiles", "stage2_ksteps", "stage1_exec_flops",
@@ -407,8 +412,8 @@ class Context:
         return t.value, b.value
 
     def set_precision(self, mode: int):
-        """0 FP64, 1 tensor-core BF16 single pass, 2 BF16 x3 slices, 3 BF16 x2 slices,
-        4 BF16 single pass on the TMA-staged work lists."""
+        """0 FP64, 1 tensor-core BF16 single pass, 2 BF16 x3 slices, 3 BF16 x2 slices;
+        4, 5, 6: single pass, three and two slices on the TMA-staged work lists."""
         self._check(self.lib.gbdmrg_set_precision(self.h, mode), "set_precision")
 
     def prepare(self, k: int):

@@ -226,7 +226,7 @@ gbdmrg_status gbdmrg_get_bond(gbdmrg_ctx* ctx, int32_t bond, int32_t* D, int32_t
 }
 
 gbdmrg_status gbdmrg_set_precision(gbdmrg_ctx* ctx, int32_t precision) {
-  if (!ctx || precision < 0 || precision > 4) return GBDMRG_EINVAL;
+  if (!ctx || precision < 0 || precision > 6) return GBDMRG_EINVAL;
   return guard(ctx, [&] {
     ctx->c.precision = precision;
     ctx->c.prepared = -1;
@@ -313,6 +313,14 @@ gbdmrg_status gbdmrg_set_tma_budget(gbdmrg_ctx* ctx, int64_t megabytes) {
   return guard(ctx, [&] {
     ctx->c.tma_budget_mb = (long)megabytes;
     ctx->c.prepared = -1;
+  });
+}
+
+gbdmrg_status gbdmrg_set_refinement(gbdmrg_ctx* ctx, int32_t precision, int32_t max_iters) {
+  if (!ctx || precision < -1 || precision > 6 || max_iters < 1) return GBDMRG_EINVAL;
+  return guard(ctx, [&] {
+    ctx->c.refine_precision = precision;
+    ctx->c.refine_iters = max_iters;
   });
 }
 
@@ -625,7 +633,7 @@ gbdmrg_status gbdmrg_run(gbdmrg_ctx* ctx, const gbdmrg_schedule* s, double* ener
       if (s->M[i] <= 0) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "M must be positive");
       if (!(s->dav_tol[i] > 0)) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "dav_tol must be positive");
     }
-    if (s->precision < 0 || s->precision > 4) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "precision must be 0 to 4");
+    if (s->precision < 0 || s->precision > 6) throw gbdmrg::Error(gbdmrg::ST_EINVAL, "precision must be 0 to 6");
     ctx->c.precision = s->precision;
     ctx->stats = gbdmrg::SweepStats();
     gbdmrg::run_sweeps(ctx->c, s->nsweeps, s->M, s->dav_tol, s->dav_max_iter > 0 ? s->dav_max_iter : 200,

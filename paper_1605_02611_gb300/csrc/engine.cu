@@ -790,8 +790,8 @@ void build_sigma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) 
   P.build(Lb, Rb);
   plan.in.alloc(P.nnz, c.stream);
   plan.out.alloc(P.nnz, c.stream);
-  if (c.precision == 4) {
-    build_tma_plan(c, lt, rt, k, plan);
+  if (c.precision >= 4) {
+    build_tma_plan(c, lt, rt, k, plan, c.precision == 4 ? 1 : c.precision == 5 ? 3 : 2);
     return;
   }
   if (c.precision > 0) {
@@ -1016,56 +1016,6 @@ void prepare_two_site(Context& c, int k) {
 
 // ---------------------------------------------------------------- Davidson
 
-// cyclic Jacobi for a small symmetric matrix (row-major n x n); eigenvalues
-// ascending in w, eigenvectors as columns of V
-static void jacobi_eigh(int n, std::vector<double> a, std::vector<double>& w, std::vector<double>& V) {
-  V.assign((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
-  for (int sweep = 0; sweep < 100; ++sweep) {
-    double off = 0, tot = 0;
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j) {
-        tot += a[i * n + j] * a[i * n + j];
-        if (i != j) off += a[i * n + j] * a[i * n + j];
-      }
-    if (off <= 1e-30 * tot || off == 0.0) break;
-    for (int p = 0; p < n; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        double apq = a[p * n + q];
-        if (std::fabs(apq) < 1e-300) continue;
-        double app = a[p * n + p], aqq = a[q * n + q];
-        double theta = (aqq - app) / (2 * apq);
-        double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1));
-        double cs = 1 / std::sqrt(t * t + 1), sn = t * cs;
-        for (int k = 0; k < n; ++k) {
-          double akp = a[k * n + p], akq = a[k * n + q];
-          a[k * n + p] = cs * akp - sn * akq;
-          a[k * n + q] = sn * akp + cs * akq;
-        }
-        for (int k = 0; k < n; ++k) {
-          double apk = a[p * n + k], aqk = a[q * n + k];
-          a[p * n + k] = cs * apk - sn * aqk;
-          a[q * n + k] = sn * apk + cs * aqk;
-        }
-        for (int k = 0; k < n; ++k) {
-          double vkp = V[k * n + p], vkq = V[k * n + q];
-          V[k * n + p] = cs * vkp - sn * vkq;
-          V[k * n + q] = sn * vkp + cs * vkq;
-        }
-      }
-  }
-  std::vector<int> ord(n);
-  std::iota(ord.begin(), ord.end(), 0);
-  std::sort(ord.begin(), ord.end(), [&](int x, int y) { return a[x * n + x] < a[y * n + y]; });
-  w.resize(n);
-  std::vector<double> V2((size_t)n * n);
-  for (int j = 0; j < n; ++j) {
-    w[j] = a[ord[j] * n + ord[j]];
-    for (int i = 0; i < n; ++i) V2[i * n + j] = V[i * n + ord[j]];
-  }
-  V.swap(V2);
-}
-
 struct DotHelper {
   DArr<double> part, out;
   int nblk = 128;
@@ -1084,10 +1034,17 @@ struct DotHelper {
   }
 };
 
+// Davidson on the device: the subspace vectors, their sigma vectors, the projected
+// matrix G, the Rayleigh-Ritz eigenproblem (rr_kernel, FP64 Jacobi), the Ritz
+// vector, the residual, the correction and its orthogonalisation all stay in device
+// memory.  The host reads three scalars per iteration (Ritz value, residual norm and
+// norm of the new direction, one 24-byte copy) to decide convergence, and the sigma
+// timings (CUDA events) once at the end.
 double davidson(Context& c, SigmaPlan& plan, const double* diag, double* psi, const DavidsonOpts& o, int* iters) {
   const long n = plan.psi.nnz;
-  const int ms = (int)std::max<long>(2, std::min<long>(o.max_sub, n));
-  DArr<double> V, S, x, hx, r, t, coef;
+  const int ms = (int)std::max<long>(2, std::min<long>(std::min(o.max_sub, RR_MAX_SUB), n));
+  const int nblk = 128;
+  DArr<double> V, S, x, hx, r, t, coef, ocoef, G, part, scal;
   V.alloc((size_t)ms * n, c.stream);
   S.alloc((size_t)ms * n, c.stream);
   x.alloc(n, c.stream);
@@ -1095,119 +1052,160 @@ double davidson(Context& c, SigmaPlan& plan, const double* diag, double* psi, co
   r.alloc(n, c.stream);
   t.alloc(n, c.stream);
   coef.alloc(ms, c.stream);
-  DotHelper dh;
-  dh.init(ms, c.stream);
-  std::vector<double> G((size_t)ms * ms, 0.0);
+  ocoef.alloc(ms + 1, c.stream);
+  G.alloc((size_t)ms * ms, c.stream);
+  part.alloc((size_t)(ms + 1) * nblk, c.stream);
+  // scal: [0] Ritz value, [1] |r|^2, [2] |t|^2, [3] |psi|^2, [4] |x|^2
+  scal.alloc(8, c.stream);
+  cuda_check(cudaMemsetAsync(G.p, 0, G.n * sizeof(double), c.stream), "memset");
+  double* th_d = scal.p;
+  // sigma vectors timed with CUDA events on the context stream, read after the solve
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
+  auto event = [&]() {
+    cudaEvent_t e;
+    cuda_check(cudaEventCreate(&e), "event");
+    return e;
+  };
+  auto release_events = [&]() {
+    for (auto& pr : evs) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+    evs.clear();
+  };
   auto sigma_of = [&](const double* in, double* out) {
-    cuda_check(cudaEventRecord(c.ev0, c.stream), "record");
+    evs.push_back({event(), event()});
+    cuda_check(cudaEventRecord(evs.back().first, c.stream), "record");
     run_sigma(c, plan, in, out);
-    cuda_check(cudaEventRecord(c.ev1, c.stream), "record");
-    cuda_check(cudaEventSynchronize(c.ev1), "sync");
-    float ms = 0;
-    cuda_check(cudaEventElapsedTime(&ms, c.ev0, c.ev1), "elapsed");
-    if (plan.tensor() && plan_error(c, plan)) throw Error(ST_ETIMEOUT, "tensor-core GEMM: a bounded wait ran out");
-    c.sigma_time_total += 1e-3 * ms;
+    cuda_check(cudaEventRecord(evs.back().second, c.stream), "record");
     c.sigma_flops_total += plan.flops;
     c.sigma_calls++;
   };
-  double nrm = std::sqrt(dh.dots(c, psi, 0, 1, psi, n)[0]);
-  if (!(nrm > 0) || !std::isfinite(nrm)) throw Error(ST_EINVAL, "Davidson: zero or non-finite start vector");
-  launch_axpby(n, 1.0 / nrm, psi, 0.0, V.p, c.stream);
-  sigma_of(V.p, S.p);
-  G[0] = dh.dots(c, V.p, 0, 1, S.p, n)[0];
-  int m = 1;
-  double theta = G[0];
+  auto read = [&](int i0, int cnt, double* h) {
+    cuda_check(cudaMemcpyAsync(h, scal.p + i0, cnt * sizeof(double), cudaMemcpyDeviceToHost, c.stream), "d2h");
+    cuda_check(cudaStreamSynchronize(c.stream), "sync");
+  };
+  auto dots = [&](const double* Vb, long ldv, int m, const double* y, double* out) {
+    launch_multidot(Vb, ldv, m, y, n, part.p, nblk, out, c.stream);
+  };
+  // two passes of classical Gram-Schmidt of t against V[0..m), then |t|^2
+  auto orthogonalise = [&](int m) {
+    for (int pass = 0; pass < 2; ++pass) {
+      dots(V.p, n, m, t.p, ocoef.p);
+      launch_sub_combine(V.p, n, m, ocoef.p, n, t.p, c.stream);
+    }
+    dots(t.p, 0, 1, t.p, scal.p + 2);
+  };
+  double h3[3] = {0, 0, 0};
   int it = 0;
-  std::vector<double> w, Y, sub;
-  double best_rn = 1e300;
-  int since_best = 0;
-  // learned preconditioner and training-pair collection
+  double theta = 0;
   const bool use_mlp = c.mlp != nullptr;
   const bool harvest = c.harvest.per_iter > 0 && c.harvest.count < c.harvest.cap;
-  if (use_mlp || harvest) {
-    c.mlp_s.reset(new MlpScratch());
-    mlp_scratch_build(*c.mlp_s, use_mlp ? c.mlp : nullptr, plan.psi, c.stream);
-    mlp_scratch_set_diag(*c.mlp_s, diag, c.stream);
-  }
-  double prev_rn = 1e300;
   std::vector<DArr<double>> sv_x, sv_r;  // saved Ritz vectors / residuals
   std::vector<double> sv_theta, sv_rn;
-  for (; it < o.max_iter; ++it) {
-    sub.assign((size_t)m * m, 0.0);
-    for (int i = 0; i < m; ++i)
-      for (int j = 0; j < m; ++j) sub[i * m + j] = 0.5 * (G[i * ms + j] + G[j * ms + i]);
-    jacobi_eigh(m, sub, w, Y);
-    theta = w[0];
-    std::vector<double> y(m);
-    for (int i = 0; i < m; ++i) y[i] = Y[i * m + 0];
-    cuda_check(cudaMemcpyAsync(coef.p, y.data(), m * sizeof(double), cudaMemcpyHostToDevice, c.stream), "h2d");
-    launch_combine_vectors(V.p, n, m, coef.p, n, x.p, c.stream);
-    launch_combine_vectors(S.p, n, m, coef.p, n, hx.p, c.stream);
-    cuda_check(cudaMemcpyAsync(r.p, hx.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "d2d");
-    launch_axpby(n, -theta, x.p, 1.0, r.p, c.stream);
-    double rn = std::sqrt(dh.dots(c, r.p, 0, 1, r.p, n)[0]);
-    if (!std::isfinite(rn))
-      throw Error(ST_ENOCONV, "Davidson: non-finite residual (iteration " + std::to_string(it) + ", subspace " +
-                                  std::to_string(m) + ", theta " + std::to_string(theta) + ")");
-    if (rn <= o.tol) break;
-    if (harvest && sv_x.size() < 7 && (it == 0 || it == 1 || it == 2 || it == 4 || it == 7 || it == 11 || it == 16)) {
-      sv_x.emplace_back();
-      sv_r.emplace_back();
-      sv_x.back().alloc(n, c.stream);
-      sv_r.back().alloc(n, c.stream);
-      cuda_check(cudaMemcpyAsync(sv_x.back().p, x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "d2d");
-      cuda_check(cudaMemcpyAsync(sv_r.back().p, r.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "d2d");
-      sv_theta.push_back(theta);
-      sv_rn.push_back(rn);
+  try {
+    dots(psi, 0, 1, psi, scal.p + 3);
+    read(3, 1, h3);
+    if (!(h3[0] > 0) || !std::isfinite(h3[0])) throw Error(ST_EINVAL, "Davidson: zero or non-finite start vector");
+    launch_scale_rsqrt(n, psi, scal.p + 3, V.p, c.stream);
+    sigma_of(V.p, S.p);
+    dots(V.p, 0, 1, S.p, ocoef.p);
+    launch_gcol(ocoef.p, 1, G.p, ms, 0, c.stream);
+    int m = 1;
+    double best_rn = 1e300;
+    int since_best = 0;
+    // learned preconditioner and training-pair collection
+    if (use_mlp || harvest) {
+      c.mlp_s.reset(new MlpScratch());
+      mlp_scratch_build(*c.mlp_s, use_mlp ? c.mlp : nullptr, plan.psi, c.stream);
+      mlp_scratch_set_diag(*c.mlp_s, diag, c.stream);
     }
-    if (o.stagnation > 0) {
-      // only near the operator's rounding floor (tensor-core sigma: ~1e-5 of |theta|)
-      if (rn < 0.9 * best_rn) {
-        best_rn = rn;
-        since_best = 0;
-      } else if (++since_best >= o.stagnation && rn < 2e-4 * std::fabs(theta)) {
-        break;
+    double prev_rn = 1e300;
+    for (; it < o.max_iter; ++it) {
+      // Rayleigh-Ritz, Ritz vector, residual, diagonal correction
+      if (!launch_rr(G.p, ms, m, coef.p, th_d, c.stream)) throw Error(ST_EINVAL, "Davidson: subspace too large");
+      launch_combine_vectors(V.p, n, m, coef.p, n, x.p, c.stream);
+      launch_combine_vectors(S.p, n, m, coef.p, n, hx.p, c.stream);
+      launch_resid(n, hx.p, x.p, th_d, r.p, c.stream);
+      dots(r.p, 0, 1, r.p, scal.p + 1);
+      launch_precond_dev(n, r.p, diag, th_d, 1e-8, t.p, c.stream);
+      // a full subspace restarts from the Ritz vector (harmless if this iteration
+      // turns out converged: x and hx are kept)
+      int mb = m;
+      if (m == ms) {
+        cuda_check(cudaMemcpyAsync(V.p, x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "d2d");
+        cuda_check(cudaMemcpyAsync(S.p, hx.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "d2d");
+        dots(x.p, 0, 1, x.p, scal.p + 4);
+        cuda_check(cudaMemsetAsync(G.p, 0, G.n * sizeof(double), c.stream), "memset");
+        launch_restart_g(G.p, th_d, scal.p + 4, c.stream);  // x normalised up to rounding
+        mb = 1;
       }
+      orthogonalise(mb);
+      read(0, 3, h3);
+      theta = h3[0];
+      const double rn = std::sqrt(h3[1]);
+      double tn = std::sqrt(h3[2]);
+      if (!std::isfinite(rn) || !std::isfinite(theta))
+        throw Error(ST_ENOCONV, "Davidson: non-finite residual (iteration " + std::to_string(it) + ", subspace " +
+                                    std::to_string(m) + ", theta " + std::to_string(theta) + ")");
+      if (rn <= o.tol) break;
+      if (harvest && sv_x.size() < 7 && (it == 0 || it == 1 || it == 2 || it == 4 || it == 7 || it == 11 || it == 16)) {
+        sv_x.emplace_back();
+        sv_r.emplace_back();
+        sv_x.back().alloc(n, c.stream);
+        sv_r.back().alloc(n, c.stream);
+        cuda_check(cudaMemcpyAsync(sv_x.back().p, x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "d2d");
+        cuda_check(cudaMemcpyAsync(sv_r.back().p, r.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "d2d");
+        sv_theta.push_back(theta);
+        sv_rn.push_back(rn);
+      }
+      if (o.stagnation > 0) {
+        // only near the operator's rounding floor (tensor-core sigma: ~1e-5 of |theta|)
+        if (rn < 0.9 * best_rn) {
+          best_rn = rn;
+          since_best = 0;
+        } else if (++since_best >= o.stagnation && rn < o.floor * std::fabs(theta)) {
+          break;
+        }
+      }
+      if (use_mlp) {
+        bool learned = false;
+        if (rn < prev_rn) learned = mlp_precondition(*c.mlp, *c.mlp_s, r.p, diag, theta, rn, t.p, c.stream);
+        if (learned) {
+          ++c.mlp_applied;
+          orthogonalise(mb);
+          read(2, 1, h3 + 2);
+          tn = std::sqrt(h3[2]);
+        } else {
+          // the diagonal correction computed above is the fallback when the residual
+          // did not decrease or the network produced a non-finite value
+          ++c.mlp_fallbacks;
+        }
+      }
+      prev_rn = rn;
+      m = mb;
+      if (!(tn > 1e-14)) break;  // subspace exhausted: the Ritz pair is exact in it
+      launch_scale_rsqrt(n, t.p, scal.p + 2, V.p + (size_t)m * n, c.stream);
+      sigma_of(V.p + (size_t)m * n, S.p + (size_t)m * n);
+      dots(V.p, n, m + 1, S.p + (size_t)m * n, ocoef.p);
+      launch_gcol(ocoef.p, m + 1, G.p, ms, m, c.stream);
+      ++m;
     }
-    bool learned = false;
-    if (use_mlp && rn < prev_rn) learned = mlp_precondition(*c.mlp, *c.mlp_s, r.p, diag, theta, rn, t.p, c.stream);
-    if (learned) {
-      ++c.mlp_applied;
-    } else {
-      // diagonal correction; also the fallback when the residual did not decrease
-      // or the network produced a non-finite value
-      if (use_mlp) ++c.mlp_fallbacks;
-      launch_precond(n, r.p, diag, theta, 1e-8, t.p, c.stream);
+    dots(x.p, 0, 1, x.p, scal.p + 4);
+    launch_scale_rsqrt(n, x.p, scal.p + 4, psi, c.stream);
+    cuda_check(cudaStreamSynchronize(c.stream), "sync");
+    for (auto& pr : evs) {
+      float ems = 0;
+      cuda_check(cudaEventElapsedTime(&ems, pr.first, pr.second), "elapsed");
+      c.sigma_time_total += 1e-3 * ems;
     }
-    prev_rn = rn;
-    if (m == ms) {  // restart from the Ritz vector
-      cuda_check(cudaMemcpyAsync(V.p, x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "d2d");
-      cuda_check(cudaMemcpyAsync(S.p, hx.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream), "d2d");
-      double xn = dh.dots(c, V.p, 0, 1, V.p, n)[0];
-      G.assign((size_t)ms * ms, 0.0);
-      G[0] = theta / xn;  // x normalised up to rounding
-      m = 1;
-    }
-    double tn = 0;
-    for (int pass = 0; pass < 2; ++pass) {
-      const auto& d = dh.dots(c, V.p, n, m, t.p, n);
-      std::vector<double> neg(m);
-      for (int i = 0; i < m; ++i) neg[i] = -d[i];
-      cuda_check(cudaMemcpyAsync(coef.p, neg.data(), m * sizeof(double), cudaMemcpyHostToDevice, c.stream), "h2d");
-      launch_combine_vectors(V.p, n, m, coef.p, n, hx.p, c.stream);
-      launch_axpby(n, 1.0, hx.p, 1.0, t.p, c.stream);
-    }
-    tn = std::sqrt(dh.dots(c, t.p, 0, 1, t.p, n)[0]);
-    if (!(tn > 1e-14)) break;  // subspace exhausted: the Ritz pair is exact in it
-    launch_axpby(n, 1.0 / tn, t.p, 0.0, V.p + (size_t)m * n, c.stream);
-    sigma_of(V.p + (size_t)m * n, S.p + (size_t)m * n);
-    const auto& g = dh.dots(c, V.p, n, m + 1, S.p + (size_t)m * n, n);
-    for (int i = 0; i <= m; ++i) G[i * ms + m] = G[m * ms + i] = g[i];
-    ++m;
+    release_events();
+  } catch (...) {
+    cudaStreamSynchronize(c.stream);
+    release_events();
+    throw;
   }
-  double xn = std::sqrt(dh.dots(c, x.p, 0, 1, x.p, n)[0]);
-  launch_axpby(n, 1.0 / xn, x.p, 0.0, psi, c.stream);
-  cuda_check(cudaStreamSynchronize(c.stream), "sync");
+  if (plan.tensor() && plan_error(c, plan)) throw Error(ST_ETIMEOUT, "tensor-core GEMM: a bounded wait ran out");
   if (harvest) {
     Harvest& H = c.harvest;
     for (size_t j = 0; j < sv_x.size() && H.count < H.cap; ++j) {
@@ -1584,7 +1582,44 @@ double two_site_step(Context& c, int k, int dir, int M, const DavidsonOpts& o, b
   lap(2);
   DavidsonOpts od = o;
   if (plan.tensor() && od.stagnation == 0) od.stagnation = 6;
+  // the residual of a one-pass BF16 operator stalls near 1e-2 |theta| (operands
+  // rounded to 8 bits); sliced operands near 1e-5
+  const bool one_pass = c.precision == 1 || c.precision == 4;
+  od.floor = one_pass ? 2e-2 : 2e-4;
+  // Refinement: after the solve with the tensor-core operator, the Ritz vector
+  // starts a second solve with the more accurate operator of precision
+  // refine_precision (the residual and the eigenvalue of that solve are those of the
+  // accurate operator); at most refine_iters iterations of the budget go to it
+  const bool refine = plan.tensor() && c.refine_precision >= 0 && c.refine_precision != c.precision;
+  if (refine) od.max_iter = std::max(1, o.max_iter - c.refine_iters);
   double e = davidson(c, plan, diag.p, psi.p, od, iters);
+  if (refine) {
+    const int keep = c.precision;
+    plan = SigmaPlan();
+    c.precision = c.refine_precision;
+    try {
+      // the sums that fed only the tensor-core sigma are formed again in FP64 for an
+      // FP64 refinement
+      if (c.precision == 0) {
+        if (dir == 0)
+          build_tilde_right(c, c.right[k + 2], k + 1, rt, true);
+        else
+          build_tilde_left(c, c.left[k], k, lt, true);
+      }
+      build_sigma_plan(c, lt, rt, k, plan);
+      DavidsonOpts o2 = o;
+      o2.max_iter = std::max(1, std::min(c.refine_iters, o.max_iter - (iters ? *iters : 0)));
+      o2.stagnation = plan.tensor() ? 6 : 0;
+      o2.floor = 2e-4;
+      int it2 = 0;
+      e = davidson(c, plan, diag.p, psi.p, o2, &it2);
+      if (iters) *iters += it2;
+    } catch (...) {
+      c.precision = keep;
+      throw;
+    }
+    c.precision = keep;
+  }
   if (psi_out)
     cuda_check(cudaMemcpyAsync(psi_out, psi.p, plan.psi.nnz * sizeof(double), cudaMemcpyDeviceToDevice, c.stream),
                "d2d");

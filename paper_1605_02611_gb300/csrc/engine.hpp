@@ -180,7 +180,7 @@ struct SigmaPlan {
   DArr<double> in, out, X;
   std::vector<GemmPlan> stage1, stage2;
   std::unique_ptr<MixedPlan, MixedDeleter> mx;
-  // single-pass tensor-core plan with TMA-staged operands (precision 4)
+  // tensor-core plan with TMA-staged operands (precisions 4-6)
   std::unique_ptr<TmaPlan, TmaDeleter> tm;
   double flops = 0;
   bool tensor() const { return mx != nullptr || tm != nullptr; }
@@ -259,13 +259,15 @@ struct Context {
   long tc_combo_min_terms = 100000;
   // 0: FP64 grouped GEMMs; 1: tensor cores, one BF16 pass; 2: tensor cores,
   // three BF16 slices (six products, about FP32 accuracy); 3: two BF16 slices
-  // (three products); 4: tensor cores, one BF16 pass on the TMA-staged plan
-  // (stage 1 as one dense GEMM per group over the stacked right operators)
+  // (three products); 4, 5, 6: tensor cores on the TMA-staged plan (stage 1 as
+  // one dense GEMM per group over the stacked right operators) with one BF16
+  // pass, three slices and two slices
   int precision = 0;
-  // precision of the Davidson refinement phase for the single-pass modes (1, 4):
-  // after the inner solve with the single-pass operator, the Ritz vector is
-  // refined with this operator (0 FP64, 2 three BF16 slices; -1: no refinement)
+  // Davidson refinement of the tensor-core steps: after the solve with the
+  // operator of `precision`, its Ritz vector starts a solve with the operator of
+  // refine_precision (-1: none), of at most refine_iters iterations
   int refine_precision = -1;
+  int refine_iters = 8;
   // X intermediates of the TMA-staged plan per chunk of bond states (MB)
   long tma_budget_mb = 65536;
   // keep host copies of tensor-core work lists (needed to fuse problems into batches)
@@ -306,7 +308,7 @@ void run_sigma(Context& c, SigmaPlan& plan, const double* x, double* y);
 void build_mixed_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, int nslices);
 void run_mixed_sigma(Context& c, SigmaPlan& plan, const double* x, double* y);
 int mixed_error(Context& c, SigmaPlan& plan);
-void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan);
+void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, int nslices);
 void run_tma_sigma(Context& c, SigmaPlan& plan, const double* x, double* y);
 // non-zero if a tensor-core launch of the plan reported a bounded wait that ran out
 // (reads and clears nothing; synchronises the context stream)
@@ -350,6 +352,8 @@ struct DavidsonOpts {
   // for this many iterations (used with the tensor-core operator, whose rounding
   // leaves a residual floor; 0 = never)
   int stagnation = 0;
+  // residual floor (relative to |theta|) below which the stagnation stop may fire
+  double floor = 2e-4;
 };
 double davidson(Context& c, SigmaPlan& plan, const double* diag, double* psi, const DavidsonOpts& o,
                 int* iters);

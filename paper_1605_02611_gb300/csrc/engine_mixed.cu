@@ -718,7 +718,9 @@ int mixed_error(Context& c, SigmaPlan& plan) {
 // Every block is padded to 16 rows and columns with zeros, so a K step of 16 never
 // mixes two blocks and padding contributes exact zeros.
 struct TmaPlan {
+  int nsl = 1;  // BF16 slices per operand (1: one pass; 2 or 3: slice products i + j < nsl)
   DArr<__nv_bfloat16> psi_b, a1, xt, lmir;
+  long x_stride = 0;  // slice stride of the X intermediates
   DArr<float> sig_t;
   long sig_total = 0;
   DArr<ConvJob> psi_jobs, a1_jobs, l_jobs;
@@ -760,7 +762,7 @@ static void check_conv_jobs(const std::vector<ConvJob>& jobs, const DArr<__nv_bf
       throw Error(ST_ECUDA, "internal: conversion job outside its buffer");
 }
 
-void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) {
+void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, int nsl) {
   const auto& mid = c.mpo.bonds[k + 1];
   Env& Lenv = *lt.env;
   Env& Renv = *rt.env;
@@ -769,8 +771,13 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) {
   const PsiLayout& P = plan.psi;
   auto* tp = new TmaPlan();
   plan.tm.reset(tp);
+  if (nsl < 1 || nsl > 3) throw Error(ST_EINVAL, "TMA plan: 1 to 3 slices");
+  tp->nsl = nsl;
   const int nL = Lb.nsec(), nR = Rb.nsec();
   const int nmid = (int)mid.size();
+  // slice pairs (i, j), i + j < nsl, largest products first
+  static const int PI[6] = {0, 0, 1, 0, 1, 2}, PJ[6] = {0, 1, 0, 2, 1, 0};
+  const int npair = nsl == 1 ? 1 : nsl == 2 ? 3 : 6;
   // ---- groups of the cut: rows (ql, n1) and columns (n2, qr), blocks padded to 16
   std::map<std::pair<int, int>, int> gidx;
   std::vector<std::pair<int, int>> gq;
@@ -825,7 +832,7 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) {
     sgoff[g] = stot;
     stot += (long)gC[g] * gR[g];
   }
-  tp->psi_b.alloc(std::max<long>(ptot, 8), c.stream);
+  tp->psi_b.alloc(std::max<long>(ptot, 8) * nsl, c.stream);
   cuda_check(cudaMemsetAsync(tp->psi_b.p, 0, tp->psi_b.n * sizeof(__nv_bfloat16), c.stream), "memset");
   tp->sig_total = std::max<long>(stot, 4);
   tp->sig_t.alloc(tp->sig_total, c.stream);
@@ -838,8 +845,8 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) {
       const auto cp = cpos[B.cs * 4 + P.b2[b]];
       if (rp[0] < 0 || rp[0] != cp[0]) throw Error(ST_ECUDA, "internal: psi block outside its group");
       const int g = rp[0];
-      pj.push_back({plan.in.p + B.off, tp->psi_b.p + goff[g] + (long)rp[1] * gC[g] + cp[1], 0, B.rows, B.cols,
-                    B.cols, gC[g], 1, 1.0, pad16(B.cols)});
+      pj.push_back({plan.in.p + B.off, tp->psi_b.p + goff[g] + (long)rp[1] * gC[g] + cp[1], std::max<long>(ptot, 8),
+                    B.rows, B.cols, B.cols, gC[g], nsl, 1.0, pad16(B.cols)});
       tp->psi_maxel = std::max<long>(tp->psi_maxel, (long)B.rows * pad16(B.cols));
       sj.push_back({tp->sig_t.p + sgoff[g] + (long)cp[1] * gR[g] + rp[1], plan.out.p + B.off, B.rows, B.cols, gR[g]});
       tp->sig_maxel = std::max<long>(tp->sig_maxel, (long)B.rows * B.cols);
@@ -890,7 +897,7 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) {
   for (int beta = 0; beta < nmid; ++beta)
     for (int gp = 0; gp < ng; ++gp)
       if (xhas[(size_t)beta * ng + gp]) xsz[beta] += (size_t)gC[gout[(size_t)beta * ng + gp]] * gR[gp];
-  const size_t budget = (size_t)std::max<long>(1, c.tma_budget_mb) * (1u << 20) / sizeof(__nv_bfloat16);
+  const size_t budget = (size_t)std::max<long>(1, c.tma_budget_mb) * (1u << 20) / (sizeof(__nv_bfloat16) * nsl);
   std::vector<std::pair<int, int>> chunks;
   for (int b0 = 0; b0 < nmid;) {
     int b1 = b0;
@@ -923,7 +930,8 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) {
     }
     maxchunk = std::max(maxchunk, (size_t)off);
   }
-  tp->xt.alloc(std::max<size_t>(maxchunk, 8), c.stream);
+  tp->x_stride = (long)std::max<size_t>(maxchunk, 8);
+  tp->xt.alloc((size_t)tp->x_stride * nsl, c.stream);
   cuda_check(cudaMemsetAsync(tp->xt.p, 0, tp->xt.n * sizeof(__nv_bfloat16), c.stream), "memset");
   // ---- A1 per g': row blocks sorted by (chunk, mask), beta order kept inside a run
   for (int gp = 0; gp < ng; ++gp)
@@ -940,7 +948,8 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) {
     a1rows[gp] = rows;
     a1tot += rows * gC[gp];
   }
-  tp->a1.alloc(std::max<long>(a1tot, 8), c.stream);
+  const long a1s = std::max<long>(a1tot, 8);
+  tp->a1.alloc(a1s * nsl, c.stream);
   cuda_check(cudaMemsetAsync(tp->a1.p, 0, tp->a1.n * sizeof(__nv_bfloat16), c.stream), "memset");
   struct Run {
     int chunk, mask;
@@ -965,8 +974,8 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) {
         const TRef& r = rt.ref[x.beta][x.n2 * 4 + n2p];
         const Block& B = Renv.cls[r.cls].blocks[x.bl[n2p]];
         const int coff = cpos[B.cs * 4 + n2p][1];
-        aconv.push_back({r.p + B.off, tp->a1.p + a1off[gp] + row * gC[gp] + coff, 0, B.rows, B.cols, B.cols, gC[gp],
-                         1, r.coef, pad16(B.cols)});
+        aconv.push_back({r.p + B.off, tp->a1.p + a1off[gp] + row * gC[gp] + coff, a1s, B.rows, B.cols, B.cols, gC[gp],
+                         nsl, r.coef, pad16(B.cols)});
         tp->a1_maxel = std::max<long>(tp->a1_maxel, (long)B.rows * pad16(B.cols));
       }
       row += x.rows;
@@ -1021,7 +1030,7 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) {
           const Block& B = L.blocks[b];
           // dst holds the row until the buffer exists
           lconv.push_back({r.p + B.off, (__nv_bfloat16*)(intptr_t)(row0 + lblk_row[r.cls][b]), 0, B.rows, B.cols,
-                           B.cols, WL, 1, scale, pad16(B.cols)});
+                           B.cols, WL, nsl, scale, pad16(B.cols)});
           tp->l_maxel = std::max<long>(tp->l_maxel, (long)B.rows * pad16(B.cols));
         }
         lrows += lop_rows[r.cls];
@@ -1031,9 +1040,13 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) {
       lrow0[beta][nn] = row0;
       lneg[beta][nn] = (a == 1.0 && r.coef < 0) ? 1 : 0;
     }
-  tp->lmir.alloc(std::max<long>(lrows * WL, 8), c.stream);
+  const long ls = std::max<long>(lrows * WL, 8);
+  tp->lmir.alloc(ls * nsl, c.stream);
   cuda_check(cudaMemsetAsync(tp->lmir.p, 0, tp->lmir.n * sizeof(__nv_bfloat16), c.stream), "memset");
-  for (ConvJob& j : lconv) j.dst = tp->lmir.p + (intptr_t)j.dst * WL;
+  for (ConvJob& j : lconv) {
+    j.dst = tp->lmir.p + (intptr_t)j.dst * WL;
+    j.slice_stride = ls;
+  }
   check_conv_jobs(lconv, tp->lmir);
   tp->l_jobs.upload(lconv, c.stream);
   tp->n_l_jobs = (int)lconv.size();
@@ -1046,16 +1059,22 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) {
     int box;
   };
   std::vector<MapInfo> minfo;
-  auto add_map = [&](const DArr<__nv_bfloat16>& buf, long off, long rows, long cols, long ld, int box_rows) {
-    if (off < 0 || rows < 1 || cols < 1 || ld < cols || ld % 8 != 0 || off % 8 != 0 ||
-        (size_t)(off + (rows - 1) * ld + cols) > buf.n)
-      throw Error(ST_ECUDA, "internal: tensor map outside its buffer");
-    CUtensorMap m;
-    if (!encode_bf16_map(&m, buf.p + off, (uint64_t)rows, (uint64_t)cols, (uint64_t)ld, (uint32_t)box_rows))
-      throw Error(ST_ECUDA, "cuTensorMapEncodeTiled failed");
-    maps.push_back(m);
-    minfo.push_back({rows, cols, box_rows});
-    return (int)maps.size() - 1;
+  // one map per slice, at consecutive indices (slice i of a map m is m + i)
+  auto add_map = [&](const DArr<__nv_bfloat16>& buf, long off, long stride, long rows, long cols, long ld,
+                     int box_rows) {
+    const int first = (int)maps.size();
+    for (int sl = 0; sl < nsl; ++sl) {
+      const long o = off + sl * stride;
+      if (o < 0 || rows < 1 || cols < 1 || ld < cols || ld % 8 != 0 || o % 8 != 0 ||
+          (size_t)(o + (rows - 1) * ld + cols) > buf.n)
+        throw Error(ST_ECUDA, "internal: tensor map outside its buffer");
+      CUtensorMap m;
+      if (!encode_bf16_map(&m, buf.p + o, (uint64_t)rows, (uint64_t)cols, (uint64_t)ld, (uint32_t)box_rows))
+        throw Error(ST_ECUDA, "cuTensorMapEncodeTiled failed");
+      maps.push_back(m);
+      minfo.push_back({rows, cols, box_rows});
+    }
+    return first;
   };
   const int n1max = tma_max_n(TM_MODE_STORE_BF16), n2max = tma_max_n(TM_MODE_REDUCE_F32);
   std::vector<std::vector<std::array<int, 3>>> nt1(ng);  // per g': (row0, width, Psi map) of the stage-1 N tiles
@@ -1066,18 +1085,19 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) {
     int r0 = 0;
     for (int p = 0; p < parts; ++p) {
       const int w = std::min(gR[gp] - r0, pad16((gR[gp] - r0 + (parts - p) - 1) / (parts - p)));
-      nt1[gp].push_back({r0, w, add_map(tp->psi_b, goff[gp], gR[gp], gC[gp], gC[gp], w)});
+      nt1[gp].push_back({r0, w, add_map(tp->psi_b, goff[gp], std::max<long>(ptot, 8), gR[gp], gC[gp], gC[gp], w)});
       r0 += w;
     }
-    a1map[gp] = add_map(tp->a1, a1off[gp], a1rows[gp], gC[gp], gC[gp], 128);
+    a1map[gp] = add_map(tp->a1, a1off[gp], a1s, a1rows[gp], gC[gp], gC[gp], 128);
   }
   std::vector<std::vector<int>> xtmap(nch, std::vector<int>(ng, -1));
   for (int ci = 0; ci < nch; ++ci)
     for (int gp = 0; gp < ng; ++gp)
-      if (xregrows[ci][gp] > 0) xtmap[ci][gp] = add_map(tp->xt, xreg[ci][gp], xregrows[ci][gp], gR[gp], gR[gp], 128);
+      if (xregrows[ci][gp] > 0)
+        xtmap[ci][gp] = add_map(tp->xt, xreg[ci][gp], tp->x_stride, xregrows[ci][gp], gR[gp], gR[gp], 128);
   std::vector<int> lmap(n2max / 16 + 1, -1);
   if (lrows > 0)
-    for (int h = 16; h <= n2max; h += 16) lmap[h / 16] = add_map(tp->lmir, 0, lrows, WL, WL, h);
+    for (int h = 16; h <= n2max; h += 16) lmap[h / 16] = add_map(tp->lmir, 0, ls, lrows, WL, WL, h);
   tp->maps.alloc(std::max<size_t>(maps.size(), 1), c.stream);
   if (!maps.empty())
     cuda_check(cudaMemcpyAsync(tp->maps.p, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
@@ -1110,9 +1130,10 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) {
               const int qrp = Rb.find(gq[gp].first + LQA[n2p], gq[gp].second + LQB[n2p]);
               const int coff = cpos[qrp * 4 + n2p][1];
               const int kk = pad16(Rb.dim[qrp]);
-              m1.push_back({a1map[gp], nt[2], coff, (int)r0, coff, nt[0], kk, 0});
-              ksum += kk;
-              st1_steps += (kk + 63) / 64;
+              for (int pr = 0; pr < npair; ++pr)
+                m1.push_back({a1map[gp] + PI[pr], nt[2] + PJ[pr], coff, (int)r0, coff, nt[0], kk, 0});
+              ksum += kk * npair;
+              st1_steps += (kk + 63) / 64 * npair;
             }
             tl.t1 = (int)m1.size();
             tl.n = nt[1];
@@ -1138,7 +1159,7 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) {
           for (const auto& cb : gcol[g]) {
             if (written.count(((long)beta * 4 + cb[0]) * nR + cb[1])) continue;
             const long e0 = xreg[ci][gp] + (xrow[(size_t)beta * ng + gp] + cb[2]) * (long)gR[gp];
-            zj.push_back({tp->xt.p + e0, (long)pad16(Rb.dim[cb[1]]) * gR[gp], 0, 1});
+            zj.push_back({tp->xt.p + e0, (long)pad16(Rb.dim[cb[1]]) * gR[gp], tp->x_stride, nsl});
           }
         }
       }
@@ -1178,6 +1199,18 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) {
             }
           }
           if (base.empty()) continue;
+          if (npair > 1) {
+            std::vector<TmTerm> all;
+            all.reserve(base.size() * npair);
+            for (const TmTerm& t : base)
+              for (int pr = 0; pr < npair; ++pr) {
+                TmTerm u = t;
+                u.amap += PI[pr];
+                u.bmap += PJ[pr];
+                all.push_back(u);
+              }
+            base.swap(all);
+          }
           long steps = 0;
           for (const TmTerm& t : base) steps += (t.k + 63) / 64;
           for (int r0 = 0; r0 < gC[g]; r0 += 128) {
@@ -1261,7 +1294,7 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) {
         throw Error(ST_ECUDA, "internal: stage-1 row map out of range");
       for (int r = 0; r < 128; ++r) {
         const long d = rowmap[(size_t)(tl.rowmap_off + r)];
-        if (d < -1 || (d >= 0 && ((size_t)(d + tl.out_off + tl.n) > tp->xt.n || (d + tl.out_off) % 8)))
+        if (d < -1 || (d >= 0 && ((size_t)(d + tl.out_off + tl.n) > (size_t)tp->x_stride || (d + tl.out_off) % 8)))
           throw Error(ST_ECUDA, "internal: stage-1 store outside the X buffer");
       }
     }
@@ -1270,7 +1303,8 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan) {
           tl.out_off + (long)(tl.m_valid - 1) * tl.ldo + tl.n > tp->sig_total)
         throw Error(ST_ECUDA, "internal: stage-2 reduction outside sigma^T");
     for (const ZeroJob& z : zj)
-      if (z.p < tp->xt.p || z.p + z.n > tp->xt.p + tp->xt.n) throw Error(ST_ECUDA, "internal: zero job outside X");
+      if (z.p < tp->xt.p || z.p + (long)(z.nsl - 1) * z.stride + z.n > tp->xt.p + tp->xt.n)
+        throw Error(ST_ECUDA, "internal: zero job outside X");
     ch.t1.upload(t1, c.stream);
     ch.m1.upload(m1, c.stream);
     ch.n1 = (int)t1.size();
@@ -1309,10 +1343,10 @@ void run_tma_sigma(Context& c, SigmaPlan& plan, const double* x, double* y) {
   cuda_check(cudaMemsetAsync(tp.sig_t.p, 0, tp.sig_total * sizeof(float), c.stream), "memset");
   for (auto& ch : tp.chunks) {
     if (ch.nz) launch_zero(ch.z.p, ch.nz, ch.zmax, c.stream);
-    cuda_check(launch_gemm_tma(TM_MODE_STORE_BF16, ch.t1.p, ch.n1, ch.m1.p, tp.maps.p, tp.rowmap.p, tp.xt.p, tp.err.p,
-                               c.stream),
+    cuda_check(launch_gemm_tma(TM_MODE_STORE_BF16, ch.t1.p, ch.n1, ch.m1.p, tp.maps.p, tp.rowmap.p, tp.xt.p, tp.nsl,
+                               tp.x_stride, tp.err.p, c.stream),
                "tma stage 1");
-    cuda_check(launch_gemm_tma(TM_MODE_REDUCE_F32, ch.t2.p, ch.n2, ch.m2.p, tp.maps.p, tp.rowmap.p, tp.sig_t.p,
+    cuda_check(launch_gemm_tma(TM_MODE_REDUCE_F32, ch.t2.p, ch.n2, ch.m2.p, tp.maps.p, tp.rowmap.p, tp.sig_t.p, 1, 0,
                                tp.err.p, c.stream),
                "tma stage 2");
   }

@@ -132,7 +132,7 @@ template <int MODE>
 __global__ void __launch_bounds__(TM_THREADS, 1)
     gemm_tma_kernel(const TmTile* __restrict__ tiles, int ntiles, const TmTerm* __restrict__ terms,
                     const CUtensorMap* __restrict__ maps, const long* __restrict__ rowmap, void* __restrict__ out,
-                    int* __restrict__ err) {
+                    int out_slices, long slice_stride, int* __restrict__ err) {
   constexpr int S = TmCfg<MODE>::STAGES;
   constexpr int STAGE_BYTES = TmCfg<MODE>::STAGE_BYTES;
   constexpr int NACC = TmCfg<MODE>::NACC;
@@ -286,16 +286,26 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
         if (dst < 0) continue;
         const int nv = min(32, tl.n - c0);  // a multiple of 16
         if (MODE == TM_MODE_STORE_BF16) {
+          // BF16 slices x = s0 + s1 + ... of the FP32 values, slice_stride elements apart
           __nv_bfloat16* p = reinterpret_cast<__nv_bfloat16*>(out) + dst + tl.out_off + c0;
+          for (int sl = 0; sl < out_slices; ++sl) {
 #pragma unroll
-          for (int q = 0; q < 32; q += 8) {
-            if (q >= nv) break;
-            uint4 w;
-            w.x = pack_bf16x2(v[q], v[q + 1]);
-            w.y = pack_bf16x2(v[q + 2], v[q + 3]);
-            w.z = pack_bf16x2(v[q + 4], v[q + 5]);
-            w.w = pack_bf16x2(v[q + 6], v[q + 7]);
-            *reinterpret_cast<uint4*>(p + q) = w;
+            for (int q = 0; q < 32; q += 8) {
+              if (q >= nv) break;
+              uint4 w;
+              w.x = pack_bf16x2(v[q], v[q + 1]);
+              w.y = pack_bf16x2(v[q + 2], v[q + 3]);
+              w.z = pack_bf16x2(v[q + 4], v[q + 5]);
+              w.w = pack_bf16x2(v[q + 6], v[q + 7]);
+              *reinterpret_cast<uint4*>(p + q) = w;
+            }
+            if (sl + 1 < out_slices) {
+              // remainders for the next slice
+#pragma unroll
+              for (int q = 0; q < 32; ++q)
+                v[q] = __float_as_uint(__uint_as_float(v[q]) - __bfloat162float(__float2bfloat16_rn(__uint_as_float(v[q]))));
+              p += slice_stride;
+            }
           }
         } else {
           float* p = reinterpret_cast<float*>(out) + dst + c0;
@@ -322,7 +332,8 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
 
 template <int MODE>
 cudaError_t launch_mode(const TmTile* d_tiles, int ntiles, const TmTerm* d_terms, const CUtensorMap* d_maps,
-                        const long* d_rowmap, void* out, int* d_err, cudaStream_t s) {
+                        const long* d_rowmap, void* out, int out_slices, long slice_stride, int* d_err,
+                        cudaStream_t s) {
   static const int nsm = [] {
     if (cudaFuncSetAttribute(gemm_tma_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TmCfg<MODE>::SMEM) !=
         cudaSuccess)
@@ -336,7 +347,7 @@ cudaError_t launch_mode(const TmTile* d_tiles, int ntiles, const TmTerm* d_terms
   const int grid = ntiles < nsm ? ntiles : nsm;
   count_tc_launches(1);
   gemm_tma_kernel<MODE><<<grid, TM_THREADS, TmCfg<MODE>::SMEM, s>>>(d_tiles, ntiles, d_terms, d_maps, d_rowmap, out,
-                                                                     d_err);
+                                                                     out_slices, slice_stride, d_err);
   return cudaGetLastError();
 }
 
@@ -361,12 +372,15 @@ EncodeTiledFn encoder() {
 int tma_max_n(int mode) { return mode == TM_MODE_STORE_BF16 ? 256 : 128; }
 
 cudaError_t launch_gemm_tma(int mode, const TmTile* d_tiles, int ntiles, const TmTerm* d_terms,
-                            const CUtensorMap* d_maps, const long* d_rowmap, void* out, int* d_err, cudaStream_t s) {
+                            const CUtensorMap* d_maps, const long* d_rowmap, void* out, int out_slices,
+                            long slice_stride, int* d_err, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
+  if (out_slices < 1 || out_slices > 3) return cudaErrorInvalidValue;
   if (mode == TM_MODE_STORE_BF16)
-    return launch_mode<TM_MODE_STORE_BF16>(d_tiles, ntiles, d_terms, d_maps, d_rowmap, out, d_err, s);
+    return launch_mode<TM_MODE_STORE_BF16>(d_tiles, ntiles, d_terms, d_maps, d_rowmap, out, out_slices, slice_stride,
+                                           d_err, s);
   if (mode == TM_MODE_REDUCE_F32)
-    return launch_mode<TM_MODE_REDUCE_F32>(d_tiles, ntiles, d_terms, d_maps, d_rowmap, out, d_err, s);
+    return launch_mode<TM_MODE_REDUCE_F32>(d_tiles, ntiles, d_terms, d_maps, d_rowmap, out, 1, 0, d_err, s);
   return cudaErrorInvalidValue;
 }
 

@@ -37,12 +37,13 @@ struct TmTile {
 
 constexpr int TM_MODE_STORE_BF16 = 1, TM_MODE_REDUCE_F32 = 2;
 
-// maps: device array of encoded tensor maps (64-byte aligned).  err: set to 1 if a
-// bounded wait ran out (the CTA then stops, lets its copies land and frees its
-// tensor memory).
+// maps: device array of encoded tensor maps (64-byte aligned).  Store mode:
+// out_slices (1-3) BF16 slices x = s0 + s1 + ... of every FP32 result, written
+// slice_stride elements apart.  err: set to 1 if a bounded wait ran out (the CTA
+// then stops, lets its copies land and frees its tensor memory).
 cudaError_t launch_gemm_tma(int mode, const TmTile* d_tiles, int ntiles, const TmTerm* d_terms,
-                            const CUtensorMap* d_maps, const long* d_rowmap, void* out, int* d_err,
-                            cudaStream_t s);
+                            const CUtensorMap* d_maps, const long* d_rowmap, void* out, int out_slices,
+                            long slice_stride, int* d_err, cudaStream_t s);
 // maximum MMA width of a mode (256 for the BF16 store mode, 128 for the reduce mode)
 int tma_max_n(int mode);
 
