@@ -41,6 +41,8 @@ WORKLOADS = {
                       ramp=[250, 500, 1000, 2000, 2000, 2000], m0=250),
     "k24_m512": dict(K=24, N=24, two_sz=0, M=512, spread=1.0, seed=1606, offdiag_std=0.1,
                      ramp=[128, 256] + [512] * 8, m0=128),
+    "k32_m1024": dict(K=32, N=32, two_sz=0, M=1024, spread=1.0, seed=1609, offdiag_std=0.1,
+                      ramp=[128, 256, 512, 1024, 1024, 1024], m0=128),
     "k16_m256": dict(K=16, N=16, two_sz=0, M=256, spread=1.0, seed=1606, offdiag_std=0.1,
                      ramp=[64, 128, 256, 256], m0=64),
 }

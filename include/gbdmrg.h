@@ -106,6 +106,14 @@ gbdmrg_status gbdmrg_set_precision(gbdmrg_ctx* ctx, int32_t precision);
  * fit this budget (each chunk one stage-1 and one stage-2 launch).  Takes effect
  * at the next gbdmrg_prepare / gbdmrg_plan.  EINVAL for megabytes <= 0. */
 gbdmrg_status gbdmrg_set_tma_budget(gbdmrg_ctx* ctx, int64_t megabytes);
+/* Arithmetic of the environment (renormalised-operator) updates of later
+ * gbdmrg_prepare / gbdmrg_step / gbdmrg_run calls (Eqs. leftrenorm/rightrenorm,
+ * prenormmatrix/prenormdec): 0 = FP64 grouped GEMMs on the FP64 units (default);
+ * 2 = both grouped GEMMs of the update on the tensor cores with every operand in
+ * three BF16 slices (six products, FP32 accumulation, intermediates as three
+ * BF16 slices of the FP32 results), the new operators stored in FP64.  EINVAL for
+ * any other value. */
+gbdmrg_status gbdmrg_set_env_precision(gbdmrg_ctx* ctx, int32_t precision);
 /* Refinement of the Davidson solve of every later tensor-core two-site step
  * (gbdmrg_step, gbdmrg_run; not part of the paper, which names no eigensolver):
  * after the solve with the operator of the context's precision, its Ritz vector

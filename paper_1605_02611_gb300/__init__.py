@@ -60,6 +60,7 @@ SIGNATURES = {
     "gbdmrg_set_tma_budget": (C.c_int, [_P, C.c_int64]),
     "gbdmrg_plan_stats": (C.c_int, [_P, _PD]),
     "gbdmrg_set_refinement": (C.c_int, [_P, _I32, _I32]),
+    "gbdmrg_set_env_precision": (C.c_int, [_P, _I32]),
     "gbdmrg_set_tc_combos": (C.c_int, [_P, _I32, C.c_int64]),
     "gbdmrg_autotune": (C.c_int, [_I32, C.POINTER(_P), _I32, _PD, _I32, _PI32, _I32, _PD, _PD, _PI32]),
     "gbdmrg_plan": (C.c_int, [_P, _I32]),
@@ -388,6 +389,10 @@ class Context:
     def set_tma_budget(self, megabytes: int):
         """Device memory (MB) for the X intermediates of one precision 4-6 H_eff.psi chunk."""
         self._check(self.lib.gbdmrg_set_tma_budget(self.h, int(megabytes)), "set_tma_budget")
+
+    def set_env_precision(self, precision: int):
+        """Environment updates: 0 FP64 units, 2 tensor cores with three BF16 slices."""
+        self._check(self.lib.gbdmrg_set_env_precision(self.h, int(precision)), "set_env_precision")
 
     def set_refinement(self, precision: int, max_iters: int = 8):
         """Second Davidson solve of each tensor-core step with the operator of `precision` (-1: off)."""

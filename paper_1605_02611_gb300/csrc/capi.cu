@@ -316,6 +316,11 @@ gbdmrg_status gbdmrg_set_tma_budget(gbdmrg_ctx* ctx, int64_t megabytes) {
   });
 }
 
+gbdmrg_status gbdmrg_set_env_precision(gbdmrg_ctx* ctx, int32_t precision) {
+  if (!ctx || (precision != 0 && precision != 2)) return GBDMRG_EINVAL;
+  return guard(ctx, [&] { ctx->c.env_precision = precision; });
+}
+
 gbdmrg_status gbdmrg_set_refinement(gbdmrg_ctx* ctx, int32_t precision, int32_t max_iters) {
   if (!ctx || precision < -1 || precision > 6 || max_iters < 1) return GBDMRG_EINVAL;
   return guard(ctx, [&] {

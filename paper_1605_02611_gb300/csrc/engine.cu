@@ -414,7 +414,7 @@ void get_site_dense(Context& c, int k, std::vector<double>& A) {
 
 // ---------------------------------------------------------------- environments
 
-static void env_alloc(Context& c, Env& e, const Bond& b, const std::vector<BondState>& st) {
+void env_alloc(Context& c, Env& e, const Bond& b, const std::vector<BondState>& st) {
   e = Env();
   e.bond = b;
   std::map<std::pair<int, int>, int> cmap;
@@ -627,6 +627,10 @@ static inline int tilde_col(const Bond& b, const OpLayout& L, int row) {
 static size_t budget_elems(Context& c) { return (size_t)c.chunk_budget_mb * (1u << 20) / sizeof(double); }
 
 void env_update_left(Context& c, Tilde& lt, const SiteT& A, int site, Env& out) {
+  if (c.env_precision == 2) {
+    env_update_tc(c, lt, A, site, out, true);
+    return;
+  }
   const auto& st = c.mpo.bonds[site + 1];
   const Bond& Lb = A.L;
   const Bond& Rb = A.R;
@@ -703,6 +707,10 @@ void env_update_left(Context& c, Tilde& lt, const SiteT& A, int site, Env& out) 
 }
 
 void env_update_right(Context& c, Tilde& rt, const SiteT& B, int site, Env& out) {
+  if (c.env_precision == 2) {
+    env_update_tc(c, rt, B, site, out, false);
+    return;
+  }
   const auto& st = c.mpo.bonds[site];
   const Bond& Lb = B.L;
   const Bond& Rb = B.R;

@@ -268,6 +268,8 @@ struct Context {
   // refine_precision (-1: none), of at most refine_iters iterations
   int refine_precision = -1;
   int refine_iters = 8;
+  // environment updates: 0 FP64 grouped GEMMs; 2 tensor cores, three BF16 slices
+  int env_precision = 0;
   // X intermediates of the TMA-staged plan per chunk of bond states (MB)
   long tma_budget_mb = 65536;
   // keep host copies of tensor-core work lists (needed to fuse problems into batches)
@@ -300,6 +302,10 @@ void build_tilde_right(Context& c, Env& R, int site, Tilde& t, bool approx = fal
 // (engine_mixed.cu); out_cls[i] is the operator class of output i
 void combos_tc(Context& c, Env& env, const std::vector<ComboOut>& outs, const std::vector<ComboTerm>& terms,
                const std::vector<int>& out_cls);
+void env_alloc(Context& c, Env& e, const Bond& b, const std::vector<BondState>& st);
+// environment update with both grouped GEMMs on the tensor cores, operands in three BF16
+// slices (engine_mixed.cu); left = true: L_{k+1} from L_k and A[k], else R_k from R_{k+1}
+void env_update_tc(Context& c, Tilde& t, const SiteT& A, int site, Env& out, bool left);
 void env_update_left(Context& c, Tilde& lt, const SiteT& A, int site, Env& out);
 void env_update_right(Context& c, Tilde& rt, const SiteT& B, int site, Env& out);
 

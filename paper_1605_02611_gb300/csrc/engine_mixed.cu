@@ -1136,6 +1136,7 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
               st1_steps += (kk + 63) / 64 * npair;
             }
             tl.t1 = (int)m1.size();
+            tl.nseg = 1;
             tl.n = nt[1];
             tl.m_valid = 128;
             tl.ldo = gR[gp];
@@ -1243,6 +1244,7 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
             ks += pd.terms[u].k;
           }
           tl.t1 = (int)m2.size();
+          tl.nseg = (int)((acc + TM_SEG_KSTEPS - 1) / TM_SEG_KSTEPS);
           t2.push_back(tl);
           st2_steps += acc;
           st2_fl += 2.0 * 128 * tl.n * ks;
@@ -1297,6 +1299,12 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
         if (d < -1 || (d >= 0 && ((size_t)(d + tl.out_off + tl.n) > (size_t)tp->x_stride || (d + tl.out_off) % 8)))
           throw Error(ST_ECUDA, "internal: stage-1 store outside the X buffer");
       }
+    }
+    for (const TmTile& tl : t2) {
+      long ks = 0;
+      for (int t = tl.t0; t < tl.t1; ++t) ks += (m2[t].k + 63) / 64;
+      if (tl.nseg != (int)((ks + TM_SEG_KSTEPS - 1) / TM_SEG_KSTEPS))
+        throw Error(ST_ECUDA, "internal: stage-2 segment count");
     }
     for (const TmTile& tl : t2)
       if (tl.m_valid < 1 || tl.m_valid > 128 || tl.out_off < 0 || tl.out_off % 4 || tl.ldo % 4 ||
@@ -1361,6 +1369,308 @@ int plan_error(Context& c, SigmaPlan& plan) {
   cuda_check(cudaMemcpyAsync(&h, p, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h");
   cuda_check(cudaStreamSynchronize(c.stream), "sync");
   return h;
+}
+
+// ---------------------------------------------------------------- environment update on the tensor cores
+
+namespace {
+
+// transposed FP64 block -> nsl BF16 slices: dst[j * ldd + i] = slices of scale * src[i * lds + j]
+// for i < rows, j < cols; zeros for rows <= i < wrows (the padded contraction columns)
+struct ConvTJob {
+  const double* src;
+  __nv_bfloat16* dst;
+  long slice_stride;
+  int rows, cols, lds, ldd, nsl, wrows;
+  double scale;
+};
+
+__global__ void convt_kernel(const ConvTJob* __restrict__ jobs) {
+  const ConvTJob jb = jobs[blockIdx.y];
+  const long n = (long)jb.cols * jb.wrows;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    const int j = (int)(e / jb.wrows), i = (int)(e % jb.wrows);
+    double v = i < jb.rows ? jb.scale * jb.src[(long)i * jb.lds + j] : 0.0;
+    __nv_bfloat16* d = jb.dst + (long)j * jb.ldd + i;
+    for (int s = 0; s < jb.nsl; ++s) {
+      const __nv_bfloat16 h = __double2bfloat16(v);
+      d[s * jb.slice_stride] = h;
+      v -= (double)__bfloat162float(h);
+    }
+  }
+}
+
+__global__ void f32_to_f64_kernel(const float* __restrict__ src, double* __restrict__ dst, long n) {
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+    dst[e] = (double)src[e];
+}
+
+}  // namespace
+
+// L_{k+1}[beta] = sum (A^{n1})^T Lt_beta^{n1 n1'} A^{n1'} (left, Eqs. leftrenorm / prenormdec) or
+// R_k[beta] = sum B^{n2} Rt_beta^{n2 n2'} (B^{n2'})^T (right), both stages as tensor-core
+// grouped GEMMs with every operand in three BF16 slices (six products, FP32 accumulation):
+//   left : stage 1 T^T_beta[n1][j, ql] = sum_{n1'} At^{n1'}[j, ql'] Lt^{n1 n1'}[ql, ql']   (At = A^T per block)
+//          stage 2 L'[qa, qa']       = sum_{n1} At^{n1}[qa, ql] T^T_beta[n1][qa', ql]
+//   right: stage 1 T_beta[n2][j, qr] = sum_{n2'} B^{n2'}[j, qr'] Rt^{n2 n2'}[qr, qr']
+//          stage 2 R'[qb, qb']       = sum_{n2} B^{n2}[qb, qr] T_beta[n2][qb', qr]
+// The intermediates are BF16 slices of the FP32 results; the new operators are
+// accumulated in FP32 and stored in FP64.
+void env_update_tc(Context& c, Tilde& t, const SiteT& A, int site, Env& out, bool left) {
+  constexpr int NSL = 3;
+  const auto& st = left ? c.mpo.bonds[site + 1] : c.mpo.bonds[site];
+  const Bond& Lb = A.L;
+  const Bond& Rb = A.R;
+  Env& env = *t.env;
+  const Bond& ob = left ? Rb : Lb;  // bond of the new operators
+  env_alloc(c, out, ob, st);
+  const int no = ob.nsec();
+  // ---- site-tensor mirror: left: At per block [d(qr) x pad8(d(ql))]; right: [d(ql) x pad8(d(qr))]
+  std::vector<long> soff(A.blocks.size());
+  long stot = 0;
+  for (size_t b = 0; b < A.blocks.size(); ++b) {
+    const Block& B = A.blocks[b];
+    soff[b] = stot;
+    stot += left ? (long)B.cols * pad8(B.rows) : (long)B.rows * pad8(B.cols);
+  }
+  const long ss = std::max<long>(stot, 8);
+  DArr<__nv_bfloat16> smir;
+  smir.alloc((size_t)ss * NSL, c.stream);
+  {
+    if (left) {
+      std::vector<ConvTJob> jobs;
+      long mx = 0;
+      for (size_t b = 0; b < A.blocks.size(); ++b) {
+        const Block& B = A.blocks[b];
+        jobs.push_back({A.d.p + B.off, smir.p + soff[b], ss, B.rows, B.cols, B.cols, pad8(B.rows), NSL, pad8(B.rows),
+                        1.0});
+        mx = std::max<long>(mx, (long)B.cols * pad8(B.rows));
+      }
+      DArr<ConvTJob> dj;
+      dj.upload(jobs, c.stream);
+      for (int o0 = 0; o0 < (int)jobs.size(); o0 += 65535) {
+        const int nj = std::min(65535, (int)jobs.size() - o0);
+        const long g = std::min<long>(std::max<long>(1, (mx + 255) / 256), 64);
+        convt_kernel<<<dim3((unsigned)g, nj), 256, 0, c.stream>>>(dj.p + o0);
+        count_launches(1);
+      }
+      cuda_check(cudaGetLastError(), "convt launch");
+      cuda_check(cudaStreamSynchronize(c.stream), "sync");
+    } else {
+      std::vector<ConvJob> jobs;
+      long mx = 0;
+      for (size_t b = 0; b < A.blocks.size(); ++b) {
+        const Block& B = A.blocks[b];
+        jobs.push_back({A.d.p + B.off, smir.p + soff[b], ss, B.rows, B.cols, B.cols, pad8(B.cols), NSL, 1.0,
+                        pad8(B.cols)});
+        mx = std::max<long>(mx, (long)B.rows * pad8(B.cols));
+      }
+      DArr<ConvJob> dj;
+      dj.upload(jobs, c.stream);
+      if (!jobs.empty()) launch_conv(dj, (int)jobs.size(), mx, c.stream);
+      cuda_check(cudaStreamSynchronize(c.stream), "sync");
+    }
+  }
+  // ---- W-contracted operator mirror: every distinct (operator, scale), all blocks,
+  // row-major with leading dimension pad8(cols)
+  std::vector<std::vector<long>> boff(env.cls.size());
+  std::vector<long> bsz(env.cls.size());
+  for (size_t i = 0; i < env.cls.size(); ++i) boff[i] = padded_offsets(env.cls[i], &bsz[i]);
+  struct KeyHash {
+    size_t operator()(const std::pair<const double*, double>& kk) const {
+      uint64_t b;
+      std::memcpy(&b, &kk.second, sizeof b);
+      return std::hash<uint64_t>()((uint64_t)(uintptr_t)kk.first * 0x9e3779b97f4a7c15ULL ^ b);
+    }
+  };
+  std::unordered_map<std::pair<const double*, double>, long, KeyHash> moff;
+  std::vector<std::array<long, 16>> mref(st.size());
+  std::vector<std::array<char, 16>> mneg(st.size());
+  long mtot = 0;
+  std::vector<std::pair<const TRef*, long>> created;
+  for (size_t beta = 0; beta < st.size(); ++beta)
+    for (int nn = 0; nn < 16; ++nn) {
+      mref[beta][nn] = -1;
+      mneg[beta][nn] = 0;
+      const TRef& r = t.ref[beta][nn];
+      if (!r.p) continue;
+      const double a = std::fabs(r.coef);
+      const double scale = a == 1.0 ? 1.0 : r.coef;
+      auto key = std::make_pair(r.p, scale);
+      auto it = moff.find(key);
+      if (it == moff.end()) {
+        it = moff.emplace(key, mtot).first;
+        created.push_back({&r, mtot});
+        mtot += bsz[r.cls];
+      }
+      mref[beta][nn] = it->second;
+      mneg[beta][nn] = (a == 1.0 && r.coef < 0) ? 1 : 0;
+    }
+  const long ms_ = std::max<long>(mtot, 8);
+  DArr<__nv_bfloat16> omir;
+  omir.alloc((size_t)ms_ * NSL, c.stream);
+  {
+    std::vector<ConvJob> jobs;
+    long mx = 0;
+    for (const auto& cr : created) {
+      const TRef& r = *cr.first;
+      const double a = std::fabs(r.coef);
+      const double scale = a == 1.0 ? 1.0 : r.coef;
+      const OpLayout& L = env.cls[r.cls];
+      for (size_t b = 0; b < L.blocks.size(); ++b) {
+        const Block& B = L.blocks[b];
+        jobs.push_back({r.p + B.off, omir.p + cr.second + boff[r.cls][b], ms_, B.rows, B.cols, B.cols, pad8(B.cols),
+                        NSL, scale, pad8(B.cols)});
+        mx = std::max<long>(mx, (long)B.rows * pad8(B.cols));
+      }
+    }
+    DArr<ConvJob> dj;
+    dj.upload(jobs, c.stream);
+    if (!jobs.empty()) launch_conv(dj, (int)jobs.size(), mx, c.stream);
+    cuda_check(cudaStreamSynchronize(c.stream), "sync");
+  }
+  // ---- FP32 staging of the new operators (same layout as their FP64 data)
+  std::vector<DArr<float>> f32(out.cls.size());
+  for (size_t ci = 0; ci < out.cls.size(); ++ci) {
+    f32[ci].alloc(std::max<size_t>(out.data[ci].n, 1), c.stream);
+    cuda_check(cudaMemsetAsync(f32[ci].p, 0, f32[ci].n * sizeof(float), c.stream), "memset");
+  }
+  auto f32_op = [&](int beta) {
+    return f32[out.st_cls[beta]].p + (size_t)out.st_slot[beta] * out.cls[out.st_cls[beta]].nnz;
+  };
+  // ---- the intermediate blocks per bond state: left (n1, j): d(j) x pad8(d(ql));
+  // right (n2, j): d(j) x pad8(d(qr))
+  const Bond& ib = left ? Lb : Rb;  // bond of the contracted index of stage 1
+  auto inner_of = [&](int beta, int n, int j) -> int {
+    // left: ql with ql + q(n1) + dQ_beta = qr_j; right: qr with qr = ql_j + dQ + q(n2)
+    if (left) return Lb.find(Rb.qa[j] + st[beta].dna - LQA[n], Rb.qb[j] + st[beta].dnb - LQB[n]);
+    return Rb.find(Lb.qa[j] + st[beta].dna + LQA[n], Lb.qb[j] + st[beta].dnb + LQB[n]);
+  };
+  std::vector<size_t> tsz(st.size(), 0);
+  for (size_t beta = 0; beta < st.size(); ++beta)
+    for (int n = 0; n < 4; ++n)
+      for (int j = 0; j < no; ++j) {
+        const int q = inner_of((int)beta, n, j);
+        if (q >= 0) tsz[beta] += (size_t)ob.dim[j] * pad8(ib.dim[q]);
+      }
+  const size_t budget = std::max<size_t>(1, (size_t)c.chunk_budget_mb * (1u << 20) / (2 * NSL));
+  for (size_t b0 = 0; b0 < st.size();) {
+    size_t b1 = b0, tot = 0;
+    while (b1 < st.size() && (b1 == b0 || tot + tsz[b1] <= budget)) tot += tsz[b1++];
+    const long ts = std::max<long>((long)tot, 8);
+    DArr<__nv_bfloat16> T;
+    T.alloc((size_t)ts * NSL, c.stream);
+    cuda_check(cudaMemsetAsync(T.p, 0, T.n * sizeof(__nv_bfloat16), c.stream), "memset");
+    TcBuilder g1, g2;
+    size_t toff = 0;
+    double fl = 0;
+    for (size_t beta = b0; beta < b1; ++beta) {
+      std::vector<long> tpos((size_t)4 * no, -1);
+      for (int n = 0; n < 4; ++n)
+        for (int j = 0; j < no; ++j) {
+          const int q = inner_of((int)beta, n, j);
+          if (q < 0) continue;
+          const int m = ob.dim[j], nn = ib.dim[q];
+          TcTask tk{};
+          tk.Cb = T.p + toff;
+          tk.slice_stride = ts;
+          tk.ldcb = pad8(nn);
+          tk.m = m;
+          tk.n = nn;
+          tk.nslices = NSL;
+          g1.begin(tk);
+          for (int np = 0; np < 4; ++np) {
+            const int slot = n * 4 + np;
+            const TRef& r = t.ref[beta][slot];
+            if (!r.p) continue;
+            const OpLayout& Lay = env.cls[r.cls];
+            int qp, bl, sb;
+            if (left) {
+              qp = Lb.find(Lb.qa[q] - Lay.da, Lb.qb[q] - Lay.db);  // ql'
+              if (qp < 0) continue;
+              bl = Lay.blk_of_col[qp];
+              if (bl < 0 || Lay.blocks[bl].rs != q) continue;
+              sb = A.blk(qp, np);
+              if (sb < 0 || A.blocks[sb].cs != j) continue;
+            } else {
+              qp = Rb.find(Lb.qa[j] + LQA[np], Lb.qb[j] + LQB[np]);  // qr'
+              if (qp < 0) continue;
+              bl = Lay.blk_of_col[qp];
+              if (bl < 0 || Lay.blocks[bl].rs != q) continue;
+              sb = A.blk(j, np);
+              if (sb < 0 || A.blocks[sb].cs != qp) continue;
+            }
+            const int kk = ib.dim[qp];
+            g1.term(smir.p + soff[sb], ss, pad8(kk), omir.p + mref[beta][slot] + boff[r.cls][bl], ms_, pad8(kk), kk,
+                    mneg[beta][slot] != 0, NSL);
+            fl += 2.0 * m * nn * kk;
+          }
+          if (g1.end()) {
+            tpos[(size_t)n * no + j] = (long)toff;
+            toff += (size_t)m * pad8(nn);
+          }
+        }
+      const OpLayout& Lo = out.lay((int)beta);
+      float* obase = f32_op((int)beta);
+      for (const Block& B : Lo.blocks) {
+        TcTask tk{};
+        tk.C = obase + B.off;
+        tk.ldc = B.cols;
+        tk.m = B.rows;
+        tk.n = B.cols;
+        g2.begin(tk);
+        for (int n = 0; n < 4; ++n) {
+          int q, sb;
+          if (left) {
+            q = Lb.find(Rb.qa[B.rs] - LQA[n], Rb.qb[B.rs] - LQB[n]);  // ql of A^{n}[ql, qa]
+            if (q < 0) continue;
+            sb = A.blk(q, n);
+            if (sb < 0 || A.blocks[sb].cs != B.rs) continue;
+          } else {
+            q = Rb.find(Lb.qa[B.rs] + LQA[n], Lb.qb[B.rs] + LQB[n]);  // qr of B^{n}[qb, qr]
+            if (q < 0) continue;
+            sb = A.blk(B.rs, n);
+            if (sb < 0 || A.blocks[sb].cs != q) continue;
+          }
+          const long tp = tpos[(size_t)n * no + B.cs];
+          if (tp < 0) continue;
+          const int kk = ib.dim[q];
+          g2.term(smir.p + soff[sb], ss, pad8(kk), T.p + tp, ts, pad8(kk), kk, false, NSL);
+          fl += 2.0 * B.rows * B.cols * kk;
+        }
+        g2.end();
+      }
+    }
+    c.other_flops_total += fl;
+    DArr<int> err;
+    err.alloc(1, c.stream);
+    cuda_check(cudaMemsetAsync(err.p, 0, sizeof(int), c.stream), "memset");
+    DArr<TcTile> t1, t2;
+    DArr<TcTask> k1, k2;
+    DArr<TcTerm> m1, m2;
+    t1.upload(g1.tiles, c.stream);
+    k1.upload(g1.tasks, c.stream);
+    m1.upload(g1.terms, c.stream);
+    t2.upload(g2.tiles, c.stream);
+    k2.upload(g2.tasks, c.stream);
+    m2.upload(g2.terms, c.stream);
+    cuda_check(launch_gemm_bf16_tc(t1.p, (int)g1.tiles.size(), k1.p, m1.p, err.p, c.stream, NSL), "tc env stage 1");
+    cuda_check(launch_gemm_bf16_tc(t2.p, (int)g2.tiles.size(), k2.p, m2.p, err.p, c.stream, NSL), "tc env stage 2");
+    int h = 0;
+    cuda_check(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h");
+    cuda_check(cudaStreamSynchronize(c.stream), "sync");
+    if (h) throw Error(ST_ETIMEOUT, "tensor-core GEMM: a bounded wait ran out");
+    b0 = b1;
+  }
+  for (size_t ci = 0; ci < out.cls.size(); ++ci) {
+    const long n = (long)out.data[ci].n;
+    if (n <= 0) continue;
+    f32_to_f64_kernel<<<(unsigned)std::min<long>((n + 255) / 256, 152 * 16), 256, 0, c.stream>>>(f32[ci].p,
+                                                                                                  out.data[ci].p, n);
+    count_launches(1);
+  }
+  cuda_check(cudaGetLastError(), "f32 to f64");
+  cuda_check(cudaStreamSynchronize(c.stream), "sync");
 }
 
 // ---------------------------------------------------------------- batched sigma

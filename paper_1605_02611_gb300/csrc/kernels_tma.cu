@@ -47,12 +47,17 @@ constexpr long TM_WAIT_LIMIT = 1L << 24;
 
 template <int MODE>
 struct TmCfg {
-  static constexpr int NMAX = MODE == TM_MODE_STORE_BF16 ? 256 : 128;
+  static constexpr bool STORE = MODE == TM_MODE_STORE_BF16;
+  static constexpr int NMAX = STORE ? 256 : 128;
   static constexpr int NACC = 512 / NMAX;
   static constexpr int B_BYTES = NMAX * TM_BOX_K * 2;
   static constexpr int STAGE_BYTES = TM_A_BYTES + B_BYTES;
-  static constexpr int STAGES = (192 * 1024) / STAGE_BYTES;  // 4 (store) or 6 (reduce)
-  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+  // store mode: the output tile is staged in shared memory (rows padded by 16 bytes
+  // against bank conflicts) and written by bulk copies, one per row
+  static constexpr int STAGE_LD = NMAX + 8;  // elements per staged row
+  static constexpr int STAGING = STORE ? 128 * STAGE_LD * 2 : 0;
+  static constexpr int STAGES = STORE ? 3 : 6;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + STAGING + 1024;
 };
 constexpr int TM_MAX_STAGES = 6, TM_MAX_ACC = 4;
 
@@ -123,6 +128,19 @@ __device__ __forceinline__ void red_add_v4(float* p, uint32_t a, uint32_t b, uin
                : "memory");
 }
 
+// 32 consecutive FP32 columns of this warp's 32 tensor-memory lanes
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
 __device__ __forceinline__ uint32_t pack_bf16x2(uint32_t lo, uint32_t hi) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(__uint_as_float(lo), __uint_as_float(hi));
   return *reinterpret_cast<const uint32_t*>(&h);
@@ -133,19 +151,29 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
     gemm_tma_kernel(const TmTile* __restrict__ tiles, int ntiles, const TmTerm* __restrict__ terms,
                     const CUtensorMap* __restrict__ maps, const long* __restrict__ rowmap, void* __restrict__ out,
                     int out_slices, long slice_stride, int* __restrict__ err) {
-  constexpr int S = TmCfg<MODE>::STAGES;
-  constexpr int STAGE_BYTES = TmCfg<MODE>::STAGE_BYTES;
-  constexpr int NACC = TmCfg<MODE>::NACC;
-  constexpr int NMAX = TmCfg<MODE>::NMAX;
+  using Cfg = TmCfg<MODE>;
+  constexpr int S = Cfg::STAGES;
+  constexpr int STAGE_BYTES = Cfg::STAGE_BYTES;
+  constexpr int NACC = Cfg::NACC;
+  constexpr int NMAX = Cfg::NMAX;
+  constexpr bool STORE = Cfg::STORE;
+  // reduce mode: a tile's products accumulate in tensor memory for at most
+  // TM_SEG_KSTEPS K steps (a segment); the epilogue adds the segments in FP32
+  // registers with round-to-nearest, so the rounding toward zero of the tensor-core
+  // accumulation acts on short sums only
+  constexpr long SEG = STORE ? (1L << 40) : TM_SEG_KSTEPS;
   extern __shared__ uint8_t dsm[];
   __shared__ __align__(8) uint64_t full_b[TM_MAX_STAGES], empty_b[TM_MAX_STAGES], tfull_b[TM_MAX_ACC],
       tempty_b[TM_MAX_ACC];
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
-  // per stage: instruction descriptor, K=16 steps, first/last K step of the tile
+  // per stage: instruction descriptor, K=16 steps, first K step of a segment, last K
+  // step of a segment, last K step of the tile
   __shared__ uint32_t meta_id[TM_MAX_STAGES];
-  __shared__ int meta_nk[TM_MAX_STAGES], meta_first[TM_MAX_STAGES], meta_last[TM_MAX_STAGES];
+  __shared__ int meta_nk[TM_MAX_STAGES], meta_first[TM_MAX_STAGES], meta_seg_end[TM_MAX_STAGES],
+      meta_last[TM_MAX_STAGES];
   const uint32_t base = (smem_u32(dsm) + 1023u) & ~1023u;
+  uint8_t* const base_ptr = dsm + (base - smem_u32(dsm));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 2) {  // an epilogue warp (all lanes take the same path) owns the tensor memory
@@ -179,21 +207,24 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
       for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
         const TmTile tl = tiles[ti];
         const uint32_t bbytes = (uint32_t)tl.n * TM_BOX_K * 2;
+        long ks = 0;  // K steps of this tile so far
         for (int t = tl.t0; t < tl.t1 && ok; ++t) {
           const TmTerm tm = terms[t];
           const uint32_t id = idesc_bf16(tl.n, tm.neg != 0);
           const CUtensorMap* ma = maps + tm.amap;
           const CUtensorMap* mb = maps + tm.bmap;
-          for (int k0 = 0; k0 < tm.k; k0 += TM_BOX_K) {
+          for (int k0 = 0; k0 < tm.k; k0 += TM_BOX_K, ++ks) {
             const int s = (int)(j % S);
             if (j >= S && !mbar_wait(&empty_b[s], (uint32_t)(((j / S) - 1) & 1), abort_flag)) {
               ok = false;
               break;
             }
+            const bool last = t + 1 == tl.t1 && k0 + TM_BOX_K >= tm.k;
             meta_id[s] = id;
             meta_nk[s] = min(TM_BOX_K / 16, (tm.k - k0) / 16);
-            meta_first[s] = (t == tl.t0 && k0 == 0) ? 1 : 0;
-            meta_last[s] = (t + 1 == tl.t1 && k0 + TM_BOX_K >= tm.k) ? 1 : 0;
+            meta_first[s] = (ks % SEG == 0) ? 1 : 0;
+            meta_seg_end[s] = (last || ks % SEG == SEG - 1) ? 1 : 0;
+            meta_last[s] = last ? 1 : 0;
             const uint32_t sa = base + s * STAGE_BYTES;
             mbar_arrive_expect_tx(&full_b[s], TM_A_BYTES + bbytes);
             tma_load_2d(sa, ma, tm.ax + k0, tm.ay, &full_b[s]);
@@ -211,114 +242,153 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
       }
     }
   } else if (warp == 1) {
-    // ---------------- MMA issuer (one thread)
+    // ---------------- MMA issuer (one thread): one accumulator per segment
     if (lane == 0) {
       long j = 0;
-      int it = 0;
+      int sg = 0;  // segments issued
       bool ok = true;
-      for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x, ++it) {
-        const int acc = it % NACC;
-        if (it >= NACC && !mbar_wait(&tempty_b[acc], (uint32_t)(((it / NACC) - 1) & 1), abort_flag)) {
-          ok = false;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-        const uint32_t dacc = tmem + (uint32_t)(acc * NMAX);
-        for (;;) {
-          const int s = (int)(j % S);
-          if (!mbar_wait(&full_b[s], (uint32_t)((j / S) & 1), abort_flag)) {
+      for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
+        bool tile_done = false;
+        while (!tile_done && ok) {
+          const int acc = sg % NACC;
+          if (sg >= NACC && !mbar_wait(&tempty_b[acc], (uint32_t)(((sg / NACC) - 1) & 1), abort_flag)) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-          const uint32_t id = meta_id[s];
-          const int nk = meta_nk[s], first = meta_first[s], last = meta_last[s];
-          const uint32_t sa = base + s * STAGE_BYTES;
-          for (int kk = 0; kk < nk; ++kk) {
-            const uint64_t ad = sdesc(sa + kk * 32), bd = sdesc(sa + TM_A_BYTES + kk * 32);
-            const uint32_t accum = (first && kk == 0) ? 0u : 1u;
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dacc),
-                "l"(ad), "l"(bd), "r"(id), "r"(accum));
+          const uint32_t dacc = tmem + (uint32_t)(acc * NMAX);
+          for (;;) {
+            const int s = (int)(j % S);
+            if (!mbar_wait(&full_b[s], (uint32_t)((j / S) & 1), abort_flag)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+            const uint32_t id = meta_id[s];
+            const int nk = meta_nk[s], first = meta_first[s], seg_end = meta_seg_end[s], last = meta_last[s];
+            const uint32_t sa = base + s * STAGE_BYTES;
+            for (int kk = 0; kk < nk; ++kk) {
+              const uint64_t ad = sdesc(sa + kk * 32), bd = sdesc(sa + TM_A_BYTES + kk * 32);
+              const uint32_t accum = (first && kk == 0) ? 0u : 1u;
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dacc),
+                  "l"(ad), "l"(bd), "r"(id), "r"(accum));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                smem_u32(&empty_b[s])));
+            ++j;
+            if (seg_end) {
+              tile_done = last != 0;
+              break;
+            }
           }
+          if (!ok) break;
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-              smem_u32(&empty_b[s])));
-          ++j;
-          if (last) break;
+              smem_u32(&tfull_b[acc])));
+          ++sg;
         }
-        if (!ok) break;
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-            smem_u32(&tfull_b[acc])));
       }
     }
   } else {
     // ---------------- epilogue (warps 2-5: tensor-memory lanes 32 * (warp % 4) ...)
     const int sub = warp & 3;
     const int r = sub * 32 + lane;  // row of the tile
-    int it = 0;
-    for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x, ++it) {
+    __nv_bfloat16* const srow =
+        reinterpret_cast<__nv_bfloat16*>(base_ptr + S * STAGE_BYTES) + (STORE ? r * Cfg::STAGE_LD : 0);
+    int sg = 0;
+    bool ok = true;
+    for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
       const TmTile tl = tiles[ti];
-      const int acc = it % NACC;
-      bool ok = mbar_wait(&tfull_b[acc], (uint32_t)((it / NACC) & 1), abort_flag);
-      ok = __all_sync(0xffffffffu, ok);
-      if (!ok) break;
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-      long dst = -1;
-      if (MODE == TM_MODE_STORE_BF16) {
-        dst = rowmap[tl.rowmap_off + r];
-      } else if (r < tl.m_valid) {
-        dst = tl.out_off + (long)r * tl.ldo;
-      }
-      for (int c0 = 0; c0 < tl.n; c0 += 32) {
-        uint32_t v[32];
-        const uint32_t taddr = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(acc * NMAX + c0);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-              "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-              "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-              "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-        if (dst < 0) continue;
-        const int nv = min(32, tl.n - c0);  // a multiple of 16
-        if (MODE == TM_MODE_STORE_BF16) {
-          // BF16 slices x = s0 + s1 + ... of the FP32 values, slice_stride elements apart
-          __nv_bfloat16* p = reinterpret_cast<__nv_bfloat16*>(out) + dst + tl.out_off + c0;
-          for (int sl = 0; sl < out_slices; ++sl) {
+      if constexpr (STORE) {
+        const int acc = sg % NACC;
+        ok = mbar_wait(&tfull_b[acc], (uint32_t)((sg / NACC) & 1), abort_flag);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+        const long dst = rowmap[tl.rowmap_off + r];
+        __nv_bfloat16* g = reinterpret_cast<__nv_bfloat16*>(out) + (dst >= 0 ? dst : 0) + tl.out_off;
+        for (int sl = 0; sl < out_slices; ++sl) {
+          // the staging row must no longer be read by an earlier bulk copy
+          asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
 #pragma unroll
-            for (int q = 0; q < 32; q += 8) {
-              if (q >= nv) break;
-              uint4 w;
-              w.x = pack_bf16x2(v[q], v[q + 1]);
-              w.y = pack_bf16x2(v[q + 2], v[q + 3]);
-              w.z = pack_bf16x2(v[q + 4], v[q + 5]);
-              w.w = pack_bf16x2(v[q + 6], v[q + 7]);
-              *reinterpret_cast<uint4*>(p + q) = w;
-            }
-            if (sl + 1 < out_slices) {
-              // remainders for the next slice
+          for (int cc = 0; cc < NMAX / 32; ++cc) {
+            const int c0 = cc * 32;
+            if (c0 < tl.n) {
+              uint32_t v[32];
+              const uint32_t taddr = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(acc * NMAX + c0);
+              tmem_ld32(taddr, v);
+              // slice sl of x = s0 + s1 + s2: BF16 of the remainder after the earlier slices
 #pragma unroll
-              for (int q = 0; q < 32; ++q)
-                v[q] = __float_as_uint(__uint_as_float(v[q]) - __bfloat162float(__float2bfloat16_rn(__uint_as_float(v[q]))));
-              p += slice_stride;
+              for (int u = 0; u < 32; ++u) {
+                float x = __uint_as_float(v[u]);
+                for (int q = 0; q < sl; ++q) x -= __bfloat162float(__float2bfloat16_rn(x));
+                v[u] = __float_as_uint(x);
+              }
+#pragma unroll
+              for (int u = 0; u < 32; u += 8) {
+                uint4 w;
+                w.x = pack_bf16x2(v[u], v[u + 1]);
+                w.y = pack_bf16x2(v[u + 2], v[u + 3]);
+                w.z = pack_bf16x2(v[u + 4], v[u + 5]);
+                w.w = pack_bf16x2(v[u + 6], v[u + 7]);
+                if (c0 + u < tl.n) *reinterpret_cast<uint4*>(srow + c0 + u) = w;
+              }
             }
           }
-        } else {
-          float* p = reinterpret_cast<float*>(out) + dst + c0;
-#pragma unroll
-          for (int q = 0; q < 32; q += 4) {
-            if (q >= nv) break;
-            red_add_v4(p + q, v[q], v[q + 1], v[q + 2], v[q + 3]);
+          if (dst >= 0) {
+            // the staging row (written through the generic proxy) is read by the bulk copy
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(g + sl * slice_stride),
+                         "r"(smem_u32(srow)), "r"((uint32_t)tl.n * 2)
+                         : "memory");
+            asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
           }
         }
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+        mbar_arrive(&tempty_b[acc]);
+        ++sg;
+      } else {
+        float run[NMAX / 32][32];  // the tile's running FP32 sum (row r)
+        for (int q = 0; q < tl.nseg; ++q, ++sg) {
+          const int acc = sg % NACC;
+          ok = mbar_wait(&tfull_b[acc], (uint32_t)((sg / NACC) & 1), abort_flag);
+          ok = __all_sync(0xffffffffu, ok);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+#pragma unroll
+          for (int cc = 0; cc < NMAX / 32; ++cc) {
+            const int c0 = cc * 32;
+            if (c0 < tl.n) {
+              uint32_t v[32];
+              tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(acc * NMAX + c0), v);
+              if (q == 0) {
+#pragma unroll
+                for (int u = 0; u < 32; ++u) run[cc][u] = __uint_as_float(v[u]);
+              } else {
+#pragma unroll
+                for (int u = 0; u < 32; ++u) run[cc][u] += __uint_as_float(v[u]);
+              }
+            }
+          }
+          asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+          mbar_arrive(&tempty_b[acc]);
+        }
+        if (!ok) break;
+        if (r < tl.m_valid) {
+          float* p = reinterpret_cast<float*>(out) + tl.out_off + (long)r * tl.ldo;
+#pragma unroll
+          for (int cc = 0; cc < NMAX / 32; ++cc)
+#pragma unroll
+            for (int u = 0; u < 32; u += 4) {
+              if (cc * 32 + u >= tl.n) break;
+              red_add_v4(p + cc * 32 + u, __float_as_uint(run[cc][u]), __float_as_uint(run[cc][u + 1]),
+                         __float_as_uint(run[cc][u + 2]), __float_as_uint(run[cc][u + 3]));
+            }
+        }
       }
-      asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
-      mbar_arrive(&tempty_b[acc]);
     }
+    if (STORE) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
   __syncthreads();

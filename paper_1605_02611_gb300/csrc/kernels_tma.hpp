@@ -27,15 +27,21 @@ struct TmTerm {
 //     + col0, columns [0, n); rowmap entries < 0 are skipped;
 //   reduce mode (sigma^T, FP32): rows r < m_valid are added (vector reductions) to
 //     out + out_off + r * ldo, columns [0, n).
+//   nseg (reduce mode): segments of the tile, ceil(K steps / TM_SEG_KSTEPS) with one K
+//     step per 64 columns of every term; each segment accumulates in tensor memory
+//     on its own and the epilogue adds the segments in FP32.
 struct TmTile {
   int t0, t1;
   int n, m_valid;
-  int ldo, pad;
+  int ldo, nseg;
   long out_off;
   long rowmap_off;
 };
 
 constexpr int TM_MODE_STORE_BF16 = 1, TM_MODE_REDUCE_F32 = 2;
+// K steps (64 columns each) accumulated in tensor memory before the reduce-mode
+// epilogue takes the partial sum over
+constexpr int TM_SEG_KSTEPS = 16;
 
 // maps: device array of encoded tensor maps (64-byte aligned).  Store mode:
 // out_slices (1-3) BF16 slices x = s0 + s1 + ... of every FP32 result, written
