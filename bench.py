@@ -241,6 +241,10 @@ def run_ours(args, rank, world, local_rank):
         ctx.set_stage1_stacked(True)
     if args.fp64_w_sums:
         ctx.set_tc_combos(False)
+    if args.env_precision:
+        ctx.set_env_precision(args.env_precision)
+    if args.refine >= 0:
+        ctx.set_refinement(args.refine, args.refine_iters)
     ctx.set_mps(T, [b.labels() for b in bonds])
     del T
     # should the tensor-core W-contracted sums report an error (here or in the first
@@ -573,6 +577,12 @@ def main():
     ap.add_argument("--fp64-w-sums", action="store_true",
                     help="form every W-contracted sum on the FP64 units (default: large sums that feed only "
                          "the tensor-core sigma run on the tensor cores)")
+    ap.add_argument("--env-precision", type=int, default=0, choices=[0, 2],
+                    help="environment updates: 0 FP64 units, 2 tensor cores with three BF16 slices")
+    ap.add_argument("--refine", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4, 5, 6],
+                    help="precision of the Davidson refinement phase of each step (-1: none)")
+    ap.add_argument("--refine-iters", type=int, default=4,
+                    help="Davidson iterations of the step budget given to the refinement phase")
     ap.add_argument("--autotune", action="store_true",
                     help="with --batched: choose the split-K granularity of the fused work lists by timing")
     ap.add_argument("--profile-sigma", type=int, default=0,

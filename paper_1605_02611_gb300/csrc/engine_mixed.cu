@@ -731,6 +731,7 @@ struct TmaPlan {
   long sig_maxel = 0;
   DArr<CUtensorMap> maps;
   DArr<long> rowmap;
+  DArr<int2> cbtab;  // (first column, width) of the column blocks of every input group
   struct Chunk {
     DArr<TmTile> t1, t2;
     DArr<TmTerm> m1, m2;
@@ -804,10 +805,12 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
     }
   }
   const int ng = (int)gq.size();
-  std::vector<std::array<int, 2>> rpos((size_t)nL * 4, {-1, 0}), cpos((size_t)nR * 4, {-1, 0});
+  // (group, offset, index of the block in its group) of every row block (ql, n1) and
+  // column block (n2, qr)
+  std::vector<std::array<int, 3>> rpos((size_t)nL * 4, {-1, 0, -1}), cpos((size_t)nR * 4, {-1, 0, -1});
   for (int g = 0; g < ng; ++g) {
-    for (auto& r : grow[g]) rpos[r[0] * 4 + r[1]] = {g, r[2]};
-    for (auto& cc : gcol[g]) cpos[cc[1] * 4 + cc[0]] = {g, cc[2]};
+    for (size_t i = 0; i < grow[g].size(); ++i) rpos[grow[g][i][0] * 4 + grow[g][i][1]] = {g, grow[g][i][2], (int)i};
+    for (size_t i = 0; i < gcol[g].size(); ++i) cpos[gcol[g][i][1] * 4 + gcol[g][i][0]] = {g, gcol[g][i][2], (int)i};
   }
   auto group_of = [&](int a, int b) {
     auto it = gidx.find({a, b});
@@ -956,7 +959,9 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
     long r0, r1;
   };
   std::vector<std::vector<Run>> runs(ng);
-  std::vector<std::vector<long>> rowdst(ng);  // per A1 row: element offset of its X^T row
+  // per A1 row: its row in the X^T region of its chunk (columns: blocks of g', each its
+  // own submatrix of the region)
+  std::vector<std::vector<long>> rowdst(ng);
   std::vector<ConvJob> aconv;
   for (int gp = 0; gp < ng; ++gp) {
     long row = 0;
@@ -966,16 +971,17 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
       if (runs[gp].empty() || runs[gp].back().chunk != ci || runs[gp].back().mask != x.mask)
         runs[gp].push_back({ci, x.mask, row, row});
       runs[gp].back().r1 = row + x.rows;
-      const long xbase =
-          xreg[ci][gp] + (xrow[(size_t)x.beta * ng + gp] + (long)cpos[x.qr * 4 + x.n2][1]) * (long)gR[gp];
-      for (int i = 0; i < x.rows; ++i) rowdst[gp][(size_t)(row + i)] = xbase + (long)i * gR[gp];
+      const long xr0 = xrow[(size_t)x.beta * ng + gp] + (long)cpos[x.qr * 4 + x.n2][1];
+      for (int i = 0; i < x.rows; ++i) rowdst[gp][(size_t)(row + i)] = xr0 + i;
       for (int n2p = 0; n2p < 4; ++n2p) {
         if (!((x.mask >> n2p) & 1)) continue;
         const TRef& r = rt.ref[x.beta][x.n2 * 4 + n2p];
         const Block& B = Renv.cls[r.cls].blocks[x.bl[n2p]];
+        // the K block (n2', qr') of g': submatrix of a1rows x pad16(d(qr')) at column offset coff
         const int coff = cpos[B.cs * 4 + n2p][1];
-        aconv.push_back({r.p + B.off, tp->a1.p + a1off[gp] + row * gC[gp] + coff, a1s, B.rows, B.cols, B.cols, gC[gp],
-                         nsl, r.coef, pad16(B.cols)});
+        const int w = pad16(B.cols);
+        aconv.push_back({r.p + B.off, tp->a1.p + a1off[gp] + a1rows[gp] * coff + row * w, a1s, B.rows, B.cols, B.cols,
+                         w, nsl, r.coef, w});
         tp->a1_maxel = std::max<long>(tp->a1_maxel, (long)B.rows * pad16(B.cols));
       }
       row += x.rows;
@@ -985,10 +991,18 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
   tp->a1_jobs.upload(aconv, c.stream);
   tp->n_a1_jobs = (int)aconv.size();
   // ---- left mirror: every distinct (operator, scale) referenced by Lt, all its blocks,
-  // each padded to 16 rows and columns, in one matrix of WL columns
-  int WL = 16;
+  // each padded to 16 rows and columns; blocks of one padded width w share one matrix of
+  // w columns (a box past the width then reads zeros without touching memory)
+  std::map<int, int> wcls;  // padded width -> class
+  std::vector<int> wcls_w;
   for (const OpLayout& L : Lenv.cls)
-    for (const Block& B : L.blocks) WL = std::max(WL, pad16(B.cols));
+    for (const Block& B : L.blocks)
+      if (!wcls.count(pad16(B.cols))) {
+        wcls[pad16(B.cols)] = (int)wcls_w.size();
+        wcls_w.push_back(pad16(B.cols));
+      }
+  const int nwc = (int)wcls_w.size();
+  std::vector<long> lrows_c(nwc, 0);
   struct MirKeyHash {
     size_t operator()(const std::pair<const double*, double>& kk) const {
       uint64_t b;
@@ -996,56 +1010,60 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
       return std::hash<uint64_t>()((uint64_t)(uintptr_t)kk.first * 0x9e3779b97f4a7c15ULL ^ b);
     }
   };
-  std::unordered_map<std::pair<const double*, double>, long, MirKeyHash> lm_row;
-  std::vector<std::vector<long>> lblk_row(Lenv.cls.size());
-  std::vector<long> lop_rows(Lenv.cls.size(), 0);
-  for (size_t ci = 0; ci < Lenv.cls.size(); ++ci) {
-    long r = 0;
-    for (const Block& B : Lenv.cls[ci].blocks) {
-      lblk_row[ci].push_back(r);
-      r += pad16(B.rows);
-    }
-    lop_rows[ci] = r;
-  }
-  long lrows = 0;
-  std::vector<ConvJob> lconv;
-  std::vector<std::array<long, 16>> lrow0((size_t)nmid);
+  std::unordered_map<std::pair<const double*, double>, int, MirKeyHash> lm_id;
+  std::vector<std::vector<long>> mblk_row;  // per mirror, per block: row in its width class
+  struct PendL {  // one block of a new mirror: source, width class, row in the class, shape
+    const double* src;
+    int cls;
+    long crow;
+    int rows, cols;
+    double scale;
+  };
+  std::vector<PendL> lpend;
+  std::vector<std::array<int, 16>> lmid((size_t)nmid);
   std::vector<std::array<char, 16>> lneg((size_t)nmid);
   for (int beta = 0; beta < nmid; ++beta)
     for (int nn = 0; nn < 16; ++nn) {
-      lrow0[beta][nn] = -1;
+      lmid[beta][nn] = -1;
       lneg[beta][nn] = 0;
       const TRef& r = lt.ref[beta][nn];
       if (!r.p) continue;
       const double a = std::fabs(r.coef);
       const double scale = a == 1.0 ? 1.0 : r.coef;
       auto key = std::make_pair(r.p, scale);
-      auto it = lm_row.find(key);
-      long row0;
-      if (it == lm_row.end()) {
-        row0 = lrows;
-        lm_row.emplace(key, row0);
+      auto it = lm_id.find(key);
+      if (it == lm_id.end()) {
+        const int id = (int)mblk_row.size();
+        it = lm_id.emplace(key, id).first;
         const OpLayout& L = Lenv.cls[r.cls];
+        mblk_row.emplace_back(L.blocks.size());
         for (size_t b = 0; b < L.blocks.size(); ++b) {
           const Block& B = L.blocks[b];
-          // dst holds the row until the buffer exists
-          lconv.push_back({r.p + B.off, (__nv_bfloat16*)(intptr_t)(row0 + lblk_row[r.cls][b]), 0, B.rows, B.cols,
-                           B.cols, WL, nsl, scale, pad16(B.cols)});
-          tp->l_maxel = std::max<long>(tp->l_maxel, (long)B.rows * pad16(B.cols));
+          const int wc = wcls[pad16(B.cols)];
+          mblk_row[id][b] = lrows_c[wc];
+          lpend.push_back({r.p + B.off, wc, lrows_c[wc], B.rows, B.cols, scale});
+          lrows_c[wc] += pad16(B.rows);
         }
-        lrows += lop_rows[r.cls];
-      } else {
-        row0 = it->second;
       }
-      lrow0[beta][nn] = row0;
+      lmid[beta][nn] = it->second;
       lneg[beta][nn] = (a == 1.0 && r.coef < 0) ? 1 : 0;
     }
-  const long ls = std::max<long>(lrows * WL, 8);
+  std::vector<long> lbase(nwc, 0);
+  long ltot = 0;
+  for (int wc = 0; wc < nwc; ++wc) {
+    lbase[wc] = ltot;
+    ltot += lrows_c[wc] * wcls_w[wc];
+  }
+  const long ls = std::max<long>(ltot, 8);
   tp->lmir.alloc(ls * nsl, c.stream);
   cuda_check(cudaMemsetAsync(tp->lmir.p, 0, tp->lmir.n * sizeof(__nv_bfloat16), c.stream), "memset");
-  for (ConvJob& j : lconv) {
-    j.dst = tp->lmir.p + (intptr_t)j.dst * WL;
-    j.slice_stride = ls;
+  std::vector<ConvJob> lconv;
+  lconv.reserve(lpend.size());
+  for (const PendL& pl : lpend) {
+    const int w = wcls_w[pl.cls];
+    lconv.push_back({pl.src, tp->lmir.p + lbase[pl.cls] + pl.crow * w, ls, pl.rows, pl.cols, pl.cols, w, nsl, pl.scale,
+                     w});
+    tp->l_maxel = std::max<long>(tp->l_maxel, (long)pl.rows * w);
   }
   check_conv_jobs(lconv, tp->lmir);
   tp->l_jobs.upload(lconv, c.stream);
@@ -1078,7 +1096,8 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
   };
   const int n1max = tma_max_n(TM_MODE_STORE_BF16), n2max = tma_max_n(TM_MODE_REDUCE_F32);
   std::vector<std::vector<std::array<int, 3>>> nt1(ng);  // per g': (row0, width, Psi map) of the stage-1 N tiles
-  std::vector<int> a1map(ng, -1);
+  // A1 of g': one map per K block (column block of g', a1rows x its padded width)
+  std::vector<std::vector<int>> a1map(ng);
   for (int gp = 0; gp < ng; ++gp) {
     if (a1rows[gp] == 0) continue;
     const int parts = (gR[gp] + n1max - 1) / n1max;
@@ -1088,16 +1107,36 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
       nt1[gp].push_back({r0, w, add_map(tp->psi_b, goff[gp], std::max<long>(ptot, 8), gR[gp], gC[gp], gC[gp], w)});
       r0 += w;
     }
-    a1map[gp] = add_map(tp->a1, a1off[gp], a1s, a1rows[gp], gC[gp], gC[gp], 128);
+    for (const auto& cc : gcol[gp]) {
+      const int w = pad16(Rb.dim[cc[1]]);
+      a1map[gp].push_back(add_map(tp->a1, a1off[gp] + a1rows[gp] * cc[2], a1s, a1rows[gp], w, w, 128));
+    }
   }
-  std::vector<std::vector<int>> xtmap(nch, std::vector<int>(ng, -1));
+  // X^T region of (chunk, g'): one submatrix (and map) per column block (ql', n1') of g',
+  // xrows x its padded width; the table cbtab lists (first column, width) per g'
+  std::vector<std::vector<std::vector<int>>> xtmap(nch, std::vector<std::vector<int>>(ng));
+  std::vector<int2> cbtab;
+  std::vector<int> cbt0(ng), cbt1(ng);
+  for (int gp = 0; gp < ng; ++gp) {
+    cbt0[gp] = (int)cbtab.size();
+    for (const auto& rr : grow[gp]) cbtab.push_back(make_int2(rr[2], pad16(Lb.dim[rr[0]])));
+    cbt1[gp] = (int)cbtab.size();
+  }
   for (int ci = 0; ci < nch; ++ci)
     for (int gp = 0; gp < ng; ++gp)
       if (xregrows[ci][gp] > 0)
-        xtmap[ci][gp] = add_map(tp->xt, xreg[ci][gp], tp->x_stride, xregrows[ci][gp], gR[gp], gR[gp], 128);
-  std::vector<int> lmap(n2max / 16 + 1, -1);
-  if (lrows > 0)
-    for (int h = 16; h <= n2max; h += 16) lmap[h / 16] = add_map(tp->lmir, 0, ls, lrows, WL, WL, h);
+        for (const auto& rr : grow[gp]) {
+          const int w = pad16(Lb.dim[rr[0]]);
+          xtmap[ci][gp].push_back(add_map(tp->xt, xreg[ci][gp] + xregrows[ci][gp] * rr[2], tp->x_stride,
+                                          xregrows[ci][gp], w, w, 128));
+        }
+  // left mirror: per width class one map per box height
+  std::vector<std::vector<int>> lmap(nwc, std::vector<int>(n2max / 16 + 1, -1));
+  for (int wc = 0; wc < nwc; ++wc)
+    if (lrows_c[wc] > 0)
+      for (int h = 16; h <= n2max; h += 16)
+        lmap[wc][h / 16] = add_map(tp->lmir, lbase[wc], ls, lrows_c[wc], wcls_w[wc], wcls_w[wc], h);
+  tp->cbtab.upload(cbtab, c.stream);
   tp->maps.alloc(std::max<size_t>(maps.size(), 1), c.stream);
   if (!maps.empty())
     cuda_check(cudaMemcpyAsync(tp->maps.p, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
@@ -1129,14 +1168,19 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
               // the K block of n2': the column block (n2', qr') of g'
               const int qrp = Rb.find(gq[gp].first + LQA[n2p], gq[gp].second + LQB[n2p]);
               const int coff = cpos[qrp * 4 + n2p][1];
+              const int cbi = cpos[qrp * 4 + n2p][2];
               const int kk = pad16(Rb.dim[qrp]);
               for (int pr = 0; pr < npair; ++pr)
-                m1.push_back({a1map[gp] + PI[pr], nt[2] + PJ[pr], coff, (int)r0, coff, nt[0], kk, 0});
+                m1.push_back({a1map[gp][cbi] + PI[pr], nt[2] + PJ[pr], 0, (int)r0, coff, nt[0], kk, 0});
               ksum += kk * npair;
               st1_steps += (kk + 63) / 64 * npair;
             }
             tl.t1 = (int)m1.size();
             tl.nseg = 1;
+            tl.xbase = xreg[ci][gp];
+            tl.xrows = xregrows[ci][gp];
+            tl.cb0 = cbt0[gp];
+            tl.cb1 = cbt1[gp];
             tl.n = nt[1];
             tl.m_valid = 128;
             tl.ldo = gR[gp];
@@ -1159,8 +1203,12 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
           const int g = gout[(size_t)beta * ng + gp];
           for (const auto& cb : gcol[g]) {
             if (written.count(((long)beta * 4 + cb[0]) * nR + cb[1])) continue;
-            const long e0 = xreg[ci][gp] + (xrow[(size_t)beta * ng + gp] + cb[2]) * (long)gR[gp];
-            zj.push_back({tp->xt.p + e0, (long)pad16(Rb.dim[cb[1]]) * gR[gp], tp->x_stride, nsl});
+            const long r0 = xrow[(size_t)beta * ng + gp] + cb[2];
+            for (const auto& rr : grow[gp]) {
+              const int w = pad16(Lb.dim[rr[0]]);
+              const long e0 = xreg[ci][gp] + xregrows[ci][gp] * rr[2] + r0 * w;
+              zj.push_back({tp->xt.p + e0, (long)pad16(Rb.dim[cb[1]]) * w, tp->x_stride, nsl});
+            }
           }
         }
       }
@@ -1194,9 +1242,10 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
               if (bl < 0 || Lay.blocks[bl].rs != ql) continue;
               const auto rpp = rpos[qlp * 4 + n1p];
               if (rpp[0] != gp) continue;
-              base.push_back({xtmap[ci][gp], lmap[nw / 16], rpp[1], (int)xrow[(size_t)beta * ng + gp], 0,
-                              (int)(lrow0[beta][n1 * 4 + n1p] + lblk_row[r.cls][bl] + c0), pad16(Lb.dim[qlp]),
-                              (int)lneg[beta][n1 * 4 + n1p]});
+              const int mid_ = lmid[beta][n1 * 4 + n1p];
+              const int wc = wcls[pad16(Lb.dim[qlp])];
+              base.push_back({xtmap[ci][gp][rpp[2]], lmap[wc][nw / 16], 0, (int)xrow[(size_t)beta * ng + gp], 0,
+                              (int)(mblk_row[mid_][bl] + c0), pad16(Lb.dim[qlp]), (int)lneg[beta][n1 * 4 + n1p]});
             }
           }
           if (base.empty()) continue;
@@ -1292,11 +1341,25 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
     check_terms(t1, m1, n1max);
     check_terms(t2, m2, n2max);
     for (const TmTile& tl : t1) {
-      if (tl.rowmap_off < 0 || tl.rowmap_off + 128 > (long)rowmap.size())
-        throw Error(ST_ECUDA, "internal: stage-1 row map out of range");
+      if (tl.rowmap_off < 0 || tl.rowmap_off + 128 > (long)rowmap.size() || tl.cb0 < 0 || tl.cb1 > (int)cbtab.size() ||
+          tl.cb0 >= tl.cb1)
+        throw Error(ST_ECUDA, "internal: stage-1 row map or column blocks out of range");
+      long dmax = -1;
       for (int r = 0; r < 128; ++r) {
         const long d = rowmap[(size_t)(tl.rowmap_off + r)];
-        if (d < -1 || (d >= 0 && ((size_t)(d + tl.out_off + tl.n) > (size_t)tp->x_stride || (d + tl.out_off) % 8)))
+        if (d < -1 || d >= tl.xrows) throw Error(ST_ECUDA, "internal: stage-1 row outside its X region");
+        dmax = std::max(dmax, d);
+      }
+      // every 8-column chunk of the tile lies in one column block; its highest row
+      // stays inside the buffer (addresses grow with the row)
+      for (int cc = 0; cc < tl.n; cc += 8) {
+        const long col = tl.out_off + cc;
+        int hit = -1;
+        for (int e = tl.cb0; e < tl.cb1; ++e)
+          if (col >= cbtab[e].x && col + 8 <= cbtab[e].x + cbtab[e].y) hit = e;
+        if (hit < 0) throw Error(ST_ECUDA, "internal: stage-1 column outside the column blocks");
+        const long a0 = tl.xbase + tl.xrows * cbtab[hit].x + (col - cbtab[hit].x);
+        if (a0 < 0 || a0 % 8 || cbtab[hit].y % 8 || (dmax >= 0 && a0 + dmax * cbtab[hit].y + 8 > tp->x_stride))
           throw Error(ST_ECUDA, "internal: stage-1 store outside the X buffer");
       }
     }
@@ -1351,11 +1414,11 @@ void run_tma_sigma(Context& c, SigmaPlan& plan, const double* x, double* y) {
   cuda_check(cudaMemsetAsync(tp.sig_t.p, 0, tp.sig_total * sizeof(float), c.stream), "memset");
   for (auto& ch : tp.chunks) {
     if (ch.nz) launch_zero(ch.z.p, ch.nz, ch.zmax, c.stream);
-    cuda_check(launch_gemm_tma(TM_MODE_STORE_BF16, ch.t1.p, ch.n1, ch.m1.p, tp.maps.p, tp.rowmap.p, tp.xt.p, tp.nsl,
-                               tp.x_stride, tp.err.p, c.stream),
+    cuda_check(launch_gemm_tma(TM_MODE_STORE_BF16, ch.t1.p, ch.n1, ch.m1.p, tp.maps.p, tp.rowmap.p, tp.cbtab.p,
+                               tp.xt.p, tp.nsl, tp.x_stride, tp.err.p, c.stream),
                "tma stage 1");
-    cuda_check(launch_gemm_tma(TM_MODE_REDUCE_F32, ch.t2.p, ch.n2, ch.m2.p, tp.maps.p, tp.rowmap.p, tp.sig_t.p, 1, 0,
-                               tp.err.p, c.stream),
+    cuda_check(launch_gemm_tma(TM_MODE_REDUCE_F32, ch.t2.p, ch.n2, ch.m2.p, tp.maps.p, tp.rowmap.p, tp.cbtab.p,
+                               tp.sig_t.p, 1, 0, tp.err.p, c.stream),
                "tma stage 2");
   }
   if (tp.n_sig_jobs) launch_unconv(tp.sig_jobs.p, tp.n_sig_jobs, tp.sig_maxel, c.stream);

@@ -19,8 +19,10 @@
 //              commits to the stage's empty barrier / the accumulator's full
 //              barrier
 //   warps 2-5  epilogue: tcgen05.ld of their 32 tensor-memory lanes; BF16 rows
-//              scattered through a row map (X intermediates) or FP32 vector
-//              reductions (sigma^T, several tiles may add into one block)
+//              (X intermediates, up to three slices) staged in shared memory and
+//              written row by row with coalesced stores to the rows a row map
+//              gives, or FP32 vector reductions (sigma^T, several tiles may add
+//              into one block) of per-segment partial sums
 // Two (store mode, N <= 256) or four (reduce mode, N <= 128) accumulators let
 // the epilogue of one tile overlap the MMAs of the next.  Every wait is
 // bounded: on timeout the CTA raises a shared abort flag, records an error,
@@ -52,8 +54,9 @@ struct TmCfg {
   static constexpr int NACC = 512 / NMAX;
   static constexpr int B_BYTES = NMAX * TM_BOX_K * 2;
   static constexpr int STAGE_BYTES = TM_A_BYTES + B_BYTES;
-  // store mode: the output tile is staged in shared memory (rows padded by 16 bytes
-  // against bank conflicts) and written by bulk copies, one per row
+  // store mode: each epilogue warp stages its 32 rows in shared memory (rows padded
+  // by 16 bytes against bank conflicts) and writes them row by row with coalesced
+  // 16-byte stores
   static constexpr int STAGE_LD = NMAX + 8;  // elements per staged row
   static constexpr int STAGING = STORE ? 128 * STAGE_LD * 2 : 0;
   static constexpr int STAGES = STORE ? 3 : 6;
@@ -149,8 +152,9 @@ __device__ __forceinline__ uint32_t pack_bf16x2(uint32_t lo, uint32_t hi) {
 template <int MODE>
 __global__ void __launch_bounds__(TM_THREADS, 1)
     gemm_tma_kernel(const TmTile* __restrict__ tiles, int ntiles, const TmTerm* __restrict__ terms,
-                    const CUtensorMap* __restrict__ maps, const long* __restrict__ rowmap, void* __restrict__ out,
-                    int out_slices, long slice_stride, int* __restrict__ err) {
+                    const CUtensorMap* __restrict__ maps, const long* __restrict__ rowmap,
+                    const int2* __restrict__ cbtab, void* __restrict__ out, int out_slices, long slice_stride,
+                    int* __restrict__ err) {
   using Cfg = TmCfg<MODE>;
   constexpr int S = Cfg::STAGES;
   constexpr int STAGE_BYTES = Cfg::STAGE_BYTES;
@@ -200,39 +204,61 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
   volatile int* abort_flag = &abort_sh;
 
   if (warp == 0) {
-    // ---------------- TMA producer (one thread)
-    if (lane == 0) {
-      long j = 0;  // K steps issued
-      bool ok = true;
-      for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
-        const TmTile tl = tiles[ti];
-        const uint32_t bbytes = (uint32_t)tl.n * TM_BOX_K * 2;
-        long ks = 0;  // K steps of this tile so far
-        for (int t = tl.t0; t < tl.t1 && ok; ++t) {
-          const TmTerm tm = terms[t];
-          const uint32_t id = idesc_bf16(tl.n, tm.neg != 0);
-          const CUtensorMap* ma = maps + tm.amap;
-          const CUtensorMap* mb = maps + tm.bmap;
-          for (int k0 = 0; k0 < tm.k; k0 += TM_BOX_K, ++ks) {
-            const int s = (int)(j % S);
-            if (j >= S && !mbar_wait(&empty_b[s], (uint32_t)(((j / S) - 1) & 1), abort_flag)) {
-              ok = false;
-              break;
+    // ---------------- TMA producer: the warp loads the term descriptors of a tile 32 at
+    // a time (one per lane) and prefetches their tensor maps; lane 0 issues the copies
+    long j = 0;  // K steps issued (lane 0)
+    bool ok = true;
+    for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
+      const TmTile tl = tiles[ti];
+      const uint32_t bbytes = (uint32_t)tl.n * TM_BOX_K * 2;
+      long ks = 0;  // K steps of this tile so far
+      for (int tb = tl.t0; tb < tl.t1 && ok; tb += 32) {
+        const int cnt = min(32, tl.t1 - tb);
+        TmTerm mine{};
+        if (lane < cnt) {
+          mine = terms[tb + lane];
+          asm volatile("prefetch.tensormap [%0];\n" ::"l"(maps + mine.amap) : "memory");
+          asm volatile("prefetch.tensormap [%0];\n" ::"l"(maps + mine.bmap) : "memory");
+        }
+        for (int q = 0; q < cnt && ok; ++q) {
+          TmTerm tm;
+          tm.amap = __shfl_sync(0xffffffffu, mine.amap, q);
+          tm.bmap = __shfl_sync(0xffffffffu, mine.bmap, q);
+          tm.ax = __shfl_sync(0xffffffffu, mine.ax, q);
+          tm.ay = __shfl_sync(0xffffffffu, mine.ay, q);
+          tm.bx = __shfl_sync(0xffffffffu, mine.bx, q);
+          tm.by = __shfl_sync(0xffffffffu, mine.by, q);
+          tm.k = __shfl_sync(0xffffffffu, mine.k, q);
+          tm.neg = __shfl_sync(0xffffffffu, mine.neg, q);
+          if (lane == 0) {
+            const uint32_t id = idesc_bf16(tl.n, tm.neg != 0);
+            const CUtensorMap* ma = maps + tm.amap;
+            const CUtensorMap* mb = maps + tm.bmap;
+            const bool last_term = tb + q + 1 == tl.t1;
+            for (int k0 = 0; k0 < tm.k; k0 += TM_BOX_K, ++ks) {
+              const int s = (int)(j % S);
+              if (j >= S && !mbar_wait(&empty_b[s], (uint32_t)(((j / S) - 1) & 1), abort_flag)) {
+                ok = false;
+                break;
+              }
+              const bool last = last_term && k0 + TM_BOX_K >= tm.k;
+              meta_id[s] = id;
+              meta_nk[s] = min(TM_BOX_K / 16, (tm.k - k0) / 16);
+              meta_first[s] = (ks % SEG == 0) ? 1 : 0;
+              meta_seg_end[s] = (last || ks % SEG == SEG - 1) ? 1 : 0;
+              meta_last[s] = last ? 1 : 0;
+              const uint32_t sa = base + s * STAGE_BYTES;
+              mbar_arrive_expect_tx(&full_b[s], TM_A_BYTES + bbytes);
+              tma_load_2d(sa, ma, tm.ax + k0, tm.ay, &full_b[s]);
+              tma_load_2d(sa + TM_A_BYTES, mb, tm.bx + k0, tm.by, &full_b[s]);
+              ++j;
             }
-            const bool last = t + 1 == tl.t1 && k0 + TM_BOX_K >= tm.k;
-            meta_id[s] = id;
-            meta_nk[s] = min(TM_BOX_K / 16, (tm.k - k0) / 16);
-            meta_first[s] = (ks % SEG == 0) ? 1 : 0;
-            meta_seg_end[s] = (last || ks % SEG == SEG - 1) ? 1 : 0;
-            meta_last[s] = last ? 1 : 0;
-            const uint32_t sa = base + s * STAGE_BYTES;
-            mbar_arrive_expect_tx(&full_b[s], TM_A_BYTES + bbytes);
-            tma_load_2d(sa, ma, tm.ax + k0, tm.ay, &full_b[s]);
-            tma_load_2d(sa + TM_A_BYTES, mb, tm.bx + k0, tm.by, &full_b[s]);
-            ++j;
           }
+          ok = __shfl_sync(0xffffffffu, ok, 0);
         }
       }
+    }
+    if (lane == 0) {
       // every issued copy must land before the CTA may exit: the last (up to S)
       // issued stages complete their full phase when their bytes arrive
       for (long q = j - 1; q >= 0 && q >= j - S; --q) {
@@ -306,43 +332,91 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-        const long dst = rowmap[tl.rowmap_off + r];
-        __nv_bfloat16* g = reinterpret_cast<__nv_bfloat16*>(out) + (dst >= 0 ? dst : 0) + tl.out_off;
-        for (int sl = 0; sl < out_slices; ++sl) {
-          // the staging row must no longer be read by an earlier bulk copy
-          asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
-#pragma unroll
-          for (int cc = 0; cc < NMAX / 32; ++cc) {
-            const int c0 = cc * 32;
-            if (c0 < tl.n) {
-              uint32_t v[32];
-              const uint32_t taddr = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(acc * NMAX + c0);
-              tmem_ld32(taddr, v);
-              // slice sl of x = s0 + s1 + s2: BF16 of the remainder after the earlier slices
-#pragma unroll
-              for (int u = 0; u < 32; ++u) {
-                float x = __uint_as_float(v[u]);
-                for (int q = 0; q < sl; ++q) x -= __bfloat162float(__float2bfloat16_rn(x));
-                v[u] = __float_as_uint(x);
-              }
-#pragma unroll
-              for (int u = 0; u < 32; u += 8) {
-                uint4 w;
-                w.x = pack_bf16x2(v[u], v[u + 1]);
-                w.y = pack_bf16x2(v[u + 2], v[u + 3]);
-                w.z = pack_bf16x2(v[u + 4], v[u + 5]);
-                w.w = pack_bf16x2(v[u + 6], v[u + 7]);
-                if (c0 + u < tl.n) *reinterpret_cast<uint4*>(srow + c0 + u) = w;
-              }
+        const long row_own = rowmap[tl.rowmap_off + r];
+        // this lane's 8-column chunk of every row: its column block, base and width
+        long lane_base = -1;
+        int lane_w = 0;
+        if (lane * 8 < tl.n) {
+          const long col = tl.out_off + lane * 8;
+          for (int e = tl.cb0; e < tl.cb1; ++e) {
+            const int2 cb = cbtab[e];
+            if (col >= cb.x && col < cb.x + cb.y) {
+              lane_base = tl.xbase + tl.xrows * cb.x + (col - cb.x);
+              lane_w = cb.y;
             }
           }
-          if (dst >= 0) {
-            // the staging row (written through the generic proxy) is read by the bulk copy
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(g + sl * slice_stride),
-                         "r"(smem_u32(srow)), "r"((uint32_t)tl.n * 2)
-                         : "memory");
-            asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+        }
+        __nv_bfloat16* const wrows =
+            reinterpret_cast<__nv_bfloat16*>(base_ptr + S * STAGE_BYTES) + sub * 32 * Cfg::STAGE_LD;
+        if (out_slices == 1) {
+          // one pass: this thread's row into the staging rows of its warp, then the warp
+          // writes its 32 rows one after another, each as one contiguous run of 16-byte
+          // stores across the lanes (up to 512 bytes per instruction)
+#pragma unroll 1
+          for (int c0 = 0; c0 < tl.n; c0 += 32) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(acc * NMAX + c0), v);
+#pragma unroll
+            for (int u = 0; u < 32; u += 8) {
+              uint4 w;
+              w.x = pack_bf16x2(v[u], v[u + 1]);
+              w.y = pack_bf16x2(v[u + 2], v[u + 3]);
+              w.z = pack_bf16x2(v[u + 4], v[u + 5]);
+              w.w = pack_bf16x2(v[u + 6], v[u + 7]);
+              if (c0 + u < tl.n) *reinterpret_cast<uint4*>(srow + c0 + u) = w;
+            }
+          }
+          __syncwarp();
+#pragma unroll 1
+          for (int rr = 0; rr < 32; ++rr) {
+            const long d = __shfl_sync(0xffffffffu, row_own, rr);
+            if (d >= 0 && lane_base >= 0) {
+              const uint4 w = *reinterpret_cast<const uint4*>(wrows + rr * Cfg::STAGE_LD + lane * 8);
+              *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(out) + lane_base + d * lane_w) = w;
+            }
+          }
+          __syncwarp();
+        } else {
+          // two or three slices x = s0 + s1 + s2 from one read of each value, stored
+          // directly: per 8 columns one 16-byte store per slice into this row (the
+          // tensor-memory loads are warp-wide, the stores only for rows that exist)
+#pragma unroll 1
+          for (int c0 = 0; c0 < tl.n; c0 += 8) {
+            uint32_t v[8];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                           "=r"(v[7])
+                         : "r"(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(acc * NMAX + c0)));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            uint32_t w[3][4];
+#pragma unroll
+            for (int u = 0; u < 8; u += 2) {
+              float a = __uint_as_float(v[u]), b = __uint_as_float(v[u + 1]);
+#pragma unroll
+              for (int sl = 0; sl < 3; ++sl) {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+                w[sl][u / 2] = *reinterpret_cast<const uint32_t*>(&h);
+                a -= __low2float(h);
+                b -= __high2float(h);
+              }
+            }
+            // the column block of these 8 columns
+            const long col = tl.out_off + c0;
+            long cb_base = -1;
+            int cb_w = 0;
+            for (int e = tl.cb0; e < tl.cb1; ++e) {
+              const int2 cb = cbtab[e];
+              if (col >= cb.x && col < cb.x + cb.y) {
+                cb_base = tl.xbase + tl.xrows * cb.x + (col - cb.x);
+                cb_w = cb.y;
+              }
+            }
+            if (cb_base < 0 || row_own < 0) continue;
+            __nv_bfloat16* g = reinterpret_cast<__nv_bfloat16*>(out) + cb_base + row_own * cb_w;
+#pragma unroll
+            for (int sl = 0; sl < 3; ++sl)
+              if (sl < out_slices)
+                *reinterpret_cast<uint4*>(g + sl * slice_stride) = make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
@@ -388,7 +462,6 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
         }
       }
     }
-    if (STORE) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
   __syncthreads();
@@ -402,8 +475,8 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
 
 template <int MODE>
 cudaError_t launch_mode(const TmTile* d_tiles, int ntiles, const TmTerm* d_terms, const CUtensorMap* d_maps,
-                        const long* d_rowmap, void* out, int out_slices, long slice_stride, int* d_err,
-                        cudaStream_t s) {
+                        const long* d_rowmap, const int2* d_cbtab, void* out, int out_slices, long slice_stride,
+                        int* d_err, cudaStream_t s) {
   static const int nsm = [] {
     if (cudaFuncSetAttribute(gemm_tma_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TmCfg<MODE>::SMEM) !=
         cudaSuccess)
@@ -416,8 +489,8 @@ cudaError_t launch_mode(const TmTile* d_tiles, int ntiles, const TmTerm* d_terms
   if (nsm < 0) return cudaErrorInvalidValue;
   const int grid = ntiles < nsm ? ntiles : nsm;
   count_tc_launches(1);
-  gemm_tma_kernel<MODE><<<grid, TM_THREADS, TmCfg<MODE>::SMEM, s>>>(d_tiles, ntiles, d_terms, d_maps, d_rowmap, out,
-                                                                     out_slices, slice_stride, d_err);
+  gemm_tma_kernel<MODE><<<grid, TM_THREADS, TmCfg<MODE>::SMEM, s>>>(d_tiles, ntiles, d_terms, d_maps, d_rowmap,
+                                                                     d_cbtab, out, out_slices, slice_stride, d_err);
   return cudaGetLastError();
 }
 
@@ -442,15 +515,15 @@ EncodeTiledFn encoder() {
 int tma_max_n(int mode) { return mode == TM_MODE_STORE_BF16 ? 256 : 128; }
 
 cudaError_t launch_gemm_tma(int mode, const TmTile* d_tiles, int ntiles, const TmTerm* d_terms,
-                            const CUtensorMap* d_maps, const long* d_rowmap, void* out, int out_slices,
-                            long slice_stride, int* d_err, cudaStream_t s) {
+                            const CUtensorMap* d_maps, const long* d_rowmap, const int2* d_cbtab, void* out,
+                            int out_slices, long slice_stride, int* d_err, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
   if (out_slices < 1 || out_slices > 3) return cudaErrorInvalidValue;
   if (mode == TM_MODE_STORE_BF16)
-    return launch_mode<TM_MODE_STORE_BF16>(d_tiles, ntiles, d_terms, d_maps, d_rowmap, out, out_slices, slice_stride,
-                                           d_err, s);
+    return launch_mode<TM_MODE_STORE_BF16>(d_tiles, ntiles, d_terms, d_maps, d_rowmap, d_cbtab, out, out_slices,
+                                           slice_stride, d_err, s);
   if (mode == TM_MODE_REDUCE_F32)
-    return launch_mode<TM_MODE_REDUCE_F32>(d_tiles, ntiles, d_terms, d_maps, d_rowmap, out, 1, 0, d_err, s);
+    return launch_mode<TM_MODE_REDUCE_F32>(d_tiles, ntiles, d_terms, d_maps, d_rowmap, d_cbtab, out, 1, 0, d_err, s);
   return cudaErrorInvalidValue;
 }
 

@@ -23,8 +23,12 @@ struct TmTerm {
 
 // Output tile over the terms [t0, t1).  n: MMA width (multiple of 16, <= the
 // kernel's maximum).
-//   store mode (X intermediates, BF16): row r of the tile goes to out + rowmap[rowmap_off + r]
-//     + col0, columns [0, n); rowmap entries < 0 are skipped;
+//   store mode (X intermediates, BF16): the output matrix is split by columns into
+//     column blocks, each its own row-major submatrix of xrows rows: block e of
+//     cbtab[cb0..cb1) = (first column c0, width w) starts at element
+//     xbase + xrows * c0 and holds column c at (c - c0) of its rows.  Row r of the
+//     tile is row rowmap[rowmap_off + r] of the submatrices (< 0: skipped); its
+//     columns are out_off .. out_off + n (every 8-column chunk inside one block).
 //   reduce mode (sigma^T, FP32): rows r < m_valid are added (vector reductions) to
 //     out + out_off + r * ldo, columns [0, n).
 //   nseg (reduce mode): segments of the tile, ceil(K steps / TM_SEG_KSTEPS) with one K
@@ -36,6 +40,8 @@ struct TmTile {
   int ldo, nseg;
   long out_off;
   long rowmap_off;
+  long xbase, xrows;
+  int cb0, cb1;
 };
 
 constexpr int TM_MODE_STORE_BF16 = 1, TM_MODE_REDUCE_F32 = 2;
@@ -48,8 +54,8 @@ constexpr int TM_SEG_KSTEPS = 16;
 // slice_stride elements apart.  err: set to 1 if a bounded wait ran out (the CTA
 // then stops, lets its copies land and frees its tensor memory).
 cudaError_t launch_gemm_tma(int mode, const TmTile* d_tiles, int ntiles, const TmTerm* d_terms,
-                            const CUtensorMap* d_maps, const long* d_rowmap, void* out, int out_slices,
-                            long slice_stride, int* d_err, cudaStream_t s);
+                            const CUtensorMap* d_maps, const long* d_rowmap, const int2* d_cbtab, void* out,
+                            int out_slices, long slice_stride, int* d_err, cudaStream_t s);
 // maximum MMA width of a mode (256 for the BF16 store mode, 128 for the reduce mode)
 int tma_max_n(int mode);
 
