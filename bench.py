@@ -440,6 +440,10 @@ def run_sweeps(args):
     h, eri = synth.integrals(K, w["seed"], w["offdiag_std"])
     bonds, T = synth.random_mps(K, N, w["two_sz"], w["m0"], w["seed"] + 1, w["spread"])
     ctx = G.Context(h, eri, N, w["two_sz"])
+    if args.env_precision:
+        ctx.set_env_precision(args.env_precision)
+    if args.refine >= 0:
+        ctx.set_refinement(args.refine, args.refine_iters)
     ctx.set_mps(T, [b.labels() for b in bonds])
     del T
     tol = [1e-5] * (len(ramp) - 1) + [1e-6]
@@ -448,6 +452,7 @@ def run_sweeps(args):
     wall = time.perf_counter() - t0
     c = ctx.counters()
     line = {"mode": "sweeps", "workload": args.workload, "K": K, "N": N, "precision": args.precision,
+            "refine": args.refine, "env_precision": args.env_precision,
             "M": ramp, "energy": out["energy"].tolist(), "discarded": out["discarded"].tolist(),
             "sweep_s": out["seconds"].tolist(), "davidson_iters": out["davidson_iters"].tolist(),
             "sigma_tflops": [f / s / 1e12 if s > 0 else None for f, s in zip(out["sigma_flops"], out["sigma_seconds"])],
