@@ -33,6 +33,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "H_eff·ψ TFLOP/s & sweep s at K=40 M=2000, mixed vs FP64 GPU at |ΔE|≤1e-6 Eh"
+# DRAM bytes (read + write) of one H_eff.psi of the K=40 centre workload, both stages,
+# per precision, from one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum
+# (profiles/gemm_tma_kernel_sigma_k40_m2000.md); None where not captured for the
+# current kernels
+TRAFFIC = {}
 
 WORKLOADS = {
     # name: K, N, two_sz, M, spread of the synthetic sector dimensions, integral seed, h off-diagonal std,
@@ -171,13 +176,17 @@ def dgemm_measured(torch):
     return 2 * n ** 3 / best / 1e9
 
 
-def workload_name(args):
+def workload_name(args, sigma_calls_per_step=None):
     """The workload both arms report: the central two-site step of the named workload."""
     w = WORKLOADS[args.workload]
     K = w["K"]
     k = K // 2 - 1
+    ref = f", refinement by precision {args.refine} ({args.refine_iters} of the iterations)" if args.refine >= 0 else ""
+    env = ", tensor-core environment update" if args.env_precision else ""
+    meas = f", {sigma_calls_per_step:.1f} sigma calls/step measured" if sigma_calls_per_step is not None else ""
     return (f"{args.workload}: K={K} N={w['N']} 2Sz={w['two_sz']} M={w['M']}, two-site step at sites "
-            f"({k},{k + 1}), Davidson {args.dav_iters} iterations/step, precision {args.precision}")
+            f"({k},{k + 1}), Davidson budget {args.dav_iters} iterations/step{meas}, precision {args.precision}"
+            f"{ref}{env}")
 
 
 def aggregate_ranks(ms, flops, t_e2e, e2e_flops, world, device):
@@ -338,6 +347,23 @@ def run_ours(args, rank, world, local_rank):
     value = flops / (ms * 1e-3) / 1e12
     peaks, src = _measured_peaks()
     achieved_alg = sig_fl / sig_s / 1e12 if sig_s > 0 else None
+    # The sigma kernels of the step timed on their own after the timed region (CUDA
+    # events on the context stream, inputs resident in HBM, larger than L2): the
+    # step's operator and, with refinement, the refinement operator.
+    kern = {}
+    xk = torch.randn(nnz, device="cuda", dtype=torch.float64)
+    yk = torch.empty_like(xk)
+    torch.cuda.synchronize()
+    for label, prec in (("primary", args.precision), ("refine", args.refine)):
+        if prec is None or prec < 0 or (label == "refine" and prec == args.precision):
+            continue
+        ctx.set_precision(prec)
+        ctx.plan(k)
+        flk = ctx.sigma_device(xk.data_ptr(), yk.data_ptr())
+        msk = ctx.sigma_timing(3, xk.data_ptr(), yk.data_ptr())
+        kern[label] = {"precision": prec, "ms": msk, "tflops": flk / msk / 1e9,
+                       "plan": ctx.plan_stats() if prec >= 4 else None}
+    ctx.set_precision(args.precision)
     # products the tensor cores execute per algorithmic multiply-add: 1 (one BF16
     # pass) or 6 (three BF16 slices, products s_i t_j with i + j <= 2)
     nprod = {0: 1, 1: 1, 2: 6, 3: 3, 4: 1, 5: 6, 6: 3}[args.precision]
@@ -377,10 +403,11 @@ def run_ours(args, rank, world, local_rank):
         except Exception as exc:
             checks["error"] = f"fp64 checks: {exc}"
         fp64_cmp["fullsize_checks"] = checks
+    ach_k = kern["primary"]["tflops"]
     if args.precision == 0:
         peak = peaks["bf16_tflops_sustained"] * 1.25 / 2250.0
-        roof = {"bound": "alu", "achieved": achieved_alg, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved_alg / peak) if achieved_alg else None, "traffic": None,
+        roof = {"bound": "alu", "achieved": ach_k, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach_k / peak, "traffic": None,
                 "kernel": "gemm_f64_kernel (sigma stages 1+2)",
                 "peak_note": f"FP64 = {src} bf16 sustained x 1.25/2250 (nominal FP64/BF16)"}
         dtype = "f64"
@@ -389,10 +416,11 @@ def run_ours(args, rank, world, local_rank):
         # achieved = ALGORITHMIC flops (2mnk over non-zero blocks, no padding, no extra
         # split-precision products) / event-timed sigma time; the products the tensor
         # cores actually execute for the slices are reported beside it, not in frac
-        roof = {"bound": "tensor", "achieved": achieved_alg, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved_alg / peak) if achieved_alg else None, "traffic": None,
-                "kernel": "gemm_bf16_tc_kernel (sigma stages 1+2)",
-                "executed_tflops": achieved_alg * nprod if achieved_alg else None,
+        roof = {"bound": "tensor", "achieved": ach_k, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach_k / peak, "traffic": TRAFFIC.get(args.precision) if args.workload == "k40_m2000" else None,
+                "kernel": ("gemm_tma_kernel<1>+<2> (sigma stages 1+2, TMA-staged)" if args.precision >= 4 else
+                           "gemm_bf16_tc_kernel (sigma stages 1+2)") + f", precision {args.precision}",
+                "executed_tflops": ach_k * nprod,
                 "products_per_multiply_add": nprod,
                 "peak_note": f"{src} bf16 dense, sustained (kernel timed inside a long step); achieved and frac "
                              f"count algorithmic flops only"}
@@ -401,14 +429,14 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-        "config": {"workload": workload_name(args),
+        "config": {"workload": workload_name(args, sig_calls / args.steps),
                    "psi_nnz": nnz, "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (no flush)",
                    "setup_s": round(setup_s, 1), "setup_launches": int(setup_launches),
                    "stage1": "stacked" if args.stage1_stacked else "per-sector",
                    "w_sums": "fp64" if args.fp64_w_sums else
                    (f"fp64 (tensor-core sums failed: {w_sums_failed})" if w_sums_failed else
                     "tensor cores (bf16x3) for sums of >= 1e5 terms that feed only the sigma, fp64 otherwise")},
-        "sigma_tflops": achieved_alg, "sigma_calls": sig_calls, "fp64_comparison": fp64_cmp,
+        "sigma_tflops": achieved_alg, "sigma_calls": sig_calls, "sigma_kernels": kern, "fp64_comparison": fp64_cmp,
         "tma_plan": plan_stats,
         "step_phase_s": phases,
         "step_phase_tflops": phase_tf,
@@ -582,8 +610,9 @@ def main():
     ap.add_argument("--fp64-w-sums", action="store_true",
                     help="form every W-contracted sum on the FP64 units (default: large sums that feed only "
                          "the tensor-core sigma run on the tensor cores)")
-    ap.add_argument("--env-precision", type=int, default=0, choices=[0, 2],
-                    help="environment updates: 0 FP64 units, 2 tensor cores with three BF16 slices")
+    ap.add_argument("--env-precision", type=int, default=0, choices=[0, 2, 3],
+                    help="environment updates: 0 FP64 units, 2 tensor cores with three BF16 slices, "
+                         "3 tensor cores with exactly split operands")
     ap.add_argument("--refine", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4, 5, 6],
                     help="precision of the Davidson refinement phase of each step (-1: none)")
     ap.add_argument("--refine-iters", type=int, default=4,

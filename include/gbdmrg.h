@@ -111,8 +111,13 @@ gbdmrg_status gbdmrg_set_tma_budget(gbdmrg_ctx* ctx, int64_t megabytes);
  * prenormmatrix/prenormdec): 0 = FP64 grouped GEMMs on the FP64 units (default);
  * 2 = both grouped GEMMs of the update on the tensor cores with every operand in
  * three BF16 slices (six products, FP32 accumulation, intermediates as three
- * BF16 slices of the FP32 results), the new operators stored in FP64.  EINVAL for
- * any other value. */
+ * BF16 slices of the FP32 results), the new operators stored in FP64 (FP32-level
+ * accuracy); 3 = both GEMMs on the tensor cores with exactly split operands: every
+ * block scaled by a power of two and split into five 7-bit integer slices (exact in
+ * BF16), the slice products of each level summed exactly in the FP32 accumulators
+ * and the levels added in two-float registers, stored in FP64 (operands carried to
+ * ~2^-35 of each block's largest element); sectors above 128 states fall back to
+ * the FP64 units.  EINVAL for any other value. */
 gbdmrg_status gbdmrg_set_env_precision(gbdmrg_ctx* ctx, int32_t precision);
 /* Refinement of the Davidson solve of every later tensor-core two-site step
  * (gbdmrg_step, gbdmrg_run; not part of the paper, which names no eigensolver):

@@ -391,7 +391,8 @@ class Context:
         self._check(self.lib.gbdmrg_set_tma_budget(self.h, int(megabytes)), "set_tma_budget")
 
     def set_env_precision(self, precision: int):
-        """Environment updates: 0 FP64 units, 2 tensor cores with three BF16 slices."""
+        """Environment updates: 0 FP64 units, 2 tensor cores with three BF16 slices,
+        3 tensor cores with exactly split operands (FP64-level)."""
         self._check(self.lib.gbdmrg_set_env_precision(self.h, int(precision)), "set_env_precision")
 
     def set_refinement(self, precision: int, max_iters: int = 8):

@@ -317,7 +317,7 @@ gbdmrg_status gbdmrg_set_tma_budget(gbdmrg_ctx* ctx, int64_t megabytes) {
 }
 
 gbdmrg_status gbdmrg_set_env_precision(gbdmrg_ctx* ctx, int32_t precision) {
-  if (!ctx || (precision != 0 && precision != 2)) return GBDMRG_EINVAL;
+  if (!ctx || (precision != 0 && precision != 2 && precision != 3)) return GBDMRG_EINVAL;
   return guard(ctx, [&] { ctx->c.env_precision = precision; });
 }
 

@@ -626,7 +626,21 @@ static inline int tilde_col(const Bond& b, const OpLayout& L, int row) {
 
 static size_t budget_elems(Context& c) { return (size_t)c.chunk_budget_mb * (1u << 20) / sizeof(double); }
 
+// sectors of at most 128 states: the exact tensor-core update sums each block's K in one
+// exact FP32 accumulation
+static bool exact_env_fits(const SiteT& A) {
+  for (int d : A.L.dim)
+    if (d > 128) return false;
+  for (int d : A.R.dim)
+    if (d > 128) return false;
+  return true;
+}
+
 void env_update_left(Context& c, Tilde& lt, const SiteT& A, int site, Env& out) {
+  if (c.env_precision == 3 && exact_env_fits(A)) {
+    env_update_exact(c, lt, A, site, out, true);
+    return;
+  }
   if (c.env_precision == 2) {
     env_update_tc(c, lt, A, site, out, true);
     return;
@@ -707,6 +721,10 @@ void env_update_left(Context& c, Tilde& lt, const SiteT& A, int site, Env& out) 
 }
 
 void env_update_right(Context& c, Tilde& rt, const SiteT& B, int site, Env& out) {
+  if (c.env_precision == 3 && exact_env_fits(B)) {
+    env_update_exact(c, rt, B, site, out, false);
+    return;
+  }
   if (c.env_precision == 2) {
     env_update_tc(c, rt, B, site, out, false);
     return;

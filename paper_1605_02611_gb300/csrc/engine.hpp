@@ -268,7 +268,8 @@ struct Context {
   // refine_precision (-1: none), of at most refine_iters iterations
   int refine_precision = -1;
   int refine_iters = 8;
-  // environment updates: 0 FP64 grouped GEMMs; 2 tensor cores, three BF16 slices
+  // environment updates: 0 FP64 grouped GEMMs; 2 tensor cores, three BF16 slices;
+  // 3 tensor cores with exactly split operands (FP64-level results)
   int env_precision = 0;
   // X intermediates of the TMA-staged plan per chunk of bond states (MB)
   long tma_budget_mb = 65536;
@@ -306,6 +307,9 @@ void env_alloc(Context& c, Env& e, const Bond& b, const std::vector<BondState>& 
 // environment update with both grouped GEMMs on the tensor cores, operands in three BF16
 // slices (engine_mixed.cu); left = true: L_{k+1} from L_k and A[k], else R_k from R_{k+1}
 void env_update_tc(Context& c, Tilde& t, const SiteT& A, int site, Env& out, bool left);
+// the same update with exactly split operands: FP64-level results on the tensor cores
+// (engine_mixed.cu); sectors of at most 128 states
+void env_update_exact(Context& c, Tilde& t, const SiteT& A, int site, Env& out, bool left);
 void env_update_left(Context& c, Tilde& lt, const SiteT& A, int site, Env& out);
 void env_update_right(Context& c, Tilde& rt, const SiteT& B, int site, Env& out);
 

@@ -1736,6 +1736,406 @@ void env_update_tc(Context& c, Tilde& t, const SiteT& A, int site, Env& out, boo
   cuda_check(cudaStreamSynchronize(c.stream), "sync");
 }
 
+// ---------------------------------------------------------------- exact environment update
+
+// Environment update (Eqs. leftrenorm/rightrenorm, prenormmatrix/prenormdec) on the
+// tensor cores with FP64-level results: every FP64 block is scaled by a power of two and
+// split into TM_EXACT_SLICES integer slices of 7 bits, exact in BF16; the products of two
+// slices summed over a block's K (<= 128 columns, products <= 2^14) are exact integers in
+// the FP32 accumulators; pairs of slices of one level i + j share a weight and accumulate
+// together (still exact), and the levels are added with their powers of two in two-float
+// (hi + lo) registers and stored in FP64.  Dropped pairs (i + j >= slices) and the
+// remainder of the splitting are below 2^-35 of each block's largest element.
+//   left : E1  T^T_beta[n1][j, ql] = sum_{n1'} At^{n1'}[j, ql'] Lt^{n1 n1'}[ql, ql']
+//          E2  L'[qa, qa']        = sum_{n1} At^{n1}[qa, ql] T^T_beta[n1][qa', ql]
+//   right: E1  T_beta[n2][j, qr]  = sum_{n2'} B^{n2'}[j, qr'] Rt^{n2 n2'}[qr, qr']
+//          E2  R'[qb, qb']        = sum_{n2} B^{n2}[qb, qr] T_beta[n2][qb', qr]
+constexpr int TM_EXACT_SLICES = 5;
+
+namespace {
+
+// matrices of one padded width (K dimension) holding blocks stacked by rows
+struct WidthClasses {
+  std::map<int, int> cls;  // width -> class
+  std::vector<int> w;
+  std::vector<long> rows, base;
+  int of(int width) {
+    auto it = cls.find(width);
+    if (it != cls.end()) return it->second;
+    const int c = (int)w.size();
+    cls[width] = c;
+    w.push_back(width);
+    rows.push_back(0);
+    base.push_back(0);
+    return c;
+  }
+  long place(int c, int nrows) {  // row offset of a new block of nrows rows (padded to 16)
+    const long r = rows[c];
+    rows[c] += pad16(nrows);
+    return r;
+  }
+  long finish() {
+    long t = 0;
+    for (size_t c = 0; c < w.size(); ++c) {
+      base[c] = t;
+      t += rows[c] * w[c];
+    }
+    return std::max<long>(t, 8);
+  }
+};
+
+}  // namespace
+
+void env_update_exact(Context& c, Tilde& t, const SiteT& A, int site, Env& out, bool left) {
+  constexpr int NSL = TM_EXACT_SLICES;
+  const auto& st = left ? c.mpo.bonds[site + 1] : c.mpo.bonds[site];
+  const Bond& Lb = A.L;
+  const Bond& Rb = A.R;
+  Env& env = *t.env;
+  const Bond& ob = left ? Rb : Lb;  // bond of the new operators
+  const Bond& ib = left ? Lb : Rb;  // bond of the contracted index
+  env_alloc(c, out, ob, st);
+  const int no = ob.nsec();
+  const int nmax = tma_max_n(TM_MODE_EXACT_F64);
+  std::vector<SplitJob> split1;  // site and operator blocks
+  int nexpo = 0;
+  // ---- site tensor: left At blocks [d(qr) x d(ql)], right B blocks [d(ql) x d(qr)]; K = columns
+  WidthClasses sc;
+  std::vector<int> s_cls(A.blocks.size()), s_exp(A.blocks.size());
+  std::vector<long> s_row(A.blocks.size());
+  for (size_t b = 0; b < A.blocks.size(); ++b) {
+    const Block& B = A.blocks[b];
+    const int rows = left ? B.cols : B.rows, kdim = left ? B.rows : B.cols;
+    s_cls[b] = sc.of(pad16(kdim));
+    s_row[b] = sc.place(s_cls[b], rows);
+    s_exp[b] = nexpo++;
+  }
+  const long ss = sc.finish();
+  DArr<__nv_bfloat16> smir;
+  smir.alloc((size_t)ss * NSL, c.stream);
+  cuda_check(cudaMemsetAsync(smir.p, 0, smir.n * sizeof(__nv_bfloat16), c.stream), "memset");
+  for (size_t b = 0; b < A.blocks.size(); ++b) {
+    const Block& B = A.blocks[b];
+    const int w = sc.w[s_cls[b]];
+    split1.push_back({A.d.p + B.off, smir.p + sc.base[s_cls[b]] + s_row[b] * w, ss, B.rows, B.cols, B.cols, w,
+                      left ? B.cols : pad16(B.cols), left ? 1 : 0, s_exp[b], 1.0});
+  }
+  // ---- W-contracted operators: every distinct (operator, coefficient), all blocks; K = columns
+  WidthClasses oc;
+  struct KeyHash {
+    size_t operator()(const std::pair<const double*, double>& kk) const {
+      uint64_t b;
+      std::memcpy(&b, &kk.second, sizeof b);
+      return std::hash<uint64_t>()((uint64_t)(uintptr_t)kk.first * 0x9e3779b97f4a7c15ULL ^ b);
+    }
+  };
+  std::unordered_map<std::pair<const double*, double>, int, KeyHash> mid_of;
+  std::vector<std::vector<long>> m_row;  // per mirror, per block
+  std::vector<std::vector<int>> m_exp;
+  std::vector<int> m_cls_of_ref;
+  struct PendO {
+    const double* src;
+    int cls;
+    long row;
+    int rows, cols, ex;
+    double coef;
+  };
+  std::vector<PendO> opend;
+  std::vector<std::array<int, 16>> mref(st.size());
+  for (size_t beta = 0; beta < st.size(); ++beta)
+    for (int nn = 0; nn < 16; ++nn) {
+      mref[beta][nn] = -1;
+      const TRef& r = t.ref[beta][nn];
+      if (!r.p) continue;
+      auto key = std::make_pair(r.p, r.coef);
+      auto it = mid_of.find(key);
+      if (it == mid_of.end()) {
+        const int id = (int)m_row.size();
+        it = mid_of.emplace(key, id).first;
+        const OpLayout& L = env.cls[r.cls];
+        m_row.emplace_back(L.blocks.size());
+        m_exp.emplace_back(L.blocks.size());
+        for (size_t b = 0; b < L.blocks.size(); ++b) {
+          const Block& B = L.blocks[b];
+          const int cl = oc.of(pad16(B.cols));
+          m_row[id][b] = oc.place(cl, B.rows);
+          m_exp[id][b] = nexpo++;
+          opend.push_back({r.p + B.off, cl, m_row[id][b], B.rows, B.cols, m_exp[id][b], r.coef});
+        }
+      }
+      mref[beta][nn] = it->second;
+    }
+  const long os = oc.finish();
+  DArr<__nv_bfloat16> omir;
+  omir.alloc((size_t)os * NSL, c.stream);
+  cuda_check(cudaMemsetAsync(omir.p, 0, omir.n * sizeof(__nv_bfloat16), c.stream), "memset");
+  for (const PendO& po : opend) {
+    const int w = oc.w[po.cls];
+    split1.push_back({po.src, omir.p + oc.base[po.cls] + po.row * w, os, po.rows, po.cols, po.cols, w, po.cols, 0,
+                      po.ex, po.coef});
+  }
+  // ---- intermediate T blocks (FP64) per (beta, n, j): d(j) x d(q) with q the inner sector
+  auto inner_of = [&](size_t beta, int n, int j) -> int {
+    if (left) return Lb.find(Rb.qa[j] + st[beta].dna - LQA[n], Rb.qb[j] + st[beta].dnb - LQB[n]);
+    return Rb.find(Lb.qa[j] + st[beta].dna + LQA[n], Lb.qb[j] + st[beta].dnb + LQB[n]);
+  };
+  std::vector<std::vector<long>> tpos(st.size());
+  std::vector<std::vector<int>> t_cls(st.size()), t_exp(st.size());
+  std::vector<std::vector<long>> t_row(st.size());
+  WidthClasses tc_;
+  long ttot = 0;
+  for (size_t beta = 0; beta < st.size(); ++beta) {
+    tpos[beta].assign((size_t)4 * no, -1);
+    t_cls[beta].assign((size_t)4 * no, -1);
+    t_exp[beta].assign((size_t)4 * no, -1);
+    t_row[beta].assign((size_t)4 * no, -1);
+  }
+  // ---- E1 work lists (also decides which T blocks exist)
+  std::vector<TmTile> e1t;
+  std::vector<TmTerm> e1m;
+  // maps are created after all buffers exist: terms first hold (class, slice) codes
+  // amap = class index of the site classes, bmap = class index of the operator classes;
+  // box heights are the tile widths, resolved below
+  struct PendTerm {
+    int acls, bcls, ay, by, k, ea, eb, flags, si, sj, n;
+  };
+  std::vector<PendTerm> e1p;
+  std::vector<long> e1_out;  // tile -> T element offset of (r0, c0), filled with tpos
+  struct E1Tile {
+    size_t beta;
+    int n, j, r0, c0, m_valid, nvalid, nw;
+    int p0, p1;
+  };
+  std::vector<E1Tile> e1x;
+  double fl = 0;
+  for (size_t beta = 0; beta < st.size(); ++beta)
+    for (int n = 0; n < 4; ++n)
+      for (int j = 0; j < no; ++j) {
+        const int q = inner_of(beta, n, j);
+        if (q < 0) continue;
+        const int rows = ob.dim[j], cols = ib.dim[q];
+        // the source terms (site block, operator block) of this T block
+        std::vector<std::array<int, 4>> src;  // (site block, mirror id, op block, slot)
+        for (int np = 0; np < 4; ++np) {
+          const int slot = n * 4 + np;
+          const TRef& r = t.ref[beta][slot];
+          if (!r.p) continue;
+          const OpLayout& Lay = env.cls[r.cls];
+          int qp, bl, sb;
+          if (left) {
+            qp = Lb.find(Lb.qa[q] - Lay.da, Lb.qb[q] - Lay.db);
+            if (qp < 0) continue;
+            bl = Lay.blk_of_col[qp];
+            if (bl < 0 || Lay.blocks[bl].rs != q) continue;
+            sb = A.blk(qp, np);
+            if (sb < 0 || A.blocks[sb].cs != j) continue;
+          } else {
+            qp = Rb.find(Lb.qa[j] + LQA[np], Lb.qb[j] + LQB[np]);
+            if (qp < 0) continue;
+            bl = Lay.blk_of_col[qp];
+            if (bl < 0 || Lay.blocks[bl].rs != q) continue;
+            sb = A.blk(j, np);
+            if (sb < 0 || A.blocks[sb].cs != qp) continue;
+          }
+          src.push_back({sb, mref[beta][slot], bl, slot});
+          fl += 2.0 * rows * cols * ib.dim[qp];
+        }
+        if (src.empty()) continue;
+        const size_t ti = (size_t)n * no + j;
+        tpos[beta][ti] = ttot;
+        ttot += (long)rows * cols;
+        t_cls[beta][ti] = tc_.of(pad16(cols));
+        t_row[beta][ti] = tc_.place(t_cls[beta][ti], rows);
+        t_exp[beta][ti] = nexpo++;
+        for (int r0 = 0; r0 < rows; r0 += 128)
+          for (int c0 = 0; c0 < cols; c0 += nmax) {
+            E1Tile x{beta, n, j, r0, c0, std::min(128, rows - r0), std::min(nmax, cols - c0), 0, (int)e1p.size(), 0};
+            x.nw = pad16(x.nvalid);
+            for (const auto& sr : src) {
+              const Block& SB = A.blocks[sr[0]];
+              const int kdim = left ? SB.rows : SB.cols;
+              e1p.push_back({s_cls[sr[0]], oc.cls[pad16(kdim)], (int)(s_row[sr[0]] + r0),
+                             (int)(m_row[sr[1]][sr[2]] + c0), pad16(kdim), s_exp[sr[0]], m_exp[sr[1]][sr[2]],
+                             NSL << 4, 0, 0, x.nw});
+            }
+            x.p1 = (int)e1p.size();
+            e1x.push_back(x);
+          }
+      }
+  const long ts = tc_.finish();
+  DArr<double> T64;
+  T64.alloc(std::max<long>(ttot, 1), c.stream);
+  DArr<__nv_bfloat16> tmir;
+  tmir.alloc((size_t)ts * NSL, c.stream);
+  cuda_check(cudaMemsetAsync(tmir.p, 0, tmir.n * sizeof(__nv_bfloat16), c.stream), "memset");
+  DArr<int> expo;
+  expo.alloc(std::max(nexpo, 1), c.stream);
+  // ---- tensor maps: per class and slice; operator and T classes per box height
+  std::vector<CUtensorMap> maps;
+  auto add_map = [&](const DArr<__nv_bfloat16>& buf, long off, long stride, long rows, int w, int box) {
+    const int first = (int)maps.size();
+    for (int sl = 0; sl < NSL; ++sl) {
+      const long o = off + sl * stride;
+      if (rows < 1 || o < 0 || o % 8 || (size_t)(o + rows * w) > buf.n)
+        throw Error(ST_ECUDA, "internal: tensor map outside its buffer");
+      CUtensorMap m;
+      if (!encode_bf16_map(&m, buf.p + o, (uint64_t)rows, (uint64_t)w, (uint64_t)w, (uint32_t)box))
+        throw Error(ST_ECUDA, "cuTensorMapEncodeTiled failed");
+      maps.push_back(m);
+    }
+    return first;
+  };
+  std::vector<int> smap(sc.w.size(), -1);
+  for (size_t k = 0; k < sc.w.size(); ++k)
+    if (sc.rows[k] > 0) smap[k] = add_map(smir, sc.base[k], ss, sc.rows[k], sc.w[k], 128);
+  std::vector<std::vector<int>> omap(oc.w.size(), std::vector<int>(nmax / 16 + 1, -1));
+  for (size_t k = 0; k < oc.w.size(); ++k)
+    if (oc.rows[k] > 0)
+      for (int h = 16; h <= nmax; h += 16) omap[k][h / 16] = add_map(omir, oc.base[k], os, oc.rows[k], oc.w[k], h);
+  std::vector<std::vector<int>> tmap(tc_.w.size(), std::vector<int>(nmax / 16 + 1, -1));
+  for (size_t k = 0; k < tc_.w.size(); ++k)
+    if (tc_.rows[k] > 0)
+      for (int h = 16; h <= nmax; h += 16) tmap[k][h / 16] = add_map(tmir, tc_.base[k], ts, tc_.rows[k], tc_.w[k], h);
+  DArr<CUtensorMap> dmaps;
+  dmaps.upload(maps, c.stream);
+  // ---- E1 tiles and terms
+  for (const E1Tile& x : e1x) {
+    TmTile tl{};
+    tl.t0 = (int)e1m.size();
+    for (int i = x.p0; i < x.p1; ++i) {
+      const PendTerm& p = e1p[(size_t)i];
+      e1m.push_back({smap[p.acls], omap[p.bcls][p.n / 16], 0, p.ay, 0, p.by, p.k, p.flags, p.ea, p.eb});
+    }
+    tl.t1 = (int)e1m.size();
+    tl.n = x.nw;
+    tl.m_valid = x.m_valid;
+    tl.nvalid = x.nvalid;
+    const int cols = ib.dim[inner_of(x.beta, x.n, x.j)];
+    tl.ldo = cols;
+    tl.out_off = tpos[x.beta][(size_t)x.n * no + x.j] + (long)x.r0 * cols + x.c0;
+    e1t.push_back(tl);
+  }
+  // ---- split of the T blocks after E1
+  std::vector<SplitJob> split2;
+  for (size_t beta = 0; beta < st.size(); ++beta)
+    for (int n = 0; n < 4; ++n)
+      for (int j = 0; j < no; ++j) {
+        const size_t ti = (size_t)n * no + j;
+        if (tpos[beta][ti] < 0) continue;
+        const int rows = ob.dim[j], cols = ib.dim[inner_of(beta, n, j)];
+        const int cl = t_cls[beta][ti], w = tc_.w[cl];
+        split2.push_back({T64.p + tpos[beta][ti], tmir.p + tc_.base[cl] + t_row[beta][ti] * w, ts, rows, cols, cols, w,
+                          pad16(cols), 0, t_exp[beta][ti], 1.0});
+      }
+  // ---- E2 tiles: every block of every new operator
+  std::vector<TmTile> e2t;
+  std::vector<TmTerm> e2m;
+  for (size_t beta = 0; beta < st.size(); ++beta) {
+    const OpLayout& Lo = out.lay((int)beta);
+    double* obase = out.op((int)beta);
+    for (const Block& B : Lo.blocks) {
+      std::vector<std::array<int, 2>> src;  // (site block, T index)
+      for (int n = 0; n < 4; ++n) {
+        int q, sb;
+        if (left) {
+          q = Lb.find(Rb.qa[B.rs] - LQA[n], Rb.qb[B.rs] - LQB[n]);
+          if (q < 0) continue;
+          sb = A.blk(q, n);
+          if (sb < 0 || A.blocks[sb].cs != B.rs) continue;
+        } else {
+          q = Rb.find(Lb.qa[B.rs] + LQA[n], Lb.qb[B.rs] + LQB[n]);
+          if (q < 0) continue;
+          sb = A.blk(B.rs, n);
+          if (sb < 0 || A.blocks[sb].cs != q) continue;
+        }
+        const size_t ti = (size_t)n * no + B.cs;
+        if (tpos[beta][ti] < 0) continue;
+        src.push_back({sb, (int)ti});
+        fl += 2.0 * B.rows * B.cols * ib.dim[q];
+      }
+      if (src.empty()) continue;
+      for (int r0 = 0; r0 < B.rows; r0 += 128)
+        for (int c0 = 0; c0 < B.cols; c0 += nmax) {
+          TmTile tl{};
+          tl.t0 = (int)e2m.size();
+          tl.m_valid = std::min(128, B.rows - r0);
+          tl.nvalid = std::min(nmax, B.cols - c0);
+          tl.n = pad16(tl.nvalid);
+          for (const auto& sr : src) {
+            const Block& SB = A.blocks[sr[0]];
+            const int kdim = left ? SB.rows : SB.cols;
+            const int tcl = t_cls[beta][(size_t)sr[1]];
+            e2m.push_back({smap[s_cls[sr[0]]], tmap[tcl][tl.n / 16], 0, (int)(s_row[sr[0]] + r0), 0,
+                           (int)(t_row[beta][(size_t)sr[1]] + c0), pad16(kdim), NSL << 4, s_exp[sr[0]],
+                           t_exp[beta][(size_t)sr[1]]});
+          }
+          tl.t1 = (int)e2m.size();
+          tl.ldo = B.cols;
+          tl.out_off = (obase - out.data[out.st_cls[(int)beta]].p) + B.off + (long)r0 * B.cols + c0;
+          tl.nseg = out.st_cls[(int)beta];  // output class (host only: selects the launch)
+          e2t.push_back(tl);
+        }
+    }
+  }
+  c.other_flops_total += fl;
+  // ---- bounds of every output and split job before anything runs
+  for (const SplitJob& j : split1)
+    if (j.rows < 1 || j.cols < 1 || j.expo < 0 || j.expo >= nexpo) throw Error(ST_ECUDA, "internal: split job");
+  for (const TmTile& tl : e1t)
+    if (tl.out_off < 0 || tl.out_off + (long)(tl.m_valid - 1) * tl.ldo + tl.nvalid > (long)T64.n || tl.n > nmax ||
+        tl.nvalid > tl.n || tl.t1 <= tl.t0)
+      throw Error(ST_ECUDA, "internal: exact stage-1 tile");
+  for (const TmTile& tl : e2t) {
+    const size_t cap = out.data[tl.nseg].n;
+    if (tl.out_off < 0 || (size_t)(tl.out_off + (long)(tl.m_valid - 1) * tl.ldo + tl.nvalid) > cap || tl.n > nmax ||
+        tl.nvalid > tl.n || tl.t1 <= tl.t0)
+      throw Error(ST_ECUDA, "internal: exact stage-2 tile");
+  }
+  auto check_m = [&](const std::vector<TmTerm>& mm) {
+    for (const TmTerm& m : mm)
+      if (m.amap < 0 || m.amap + NSL > (int)maps.size() || m.bmap < 0 || m.bmap + NSL > (int)maps.size() ||
+          m.k < 16 || m.k % 16 || m.k > 128 || m.ea < 0 || m.ea >= nexpo || m.eb < 0 || m.eb >= nexpo ||
+          ((m.neg >> 4) & 15) != NSL)
+        throw Error(ST_ECUDA, "internal: exact term");
+  };
+  check_m(e1m);
+  check_m(e2m);
+  // ---- run: split, E1, split T, E2 (one launch per output class of the new operators)
+  DArr<int> err;
+  err.alloc(1, c.stream);
+  cuda_check(cudaMemsetAsync(err.p, 0, sizeof(int), c.stream), "memset");
+  DArr<SplitJob> dj1, dj2;
+  dj1.upload(split1, c.stream);
+  cuda_check(launch_split_exact(dj1.p, (int)split1.size(), NSL, expo.p, c.stream), "exact split");
+  DArr<TmTile> d1t;
+  DArr<TmTerm> d1m;
+  d1t.upload(e1t, c.stream);
+  d1m.upload(e1m, c.stream);
+  cuda_check(launch_gemm_tma(TM_MODE_EXACT_F64, d1t.p, (int)e1t.size(), d1m.p, dmaps.p, nullptr, nullptr, T64.p, 1, 0,
+                             err.p, c.stream, expo.p),
+             "exact stage 1");
+  dj2.upload(split2, c.stream);
+  cuda_check(launch_split_exact(dj2.p, (int)split2.size(), NSL, expo.p, c.stream), "exact split of T");
+  DArr<TmTerm> d2m;
+  d2m.upload(e2m, c.stream);
+  for (size_t ci = 0; ci < out.cls.size(); ++ci) {
+    std::vector<TmTile> part;
+    for (const TmTile& tl : e2t)
+      if (tl.nseg == (int)ci) part.push_back(tl);
+    if (part.empty()) continue;
+    DArr<TmTile> d2t;
+    d2t.upload(part, c.stream);
+    cuda_check(launch_gemm_tma(TM_MODE_EXACT_F64, d2t.p, (int)part.size(), d2m.p, dmaps.p, nullptr, nullptr,
+                               out.data[ci].p, 1, 0, err.p, c.stream, expo.p),
+               "exact stage 2");
+    cuda_check(cudaStreamSynchronize(c.stream), "sync");
+  }
+  int h = 0;
+  cuda_check(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h");
+  cuda_check(cudaStreamSynchronize(c.stream), "sync");
+  if (h) throw Error(ST_ETIMEOUT, "tensor-core GEMM: a bounded wait ran out");
+}
+
 // ---------------------------------------------------------------- batched sigma
 
 // Several independent two-site problems (each prepared in tensor-core precision

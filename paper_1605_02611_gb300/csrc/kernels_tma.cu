@@ -50,7 +50,9 @@ constexpr long TM_WAIT_LIMIT = 1L << 24;
 template <int MODE>
 struct TmCfg {
   static constexpr bool STORE = MODE == TM_MODE_STORE_BF16;
-  static constexpr int NMAX = STORE ? 256 : 128;
+  static constexpr bool EXACT = MODE == TM_MODE_EXACT_F64;
+  // exact mode: 64 columns, so that the two-float sums (128 registers) fit
+  static constexpr int NMAX = STORE ? 256 : (EXACT ? 64 : 128);
   static constexpr int NACC = 512 / NMAX;
   static constexpr int B_BYTES = NMAX * TM_BOX_K * 2;
   static constexpr int STAGE_BYTES = TM_A_BYTES + B_BYTES;
@@ -59,10 +61,10 @@ struct TmCfg {
   // 16-byte stores
   static constexpr int STAGE_LD = NMAX + 8;  // elements per staged row
   static constexpr int STAGING = STORE ? 128 * STAGE_LD * 2 : 0;
-  static constexpr int STAGES = STORE ? 3 : 6;
+  static constexpr int STAGES = STORE ? 3 : (EXACT ? 8 : 6);
   static constexpr int SMEM = STAGES * STAGE_BYTES + STAGING + 1024;
 };
-constexpr int TM_MAX_STAGES = 6, TM_MAX_ACC = 4;
+constexpr int TM_MAX_STAGES = 8, TM_MAX_ACC = 8;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -154,13 +156,14 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
     gemm_tma_kernel(const TmTile* __restrict__ tiles, int ntiles, const TmTerm* __restrict__ terms,
                     const CUtensorMap* __restrict__ maps, const long* __restrict__ rowmap,
                     const int2* __restrict__ cbtab, void* __restrict__ out, int out_slices, long slice_stride,
-                    int* __restrict__ err) {
+                    int* __restrict__ err, const int* __restrict__ expo) {
   using Cfg = TmCfg<MODE>;
   constexpr int S = Cfg::STAGES;
   constexpr int STAGE_BYTES = Cfg::STAGE_BYTES;
   constexpr int NACC = Cfg::NACC;
   constexpr int NMAX = Cfg::NMAX;
   constexpr bool STORE = Cfg::STORE;
+  constexpr bool EXACT = Cfg::EXACT;
   // reduce mode: a tile's products accumulate in tensor memory for at most
   // TM_SEG_KSTEPS K steps (a segment); the epilogue adds the segments in FP32
   // registers with round-to-nearest, so the rounding toward zero of the tensor-core
@@ -230,29 +233,44 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
           tm.by = __shfl_sync(0xffffffffu, mine.by, q);
           tm.k = __shfl_sync(0xffffffffu, mine.k, q);
           tm.neg = __shfl_sync(0xffffffffu, mine.neg, q);
+          tm.ea = __shfl_sync(0xffffffffu, mine.ea, q);
+          tm.eb = __shfl_sync(0xffffffffu, mine.eb, q);
           if (lane == 0) {
-            const uint32_t id = idesc_bf16(tl.n, tm.neg != 0);
-            const CUtensorMap* ma = maps + tm.amap;
-            const CUtensorMap* mb = maps + tm.bmap;
+            const uint32_t id = idesc_bf16(tl.n, (tm.neg & 1) != 0);
             const bool last_term = tb + q + 1 == tl.t1;
-            for (int k0 = 0; k0 < tm.k; k0 += TM_BOX_K, ++ks) {
-              const int s = (int)(j % S);
-              if (j >= S && !mbar_wait(&empty_b[s], (uint32_t)(((j / S) - 1) & 1), abort_flag)) {
-                ok = false;
-                break;
+            // exact mode: the term stands for all slice pairs (i, j), i + j < nsl, in
+            // order of the level l = i + j; one segment per level (slice i of a map is
+            // the map index + i).  Other modes: one pair.
+            const int nsl = EXACT ? max(1, (tm.neg >> 4) & 15) : 1;
+            for (int l = 0; l < nsl && ok; ++l)
+              for (int i = 0; i <= l && ok; ++i) {
+                const CUtensorMap* ma = maps + tm.amap + i;
+                const CUtensorMap* mb = maps + tm.bmap + (l - i);
+                for (int k0 = 0; k0 < tm.k; k0 += TM_BOX_K, ++ks) {
+                  const int s = (int)(j % S);
+                  if (j >= S && !mbar_wait(&empty_b[s], (uint32_t)(((j / S) - 1) & 1), abort_flag)) {
+                    ok = false;
+                    break;
+                  }
+                  const bool kend = k0 + TM_BOX_K >= tm.k;
+                  const bool last = last_term && kend && l + 1 == nsl && i == l;
+                  meta_id[s] = id;
+                  meta_nk[s] = min(TM_BOX_K / 16, (tm.k - k0) / 16);
+                  if (EXACT) {
+                    meta_first[s] = (i == 0 && k0 == 0) ? 1 : 0;
+                    meta_seg_end[s] = (i == l && kend) ? 1 : 0;
+                  } else {
+                    meta_first[s] = (ks % SEG == 0) ? 1 : 0;
+                    meta_seg_end[s] = (last || ks % SEG == SEG - 1) ? 1 : 0;
+                  }
+                  meta_last[s] = last ? 1 : 0;
+                  const uint32_t sa = base + s * STAGE_BYTES;
+                  mbar_arrive_expect_tx(&full_b[s], TM_A_BYTES + bbytes);
+                  tma_load_2d(sa, ma, tm.ax + k0, tm.ay, &full_b[s]);
+                  tma_load_2d(sa + TM_A_BYTES, mb, tm.bx + k0, tm.by, &full_b[s]);
+                  ++j;
+                }
               }
-              const bool last = last_term && k0 + TM_BOX_K >= tm.k;
-              meta_id[s] = id;
-              meta_nk[s] = min(TM_BOX_K / 16, (tm.k - k0) / 16);
-              meta_first[s] = (ks % SEG == 0) ? 1 : 0;
-              meta_seg_end[s] = (last || ks % SEG == SEG - 1) ? 1 : 0;
-              meta_last[s] = last ? 1 : 0;
-              const uint32_t sa = base + s * STAGE_BYTES;
-              mbar_arrive_expect_tx(&full_b[s], TM_A_BYTES + bbytes);
-              tma_load_2d(sa, ma, tm.ax + k0, tm.ay, &full_b[s]);
-              tma_load_2d(sa + TM_A_BYTES, mb, tm.bx + k0, tm.by, &full_b[s]);
-              ++j;
-            }
           }
           ok = __shfl_sync(0xffffffffu, ok, 0);
         }
@@ -422,6 +440,53 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
         mbar_arrive(&tempty_b[acc]);
         ++sg;
+      } else if constexpr (EXACT) {
+        // per segment: its exact integer sums, times 2^(expo[ea] + expo[eb] - 7 (l + 2)),
+        // added into two-float sums hi + lo (error-free additions)
+        float hi[NMAX], lo[NMAX];
+#pragma unroll
+        for (int c = 0; c < NMAX; ++c) hi[c] = lo[c] = 0.0f;
+        for (int sgi = 0, t = tl.t0; t < tl.t1 && ok; ++sgi) {
+          const int flags = terms[t].neg;
+          const int nsl = max(1, (flags >> 4) & 15);
+          const int lvl = sgi;  // segment sgi of term t: level sgi
+          const int e = expo[terms[t].ea] + expo[terms[t].eb] - TM_EXACT_BITS * (lvl + 2);
+          if (sgi + 1 == nsl) {
+            sgi = -1;
+            ++t;
+          }
+          const int acc = sg % NACC;
+          ok = mbar_wait(&tfull_b[acc], (uint32_t)((sg / NACC) & 1), abort_flag);
+          ok = __all_sync(0xffffffffu, ok);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+#pragma unroll
+          for (int cc = 0; cc < NMAX / 32; ++cc) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(acc * NMAX + cc * 32), v);
+#pragma unroll
+            for (int u = 0; u < 32; ++u) {
+              float x = ldexpf(__uint_as_float(v[u]), e);
+              if (flags & 1) x = -x;
+              const float a = hi[cc * 32 + u];
+              const float sum = __fadd_rn(a, x);
+              const float bp = __fsub_rn(sum, a);
+              const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(sum, bp)), __fsub_rn(x, bp));
+              hi[cc * 32 + u] = sum;
+              lo[cc * 32 + u] = __fadd_rn(lo[cc * 32 + u], err);
+            }
+          }
+          asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+          mbar_arrive(&tempty_b[acc]);
+          ++sg;
+        }
+        if (!ok) break;
+        if (r < tl.m_valid) {
+          double* p = reinterpret_cast<double*>(out) + tl.out_off + (long)r * tl.ldo;
+#pragma unroll
+          for (int c = 0; c < NMAX; ++c)
+            if (c < tl.nvalid) p[c] = (double)hi[c] + (double)lo[c];
+        }
       } else {
         float run[NMAX / 32][32];  // the tile's running FP32 sum (row r)
         for (int q = 0; q < tl.nseg; ++q, ++sg) {
@@ -476,7 +541,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
 template <int MODE>
 cudaError_t launch_mode(const TmTile* d_tiles, int ntiles, const TmTerm* d_terms, const CUtensorMap* d_maps,
                         const long* d_rowmap, const int2* d_cbtab, void* out, int out_slices, long slice_stride,
-                        int* d_err, cudaStream_t s) {
+                        int* d_err, cudaStream_t s, const int* d_expo) {
   static const int nsm = [] {
     if (cudaFuncSetAttribute(gemm_tma_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TmCfg<MODE>::SMEM) !=
         cudaSuccess)
@@ -490,8 +555,48 @@ cudaError_t launch_mode(const TmTile* d_tiles, int ntiles, const TmTerm* d_terms
   const int grid = ntiles < nsm ? ntiles : nsm;
   count_tc_launches(1);
   gemm_tma_kernel<MODE><<<grid, TM_THREADS, TmCfg<MODE>::SMEM, s>>>(d_tiles, ntiles, d_terms, d_maps, d_rowmap,
-                                                                     d_cbtab, out, out_slices, slice_stride, d_err);
+                                                                     d_cbtab, out, out_slices, slice_stride, d_err,
+                                                                     d_expo);
   return cudaGetLastError();
+}
+
+// exact splitting: one block of threads per job (block maximum, then the slices)
+__global__ void split_exact_kernel(const SplitJob* __restrict__ jobs, int nsl, int* __restrict__ expo_out) {
+  const SplitJob jb = jobs[blockIdx.x];
+  __shared__ double red[256];
+  __shared__ int e_sh;
+  const long n = (long)jb.rows * jb.cols;
+  double m = 0.0;
+  for (long i = threadIdx.x; i < n; i += blockDim.x) {
+    const int r = (int)(i / jb.cols), c = (int)(i % jb.cols);
+    m = fmax(m, fabs(jb.scale * jb.src[(long)r * jb.lds + c]));
+  }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    int e = 0;
+    if (red[0] > 0.0) frexp(red[0], &e);  // red[0] = f 2^e with 0.5 <= f < 1: |x| < 2^e
+    e_sh = e;
+    expo_out[jb.expo] = e;
+  }
+  __syncthreads();
+  const int e = e_sh;
+  const long nw = (long)jb.rows * jb.wcols;
+  for (long i = threadIdx.x; i < nw; i += blockDim.x) {
+    const int r = (int)(i / jb.wcols), c = (int)(i % jb.wcols);
+    double v = c < jb.cols ? ldexp(jb.scale * jb.src[(long)r * jb.lds + c], -e) : 0.0;  // |v| < 1
+    __nv_bfloat16* d = jb.trans ? jb.dst + (long)c * jb.ldd + r : jb.dst + (long)r * jb.ldd + c;
+    for (int s = 0; s < nsl; ++s) {
+      v *= (double)(1 << TM_EXACT_BITS);
+      const double q = rint(v);  // |q| <= 128: exact in BF16
+      d[s * jb.slice_stride] = __double2bfloat16(q);
+      v -= q;
+    }
+  }
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -512,18 +617,31 @@ EncodeTiledFn encoder() {
 
 }  // namespace
 
-int tma_max_n(int mode) { return mode == TM_MODE_STORE_BF16 ? 256 : 128; }
+cudaError_t launch_split_exact(const SplitJob* d_jobs, int njobs, int nsl, int* d_expo, cudaStream_t s) {
+  if (njobs <= 0) return cudaSuccess;
+  count_tc_launches(1);
+  split_exact_kernel<<<njobs, 256, 0, s>>>(d_jobs, nsl, d_expo);
+  return cudaGetLastError();
+}
+
+int tma_max_n(int mode) { return mode == TM_MODE_STORE_BF16 ? 256 : (mode == TM_MODE_EXACT_F64 ? 64 : 128); }
 
 cudaError_t launch_gemm_tma(int mode, const TmTile* d_tiles, int ntiles, const TmTerm* d_terms,
                             const CUtensorMap* d_maps, const long* d_rowmap, const int2* d_cbtab, void* out,
-                            int out_slices, long slice_stride, int* d_err, cudaStream_t s) {
+                            int out_slices, long slice_stride, int* d_err, cudaStream_t s, const int* d_expo) {
   if (ntiles <= 0) return cudaSuccess;
   if (out_slices < 1 || out_slices > 3) return cudaErrorInvalidValue;
   if (mode == TM_MODE_STORE_BF16)
     return launch_mode<TM_MODE_STORE_BF16>(d_tiles, ntiles, d_terms, d_maps, d_rowmap, d_cbtab, out, out_slices,
-                                           slice_stride, d_err, s);
+                                           slice_stride, d_err, s, nullptr);
   if (mode == TM_MODE_REDUCE_F32)
-    return launch_mode<TM_MODE_REDUCE_F32>(d_tiles, ntiles, d_terms, d_maps, d_rowmap, d_cbtab, out, 1, 0, d_err, s);
+    return launch_mode<TM_MODE_REDUCE_F32>(d_tiles, ntiles, d_terms, d_maps, d_rowmap, d_cbtab, out, 1, 0, d_err, s,
+                                           nullptr);
+  if (mode == TM_MODE_EXACT_F64) {
+    if (!d_expo) return cudaErrorInvalidValue;
+    return launch_mode<TM_MODE_EXACT_F64>(d_tiles, ntiles, d_terms, d_maps, d_rowmap, d_cbtab, out, 1, 0, d_err, s,
+                                          d_expo);
+  }
   return cudaErrorInvalidValue;
 }
 

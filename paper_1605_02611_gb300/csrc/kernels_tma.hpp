@@ -2,6 +2,7 @@
 // the single-pass sigma vector of the group-stacked layout.
 #pragma once
 #include <cuda.h>  // CUtensorMap (type only; the encoder is reached through the runtime)
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -15,10 +16,18 @@ namespace gbdmrg {
 // map's extent read as zero).  k is a multiple of 16; columns of a 64-wide box
 // past k are loaded but never multiplied.  The B map's box height must be the
 // tile's n.
+//
+// Exact mode (TM_MODE_EXACT_F64): the operands are integer slices (|x| <= 128, exact in
+// BF16) of blocks scaled by powers of two, so every product sum is an exact integer in
+// the FP32 accumulator.  A term stands for all slice pairs (i, j), i + j < nsl (neg
+// bits 4-7; slice i of map m is map m + i), taken level by level: the pairs of level
+// l = i + j form one segment, added with weight 2^(expo[ea] + expo[eb] - 7 (l + 2));
+// neg bit 0 negates.  k <= 128, so that the sums stay below 2^24.
 struct TmTerm {
   int amap, bmap;
   int ax, ay, bx, by;
   int k, neg;
+  int ea, eb;
 };
 
 // Output tile over the terms [t0, t1).  n: MMA width (multiple of 16, <= the
@@ -42,9 +51,15 @@ struct TmTile {
   long rowmap_off;
   long xbase, xrows;
   int cb0, cb1;
+  int nvalid, pad;  // exact mode: valid columns of the output block
 };
 
-constexpr int TM_MODE_STORE_BF16 = 1, TM_MODE_REDUCE_F32 = 2;
+//   exact mode (FP64): rows r < m_valid, columns c < nvalid of
+//     out + out_off + r * ldo receive the sum of the tile's segments, accumulated in
+//     two-float (hi + lo) registers and stored as FP64.
+constexpr int TM_MODE_STORE_BF16 = 1, TM_MODE_REDUCE_F32 = 2, TM_MODE_EXACT_F64 = 3;
+// bits of the slices of the exact mode
+constexpr int TM_EXACT_BITS = 7;
 // K steps (64 columns each) accumulated in tensor memory before the reduce-mode
 // epilogue takes the partial sum over
 constexpr int TM_SEG_KSTEPS = 16;
@@ -55,7 +70,23 @@ constexpr int TM_SEG_KSTEPS = 16;
 // then stops, lets its copies land and frees its tensor memory).
 cudaError_t launch_gemm_tma(int mode, const TmTile* d_tiles, int ntiles, const TmTerm* d_terms,
                             const CUtensorMap* d_maps, const long* d_rowmap, const int2* d_cbtab, void* out,
-                            int out_slices, long slice_stride, int* d_err, cudaStream_t s);
+                            int out_slices, long slice_stride, int* d_err, cudaStream_t s,
+                            const int* d_expo = nullptr);
+
+// Exact splitting of FP64 blocks for the exact mode: per job, e = the smallest
+// exponent with |scale * x| < 2^e over the block, then nsl integer slices d_s with
+// scale * x * 2^-e = sum_s d_s 2^(-7 (s + 1)) (+ remainder below 2^(-7 nsl)), each
+// stored exactly as BF16, nsl slices slice_stride elements apart; columns
+// [cols, wcols) are zero.  trans: dst[j * ldd + i] holds element (i, j) (rows of
+// the source become columns).  expo[job.expo] receives e.
+struct SplitJob {
+  const double* src;
+  __nv_bfloat16* dst;
+  long slice_stride;
+  int rows, cols, lds, ldd, wcols, trans, expo;
+  double scale;
+};
+cudaError_t launch_split_exact(const SplitJob* d_jobs, int njobs, int nsl, int* d_expo, cudaStream_t s);
 // maximum MMA width of a mode (256 for the BF16 store mode, 128 for the reduce mode)
 int tma_max_n(int mode);
 

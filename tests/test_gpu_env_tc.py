@@ -1,5 +1,8 @@
-"""Environment (renormalised-operator) updates on the tensor cores, three BF16
-slices (gbdmrg_set_env_precision(ctx, 2)), against the FP64 updates.
+"""Environment (renormalised-operator) updates on the tensor cores against the FP64
+updates: three BF16 slices (gbdmrg_set_env_precision(ctx, 2), FP32-level) and the
+exact splitting (precision 3: every block scaled by a power of two and split into
+five 7-bit integer slices, exact products and sums in the FP32 accumulators, the
+levels added in two-float registers and stored in FP64).
 
 The updates of Eqs. leftrenorm/rightrenorm (blocking, then decimation with the
 new site tensor, Eq. prenormdec) build every environment up to the two-site
@@ -69,3 +72,52 @@ def test_tc_environment_sweeps_match_fp64():
         ctx.close()
     print("tensor-core - fp64 sweep energies:", e["tc"] - e["fp64"])
     assert abs(e["tc"][-1] - e["fp64"][-1]) < 5e-5
+
+
+@pytest.mark.parametrize("K,N,two_sz,M,k", [
+    (8, 8, 0, 60, 3),
+    (9, 9, 1, 60, 4),
+    (10, 10, 0, 1000, 4),
+])
+def test_exact_tc_environments_give_the_fp64_sigma(K, N, two_sz, M, k):
+    """Five 7-bit slices carry every block to ~2^-35 of its largest element: the
+    environments agree with the FP64 ones to ~1e-10, far below the tensor-core sigma's
+    own error and the 1e-6 Eh energy target."""
+    require_gpu()
+    seed = 900 + K
+    h, eri = synth.integrals(K, seed)
+    bonds, T = synth.random_isometric_mps(K, N, two_sz, M, seed + 1, k, 0.5)
+    psi = synth.random_psi(bonds[k], bonds[k + 2], seed + 2)
+    out = {}
+    for envp in (0, 3):
+        ctx = context_with_mps(h, eri, N, two_sz, bonds, T)
+        ctx.set_env_precision(envp)
+        ctx.prepare(k)
+        out[envp] = (ctx.sigma(ctx.pack(psi))[0], ctx.expectation())
+        ctx.close()
+    err = rel_err(out[3][0], out[0][0])
+    de = abs(out[3][1] - out[0][1])
+    print(f"K={K} M={M}: sigma with exact tensor-core environments vs FP64 environments {err:.2e}; "
+          f"<H> difference {de:.2e} Eh")
+    assert err < 1e-9
+    assert de < 1e-9 * max(1.0, abs(out[0][1]))
+
+
+def test_exact_tc_environment_sweeps_match_fp64():
+    """K=12, M=64, six sweeps: exact tensor-core environment updates with the FP64 sigma
+    reach the FP64 sweep energies within 1e-9 Eh, and with the three-slice tensor-core
+    sigma within 1e-6 Eh."""
+    require_gpu()
+    K, N, M = 12, 12, 64
+    h, eri = synth.integrals(K, 1606)
+    bonds, T = synth.random_mps(K, N, 0, M, 1607)
+    e = {}
+    for label, prec, envp in (("fp64", 0, 0), ("fp64 exact env", 0, 3), ("tc exact env", 5, 3)):
+        ctx = context_with_mps(h, eri, N, 0, bonds, T)
+        ctx.set_env_precision(envp)
+        e[label] = ctx.run([M] * 6, [1e-6, 1e-7, 1e-8, 1e-9, 1e-9, 1e-9], precision=prec)["energy"]
+        ctx.close()
+    print("exact env (fp64 sigma) - fp64:", e["fp64 exact env"] - e["fp64"])
+    print("exact env (tc sigma) - fp64:", e["tc exact env"] - e["fp64"])
+    assert abs(e["fp64 exact env"][-1] - e["fp64"][-1]) < 1e-9
+    assert abs(e["tc exact env"][-1] - e["fp64"][-1]) < 1e-6
