@@ -116,8 +116,8 @@ gbdmrg_status gbdmrg_set_tma_budget(gbdmrg_ctx* ctx, int64_t megabytes);
  * block scaled by a power of two and split into five 7-bit integer slices (exact in
  * BF16), the slice products of each level summed exactly in the FP32 accumulators
  * and the levels added in two-float registers, stored in FP64 (operands carried to
- * ~2^-35 of each block's largest element); sectors above 128 states fall back to
- * the FP64 units.  EINVAL for any other value. */
+ * ~2^-35 of each block's largest element; contractions longer than 128 are cut
+ * into exact sums of at most 128 products).  EINVAL for any other value. */
 gbdmrg_status gbdmrg_set_env_precision(gbdmrg_ctx* ctx, int32_t precision);
 /* Refinement of the Davidson solve of every later tensor-core two-site step
  * (gbdmrg_step, gbdmrg_run; not part of the paper, which names no eigensolver):

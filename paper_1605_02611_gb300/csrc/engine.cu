@@ -626,18 +626,8 @@ static inline int tilde_col(const Bond& b, const OpLayout& L, int row) {
 
 static size_t budget_elems(Context& c) { return (size_t)c.chunk_budget_mb * (1u << 20) / sizeof(double); }
 
-// sectors of at most 128 states: the exact tensor-core update sums each block's K in one
-// exact FP32 accumulation
-static bool exact_env_fits(const SiteT& A) {
-  for (int d : A.L.dim)
-    if (d > 128) return false;
-  for (int d : A.R.dim)
-    if (d > 128) return false;
-  return true;
-}
-
 void env_update_left(Context& c, Tilde& lt, const SiteT& A, int site, Env& out) {
-  if (c.env_precision == 3 && exact_env_fits(A)) {
+  if (c.env_precision == 3) {
     env_update_exact(c, lt, A, site, out, true);
     return;
   }
@@ -721,7 +711,7 @@ void env_update_left(Context& c, Tilde& lt, const SiteT& A, int site, Env& out) 
 }
 
 void env_update_right(Context& c, Tilde& rt, const SiteT& B, int site, Env& out) {
-  if (c.env_precision == 3 && exact_env_fits(B)) {
+  if (c.env_precision == 3) {
     env_update_exact(c, rt, B, site, out, false);
     return;
   }
@@ -1656,6 +1646,11 @@ double two_site_step(Context& c, int k, int dir, int M, const DavidsonOpts& o, b
   if (discarded) *discarded = dw;
   c.sites[k] = std::move(A);
   c.sites[k + 1] = std::move(B);
+  // the H_eff work lists (tens of GB for tensor-core plans of large bonds) are not needed
+  // by the environment update
+  plan = SigmaPlan();
+  psi.release();
+  diag.release();
   lap(4);
   if (dir == 0) {
     env_update_left(c, lt, c.sites[k], k, c.left[k + 1]);

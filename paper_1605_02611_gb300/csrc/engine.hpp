@@ -308,7 +308,7 @@ void env_alloc(Context& c, Env& e, const Bond& b, const std::vector<BondState>& 
 // slices (engine_mixed.cu); left = true: L_{k+1} from L_k and A[k], else R_k from R_{k+1}
 void env_update_tc(Context& c, Tilde& t, const SiteT& A, int site, Env& out, bool left);
 // the same update with exactly split operands: FP64-level results on the tensor cores
-// (engine_mixed.cu); sectors of at most 128 states
+// (engine_mixed.cu)
 void env_update_exact(Context& c, Tilde& t, const SiteT& A, int site, Env& out, bool left);
 void env_update_left(Context& c, Tilde& lt, const SiteT& A, int site, Env& out);
 void env_update_right(Context& c, Tilde& rt, const SiteT& B, int site, Env& out);

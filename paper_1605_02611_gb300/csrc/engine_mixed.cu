@@ -776,8 +776,7 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
   tp->nsl = nsl;
   const int nL = Lb.nsec(), nR = Rb.nsec();
   const int nmid = (int)mid.size();
-  // slice pairs (i, j), i + j < nsl, largest products first
-  static const int PI[6] = {0, 0, 1, 0, 1, 2}, PJ[6] = {0, 1, 0, 2, 1, 0};
+  // slice pairs (i, j), i + j < nsl, per term (expanded by the kernel, level by level)
   const int npair = nsl == 1 ? 1 : nsl == 2 ? 3 : 6;
   // ---- groups of the cut: rows (ql, n1) and columns (n2, qr), blocks padded to 16
   std::map<std::pair<int, int>, int> gidx;
@@ -1170,8 +1169,8 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
               const int coff = cpos[qrp * 4 + n2p][1];
               const int cbi = cpos[qrp * 4 + n2p][2];
               const int kk = pad16(Rb.dim[qrp]);
-              for (int pr = 0; pr < npair; ++pr)
-                m1.push_back({a1map[gp][cbi] + PI[pr], nt[2] + PJ[pr], 0, (int)r0, coff, nt[0], kk, 0});
+              // one term for all slice pairs (expanded by the kernel)
+              m1.push_back({a1map[gp][cbi], nt[2], 0, (int)r0, coff, nt[0], kk, nsl << 4});
               ksum += kk * npair;
               st1_steps += (kk + 63) / 64 * npair;
             }
@@ -1249,20 +1248,9 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
             }
           }
           if (base.empty()) continue;
-          if (npair > 1) {
-            std::vector<TmTerm> all;
-            all.reserve(base.size() * npair);
-            for (const TmTerm& t : base)
-              for (int pr = 0; pr < npair; ++pr) {
-                TmTerm u = t;
-                u.amap += PI[pr];
-                u.bmap += PJ[pr];
-                all.push_back(u);
-              }
-            base.swap(all);
-          }
+          for (TmTerm& t : base) t.neg |= nsl << 4;  // all slice pairs, expanded by the kernel
           long steps = 0;
-          for (const TmTerm& t : base) steps += (t.k + 63) / 64;
+          for (const TmTerm& t : base) steps += (t.k + 63) / 64 * npair;
           for (int r0 = 0; r0 < gC[g]; r0 += 128) {
             Pending pd;
             pd.tl = TmTile{};
@@ -1283,14 +1271,14 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
       long acc = 0;
       size_t t0 = 0;
       for (size_t t = 0; t < pd.terms.size(); ++t) {
-        acc += (pd.terms[t].k + 63) / 64;
+        acc += (pd.terms[t].k + 63) / 64 * npair;
         if (acc >= target || t + 1 == pd.terms.size()) {
           TmTile tl = pd.tl;
           tl.t0 = (int)m2.size();
           long ks = 0;
           for (size_t u = t0; u <= t; ++u) {
             m2.push_back(pd.terms[u]);
-            ks += pd.terms[u].k;
+            ks += (long)pd.terms[u].k * npair;
           }
           tl.t1 = (int)m2.size();
           tl.nseg = (int)((acc + TM_SEG_KSTEPS - 1) / TM_SEG_KSTEPS);
@@ -1330,7 +1318,8 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
           throw Error(ST_ECUDA, "internal: malformed TMA tile");
         for (int t = tl.t0; t < tl.t1; ++t) {
           const TmTerm& m = mm[t];
-          if (m.amap < 0 || m.amap >= (int)minfo.size() || m.bmap < 0 || m.bmap >= (int)minfo.size() ||
+          if (((m.neg >> 4) & 15) != nsl || m.amap < 0 || m.amap + nsl > (int)minfo.size() || m.bmap < 0 ||
+              m.bmap + nsl > (int)minfo.size() ||
               minfo[m.amap].box != 128 || minfo[m.bmap].box != tl.n || m.k < 16 || m.k % 16 || m.ax % 16 ||
               m.bx % 16 || m.ax < 0 || m.bx < 0 || m.ay < 0 || m.by < 0 || m.ax + m.k > minfo[m.amap].cols + 63 ||
               m.bx + m.k > minfo[m.bmap].cols + 63)
@@ -1365,7 +1354,7 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
     }
     for (const TmTile& tl : t2) {
       long ks = 0;
-      for (int t = tl.t0; t < tl.t1; ++t) ks += (m2[t].k + 63) / 64;
+      for (int t = tl.t0; t < tl.t1; ++t) ks += (m2[t].k + 63) / 64 * npair;
       if (tl.nseg != (int)((ks + TM_SEG_KSTEPS - 1) / TM_SEG_KSTEPS))
         throw Error(ST_ECUDA, "internal: stage-2 segment count");
     }
@@ -1879,98 +1868,66 @@ void env_update_exact(Context& c, Tilde& t, const SiteT& A, int site, Env& out, 
     if (left) return Lb.find(Rb.qa[j] + st[beta].dna - LQA[n], Rb.qb[j] + st[beta].dnb - LQB[n]);
     return Rb.find(Lb.qa[j] + st[beta].dna + LQA[n], Lb.qb[j] + st[beta].dnb + LQB[n]);
   };
-  std::vector<std::vector<long>> tpos(st.size());
-  std::vector<std::vector<int>> t_cls(st.size()), t_exp(st.size());
-  std::vector<std::vector<long>> t_row(st.size());
-  WidthClasses tc_;
-  long ttot = 0;
-  for (size_t beta = 0; beta < st.size(); ++beta) {
-    tpos[beta].assign((size_t)4 * no, -1);
-    t_cls[beta].assign((size_t)4 * no, -1);
-    t_exp[beta].assign((size_t)4 * no, -1);
-    t_row[beta].assign((size_t)4 * no, -1);
-  }
-  // ---- E1 work lists (also decides which T blocks exist)
-  std::vector<TmTile> e1t;
-  std::vector<TmTerm> e1m;
-  // maps are created after all buffers exist: terms first hold (class, slice) codes
-  // amap = class index of the site classes, bmap = class index of the operator classes;
-  // box heights are the tile widths, resolved below
-  struct PendTerm {
-    int acls, bcls, ay, by, k, ea, eb, flags, si, sj, n;
+  // the source terms (site block, mirror, operator block) of the T block (beta, n, j)
+  auto sources = [&](size_t beta, int n, int j, int q, std::vector<std::array<int, 3>>& src, double& fl) {
+    src.clear();
+    for (int np = 0; np < 4; ++np) {
+      const int slot = n * 4 + np;
+      const TRef& r = t.ref[beta][slot];
+      if (!r.p) continue;
+      const OpLayout& Lay = env.cls[r.cls];
+      int qp, bl, sb;
+      if (left) {
+        qp = Lb.find(Lb.qa[q] - Lay.da, Lb.qb[q] - Lay.db);
+        if (qp < 0) continue;
+        bl = Lay.blk_of_col[qp];
+        if (bl < 0 || Lay.blocks[bl].rs != q) continue;
+        sb = A.blk(qp, np);
+        if (sb < 0 || A.blocks[sb].cs != j) continue;
+      } else {
+        qp = Rb.find(Lb.qa[j] + LQA[np], Lb.qb[j] + LQB[np]);
+        if (qp < 0) continue;
+        bl = Lay.blk_of_col[qp];
+        if (bl < 0 || Lay.blocks[bl].rs != q) continue;
+        sb = A.blk(j, np);
+        if (sb < 0 || A.blocks[sb].cs != qp) continue;
+      }
+      src.push_back({sb, mref[beta][slot], bl});
+      fl += 2.0 * ob.dim[j] * ib.dim[q] * ib.dim[qp];
+    }
   };
-  std::vector<PendTerm> e1p;
-  std::vector<long> e1_out;  // tile -> T element offset of (r0, c0), filled with tpos
-  struct E1Tile {
-    size_t beta;
-    int n, j, r0, c0, m_valid, nvalid, nw;
-    int p0, p1;
-  };
-  std::vector<E1Tile> e1x;
-  double fl = 0;
+  // chunks of bond states whose T blocks (FP64 + slices, 18 bytes per element) fit the budget
+  std::vector<size_t> tsz(st.size(), 0);
   for (size_t beta = 0; beta < st.size(); ++beta)
     for (int n = 0; n < 4; ++n)
       for (int j = 0; j < no; ++j) {
         const int q = inner_of(beta, n, j);
-        if (q < 0) continue;
-        const int rows = ob.dim[j], cols = ib.dim[q];
-        // the source terms (site block, operator block) of this T block
-        std::vector<std::array<int, 4>> src;  // (site block, mirror id, op block, slot)
-        for (int np = 0; np < 4; ++np) {
-          const int slot = n * 4 + np;
-          const TRef& r = t.ref[beta][slot];
-          if (!r.p) continue;
-          const OpLayout& Lay = env.cls[r.cls];
-          int qp, bl, sb;
-          if (left) {
-            qp = Lb.find(Lb.qa[q] - Lay.da, Lb.qb[q] - Lay.db);
-            if (qp < 0) continue;
-            bl = Lay.blk_of_col[qp];
-            if (bl < 0 || Lay.blocks[bl].rs != q) continue;
-            sb = A.blk(qp, np);
-            if (sb < 0 || A.blocks[sb].cs != j) continue;
-          } else {
-            qp = Rb.find(Lb.qa[j] + LQA[np], Lb.qb[j] + LQB[np]);
-            if (qp < 0) continue;
-            bl = Lay.blk_of_col[qp];
-            if (bl < 0 || Lay.blocks[bl].rs != q) continue;
-            sb = A.blk(j, np);
-            if (sb < 0 || A.blocks[sb].cs != qp) continue;
-          }
-          src.push_back({sb, mref[beta][slot], bl, slot});
-          fl += 2.0 * rows * cols * ib.dim[qp];
-        }
-        if (src.empty()) continue;
-        const size_t ti = (size_t)n * no + j;
-        tpos[beta][ti] = ttot;
-        ttot += (long)rows * cols;
-        t_cls[beta][ti] = tc_.of(pad16(cols));
-        t_row[beta][ti] = tc_.place(t_cls[beta][ti], rows);
-        t_exp[beta][ti] = nexpo++;
-        for (int r0 = 0; r0 < rows; r0 += 128)
-          for (int c0 = 0; c0 < cols; c0 += nmax) {
-            E1Tile x{beta, n, j, r0, c0, std::min(128, rows - r0), std::min(nmax, cols - c0), 0, (int)e1p.size(), 0};
-            x.nw = pad16(x.nvalid);
-            for (const auto& sr : src) {
-              const Block& SB = A.blocks[sr[0]];
-              const int kdim = left ? SB.rows : SB.cols;
-              e1p.push_back({s_cls[sr[0]], oc.cls[pad16(kdim)], (int)(s_row[sr[0]] + r0),
-                             (int)(m_row[sr[1]][sr[2]] + c0), pad16(kdim), s_exp[sr[0]], m_exp[sr[1]][sr[2]],
-                             NSL << 4, 0, 0, x.nw});
-            }
-            x.p1 = (int)e1p.size();
-            e1x.push_back(x);
-          }
+        if (q >= 0) tsz[beta] += (size_t)pad16(ob.dim[j]) * pad16(ib.dim[q]);
       }
-  const long ts = tc_.finish();
-  DArr<double> T64;
-  T64.alloc(std::max<long>(ttot, 1), c.stream);
-  DArr<__nv_bfloat16> tmir;
-  tmir.alloc((size_t)ts * NSL, c.stream);
-  cuda_check(cudaMemsetAsync(tmir.p, 0, tmir.n * sizeof(__nv_bfloat16), c.stream), "memset");
+  const size_t budget = std::max<size_t>(1, (size_t)c.chunk_budget_mb * (1u << 20) / (8 + 2 * NSL));
+  // split of the site and operator blocks (shared by all chunks)
+  const int nexpo_fixed = nexpo;
+  int max_texp = 0;
+  for (size_t b0 = 0, b1; b0 < st.size(); b0 = b1) {
+    size_t tot = 0;
+    for (b1 = b0; b1 < st.size() && (b1 == b0 || tot + tsz[b1] <= budget); ++b1) tot += tsz[b1];
+    int cnt = 0;
+    for (size_t beta = b0; beta < b1; ++beta)
+      for (int n = 0; n < 4; ++n)
+        for (int j = 0; j < no; ++j) cnt += inner_of(beta, n, j) >= 0;
+    max_texp = std::max(max_texp, cnt);
+  }
   DArr<int> expo;
-  expo.alloc(std::max(nexpo, 1), c.stream);
-  // ---- tensor maps: per class and slice; operator and T classes per box height
+  expo.alloc(std::max(nexpo_fixed + max_texp, 1), c.stream);
+  DArr<int> err;
+  err.alloc(1, c.stream);
+  cuda_check(cudaMemsetAsync(err.p, 0, sizeof(int), c.stream), "memset");
+  DArr<SplitJob> dj1;
+  dj1.upload(split1, c.stream);
+  for (const SplitJob& j : split1)
+    if (j.rows < 1 || j.cols < 1 || j.expo < 0 || j.expo >= nexpo_fixed) throw Error(ST_ECUDA, "internal: split job");
+  cuda_check(launch_split_exact(dj1.p, (int)split1.size(), NSL, expo.p, c.stream), "exact split");
+  // tensor maps of the site and operator classes (per slice; operators per box height)
   std::vector<CUtensorMap> maps;
   auto add_map = [&](const DArr<__nv_bfloat16>& buf, long off, long stride, long rows, int w, int box) {
     const int first = (int)maps.size();
@@ -1992,144 +1949,189 @@ void env_update_exact(Context& c, Tilde& t, const SiteT& A, int site, Env& out, 
   for (size_t k = 0; k < oc.w.size(); ++k)
     if (oc.rows[k] > 0)
       for (int h = 16; h <= nmax; h += 16) omap[k][h / 16] = add_map(omir, oc.base[k], os, oc.rows[k], oc.w[k], h);
-  std::vector<std::vector<int>> tmap(tc_.w.size(), std::vector<int>(nmax / 16 + 1, -1));
-  for (size_t k = 0; k < tc_.w.size(); ++k)
-    if (tc_.rows[k] > 0)
-      for (int h = 16; h <= nmax; h += 16) tmap[k][h / 16] = add_map(tmir, tc_.base[k], ts, tc_.rows[k], tc_.w[k], h);
-  DArr<CUtensorMap> dmaps;
-  dmaps.upload(maps, c.stream);
-  // ---- E1 tiles and terms
-  for (const E1Tile& x : e1x) {
-    TmTile tl{};
-    tl.t0 = (int)e1m.size();
-    for (int i = x.p0; i < x.p1; ++i) {
-      const PendTerm& p = e1p[(size_t)i];
-      e1m.push_back({smap[p.acls], omap[p.bcls][p.n / 16], 0, p.ay, 0, p.by, p.k, p.flags, p.ea, p.eb});
-    }
-    tl.t1 = (int)e1m.size();
-    tl.n = x.nw;
-    tl.m_valid = x.m_valid;
-    tl.nvalid = x.nvalid;
-    const int cols = ib.dim[inner_of(x.beta, x.n, x.j)];
-    tl.ldo = cols;
-    tl.out_off = tpos[x.beta][(size_t)x.n * no + x.j] + (long)x.r0 * cols + x.c0;
-    e1t.push_back(tl);
-  }
-  // ---- split of the T blocks after E1
-  std::vector<SplitJob> split2;
-  for (size_t beta = 0; beta < st.size(); ++beta)
-    for (int n = 0; n < 4; ++n)
-      for (int j = 0; j < no; ++j) {
-        const size_t ti = (size_t)n * no + j;
-        if (tpos[beta][ti] < 0) continue;
-        const int rows = ob.dim[j], cols = ib.dim[inner_of(beta, n, j)];
-        const int cl = t_cls[beta][ti], w = tc_.w[cl];
-        split2.push_back({T64.p + tpos[beta][ti], tmir.p + tc_.base[cl] + t_row[beta][ti] * w, ts, rows, cols, cols, w,
-                          pad16(cols), 0, t_exp[beta][ti], 1.0});
-      }
-  // ---- E2 tiles: every block of every new operator
-  std::vector<TmTile> e2t;
-  std::vector<TmTerm> e2m;
-  for (size_t beta = 0; beta < st.size(); ++beta) {
-    const OpLayout& Lo = out.lay((int)beta);
-    double* obase = out.op((int)beta);
-    for (const Block& B : Lo.blocks) {
-      std::vector<std::array<int, 2>> src;  // (site block, T index)
-      for (int n = 0; n < 4; ++n) {
-        int q, sb;
-        if (left) {
-          q = Lb.find(Rb.qa[B.rs] - LQA[n], Rb.qb[B.rs] - LQB[n]);
+  const size_t nfixed_maps = maps.size();
+  double fl = 0;
+  std::vector<std::array<int, 3>> src;
+  for (size_t b0 = 0, b1; b0 < st.size(); b0 = b1) {
+    size_t tot = 0;
+    for (b1 = b0; b1 < st.size() && (b1 == b0 || tot + tsz[b1] <= budget); ++b1) tot += tsz[b1];
+    maps.resize(nfixed_maps);
+    // T layout of this chunk: FP64 blocks, their slices by width class, their exponents
+    const size_t nb = b1 - b0;
+    std::vector<long> tpos(nb * 4 * no, -1), t_row(nb * 4 * no, -1);
+    std::vector<int> t_cls(nb * 4 * no, -1), t_exp(nb * 4 * no, -1);
+    WidthClasses tcw;
+    long ttot = 0;
+    int nte = nexpo_fixed;
+    struct E1 {
+      size_t tix;
+      int r0, c0, m_valid, nvalid, cols;
+      size_t s0, s1;  // range in srcs
+    };
+    std::vector<E1> e1x;
+    std::vector<std::array<int, 3>> srcs;
+    for (size_t beta = b0; beta < b1; ++beta)
+      for (int n = 0; n < 4; ++n)
+        for (int j = 0; j < no; ++j) {
+          const int q = inner_of(beta, n, j);
           if (q < 0) continue;
-          sb = A.blk(q, n);
-          if (sb < 0 || A.blocks[sb].cs != B.rs) continue;
-        } else {
-          q = Rb.find(Lb.qa[B.rs] + LQA[n], Lb.qb[B.rs] + LQB[n]);
-          if (q < 0) continue;
-          sb = A.blk(B.rs, n);
-          if (sb < 0 || A.blocks[sb].cs != q) continue;
+          sources(beta, n, j, q, src, fl);
+          if (src.empty()) continue;
+          const size_t tix = ((beta - b0) * 4 + n) * no + j;
+          const int rows = ob.dim[j], cols = ib.dim[q];
+          tpos[tix] = ttot;
+          ttot += (long)rows * cols;
+          t_cls[tix] = tcw.of(pad16(cols));
+          t_row[tix] = tcw.place(t_cls[tix], rows);
+          t_exp[tix] = nte++;
+          const size_t s0 = srcs.size();
+          srcs.insert(srcs.end(), src.begin(), src.end());
+          for (int r0 = 0; r0 < rows; r0 += 128)
+            for (int c0 = 0; c0 < cols; c0 += nmax)
+              e1x.push_back({tix, r0, c0, std::min(128, rows - r0), std::min(nmax, cols - c0), cols, s0, srcs.size()});
         }
-        const size_t ti = (size_t)n * no + B.cs;
-        if (tpos[beta][ti] < 0) continue;
-        src.push_back({sb, (int)ti});
-        fl += 2.0 * B.rows * B.cols * ib.dim[q];
+    const long ts = tcw.finish();
+    DArr<double> T64;
+    T64.alloc(std::max<long>(ttot, 1), c.stream);
+    DArr<__nv_bfloat16> tmir;
+    tmir.alloc((size_t)ts * NSL, c.stream);
+    cuda_check(cudaMemsetAsync(tmir.p, 0, tmir.n * sizeof(__nv_bfloat16), c.stream), "memset");
+    std::vector<std::vector<int>> tmap(tcw.w.size(), std::vector<int>(nmax / 16 + 1, -1));
+    for (size_t k = 0; k < tcw.w.size(); ++k)
+      if (tcw.rows[k] > 0)
+        for (int h = 16; h <= nmax; h += 16) tmap[k][h / 16] = add_map(tmir, tcw.base[k], ts, tcw.rows[k], tcw.w[k], h);
+    // E1 tiles: T block (rows, <= 64 columns) per tile; contractions cut into <= 128 columns
+    std::vector<TmTile> e1t;
+    std::vector<TmTerm> e1m;
+    for (const E1& x : e1x) {
+      TmTile tl{};
+      tl.t0 = (int)e1m.size();
+      tl.m_valid = x.m_valid;
+      tl.nvalid = x.nvalid;
+      tl.n = pad16(x.nvalid);
+      for (size_t si = x.s0; si < x.s1; ++si) {
+        const auto& sr = srcs[si];
+        const Block& SB = A.blocks[sr[0]];
+        const int kdim = left ? SB.rows : SB.cols;
+        for (int kc = 0; kc < pad16(kdim); kc += 128)
+          e1m.push_back({smap[s_cls[sr[0]]], omap[oc.cls[pad16(kdim)]][tl.n / 16], kc, (int)(s_row[sr[0]] + x.r0), kc,
+                         (int)(m_row[sr[1]][sr[2]] + x.c0), std::min(128, pad16(kdim) - kc), NSL << 4, s_exp[sr[0]],
+                         m_exp[sr[1]][sr[2]]});
       }
-      if (src.empty()) continue;
-      for (int r0 = 0; r0 < B.rows; r0 += 128)
-        for (int c0 = 0; c0 < B.cols; c0 += nmax) {
-          TmTile tl{};
-          tl.t0 = (int)e2m.size();
-          tl.m_valid = std::min(128, B.rows - r0);
-          tl.nvalid = std::min(nmax, B.cols - c0);
-          tl.n = pad16(tl.nvalid);
-          for (const auto& sr : src) {
-            const Block& SB = A.blocks[sr[0]];
-            const int kdim = left ? SB.rows : SB.cols;
-            const int tcl = t_cls[beta][(size_t)sr[1]];
-            e2m.push_back({smap[s_cls[sr[0]]], tmap[tcl][tl.n / 16], 0, (int)(s_row[sr[0]] + r0), 0,
-                           (int)(t_row[beta][(size_t)sr[1]] + c0), pad16(kdim), NSL << 4, s_exp[sr[0]],
-                           t_exp[beta][(size_t)sr[1]]});
+      tl.t1 = (int)e1m.size();
+      tl.ldo = x.cols;
+      tl.out_off = tpos[x.tix] + (long)x.r0 * x.cols + x.c0;
+      e1t.push_back(tl);
+    }
+    // split of this chunk's T blocks
+    std::vector<SplitJob> split2;
+    for (size_t tix = 0; tix < tpos.size(); ++tix) {
+      if (tpos[tix] < 0) continue;
+      const int j = (int)(tix % no), n = (int)((tix / no) % 4);
+      const size_t beta = b0 + tix / ((size_t)4 * no);
+      const int rows = ob.dim[j], cols = ib.dim[inner_of(beta, n, j)];
+      const int w = tcw.w[t_cls[tix]];
+      split2.push_back({T64.p + tpos[tix], tmir.p + tcw.base[t_cls[tix]] + t_row[tix] * w, ts, rows, cols, cols, w,
+                        pad16(cols), 0, t_exp[tix], 1.0});
+    }
+    // E2 tiles: every block of every new operator of the chunk, per output class
+    std::vector<std::vector<TmTile>> e2t(out.cls.size());
+    std::vector<TmTerm> e2m;
+    std::vector<std::array<int, 2>> s2;
+    for (size_t beta = b0; beta < b1; ++beta) {
+      const OpLayout& Lo = out.lay((int)beta);
+      const int oc_ = out.st_cls[(int)beta];
+      const long obase = (long)(out.op((int)beta) - out.data[oc_].p);
+      for (const Block& B : Lo.blocks) {
+        s2.clear();
+        for (int n = 0; n < 4; ++n) {
+          int q, sb;
+          if (left) {
+            q = Lb.find(Rb.qa[B.rs] - LQA[n], Rb.qb[B.rs] - LQB[n]);
+            if (q < 0) continue;
+            sb = A.blk(q, n);
+            if (sb < 0 || A.blocks[sb].cs != B.rs) continue;
+          } else {
+            q = Rb.find(Lb.qa[B.rs] + LQA[n], Lb.qb[B.rs] + LQB[n]);
+            if (q < 0) continue;
+            sb = A.blk(B.rs, n);
+            if (sb < 0 || A.blocks[sb].cs != q) continue;
           }
-          tl.t1 = (int)e2m.size();
-          tl.ldo = B.cols;
-          tl.out_off = (obase - out.data[out.st_cls[(int)beta]].p) + B.off + (long)r0 * B.cols + c0;
-          tl.nseg = out.st_cls[(int)beta];  // output class (host only: selects the launch)
-          e2t.push_back(tl);
+          const size_t tix = ((beta - b0) * 4 + n) * no + B.cs;
+          if (tpos[tix] < 0) continue;
+          s2.push_back({sb, (int)tix});
+          fl += 2.0 * B.rows * B.cols * ib.dim[q];
         }
+        if (s2.empty()) continue;
+        for (int r0 = 0; r0 < B.rows; r0 += 128)
+          for (int c0 = 0; c0 < B.cols; c0 += nmax) {
+            TmTile tl{};
+            tl.t0 = (int)e2m.size();
+            tl.m_valid = std::min(128, B.rows - r0);
+            tl.nvalid = std::min(nmax, B.cols - c0);
+            tl.n = pad16(tl.nvalid);
+            for (const auto& sr : s2) {
+              const Block& SB = A.blocks[sr[0]];
+              const int kdim = left ? SB.rows : SB.cols;
+              for (int kc = 0; kc < pad16(kdim); kc += 128)
+                e2m.push_back({smap[s_cls[sr[0]]], tmap[t_cls[(size_t)sr[1]]][tl.n / 16], kc, (int)(s_row[sr[0]] + r0),
+                               kc, (int)(t_row[(size_t)sr[1]] + c0), std::min(128, pad16(kdim) - kc), NSL << 4,
+                               s_exp[sr[0]], t_exp[(size_t)sr[1]]});
+            }
+            tl.t1 = (int)e2m.size();
+            tl.ldo = B.cols;
+            tl.out_off = obase + B.off + (long)r0 * B.cols + c0;
+            e2t[(size_t)oc_].push_back(tl);
+          }
+      }
     }
-  }
-  c.other_flops_total += fl;
-  // ---- bounds of every output and split job before anything runs
-  for (const SplitJob& j : split1)
-    if (j.rows < 1 || j.cols < 1 || j.expo < 0 || j.expo >= nexpo) throw Error(ST_ECUDA, "internal: split job");
-  for (const TmTile& tl : e1t)
-    if (tl.out_off < 0 || tl.out_off + (long)(tl.m_valid - 1) * tl.ldo + tl.nvalid > (long)T64.n || tl.n > nmax ||
-        tl.nvalid > tl.n || tl.t1 <= tl.t0)
-      throw Error(ST_ECUDA, "internal: exact stage-1 tile");
-  for (const TmTile& tl : e2t) {
-    const size_t cap = out.data[tl.nseg].n;
-    if (tl.out_off < 0 || (size_t)(tl.out_off + (long)(tl.m_valid - 1) * tl.ldo + tl.nvalid) > cap || tl.n > nmax ||
-        tl.nvalid > tl.n || tl.t1 <= tl.t0)
-      throw Error(ST_ECUDA, "internal: exact stage-2 tile");
-  }
-  auto check_m = [&](const std::vector<TmTerm>& mm) {
-    for (const TmTerm& m : mm)
-      if (m.amap < 0 || m.amap + NSL > (int)maps.size() || m.bmap < 0 || m.bmap + NSL > (int)maps.size() ||
-          m.k < 16 || m.k % 16 || m.k > 128 || m.ea < 0 || m.ea >= nexpo || m.eb < 0 || m.eb >= nexpo ||
-          ((m.neg >> 4) & 15) != NSL)
-        throw Error(ST_ECUDA, "internal: exact term");
-  };
-  check_m(e1m);
-  check_m(e2m);
-  // ---- run: split, E1, split T, E2 (one launch per output class of the new operators)
-  DArr<int> err;
-  err.alloc(1, c.stream);
-  cuda_check(cudaMemsetAsync(err.p, 0, sizeof(int), c.stream), "memset");
-  DArr<SplitJob> dj1, dj2;
-  dj1.upload(split1, c.stream);
-  cuda_check(launch_split_exact(dj1.p, (int)split1.size(), NSL, expo.p, c.stream), "exact split");
-  DArr<TmTile> d1t;
-  DArr<TmTerm> d1m;
-  d1t.upload(e1t, c.stream);
-  d1m.upload(e1m, c.stream);
-  cuda_check(launch_gemm_tma(TM_MODE_EXACT_F64, d1t.p, (int)e1t.size(), d1m.p, dmaps.p, nullptr, nullptr, T64.p, 1, 0,
-                             err.p, c.stream, expo.p),
-             "exact stage 1");
-  dj2.upload(split2, c.stream);
-  cuda_check(launch_split_exact(dj2.p, (int)split2.size(), NSL, expo.p, c.stream), "exact split of T");
-  DArr<TmTerm> d2m;
-  d2m.upload(e2m, c.stream);
-  for (size_t ci = 0; ci < out.cls.size(); ++ci) {
-    std::vector<TmTile> part;
-    for (const TmTile& tl : e2t)
-      if (tl.nseg == (int)ci) part.push_back(tl);
-    if (part.empty()) continue;
-    DArr<TmTile> d2t;
-    d2t.upload(part, c.stream);
-    cuda_check(launch_gemm_tma(TM_MODE_EXACT_F64, d2t.p, (int)part.size(), d2m.p, dmaps.p, nullptr, nullptr,
-                               out.data[ci].p, 1, 0, err.p, c.stream, expo.p),
-               "exact stage 2");
+    // bounds of every output, term and split job before anything runs
+    for (const TmTile& tl : e1t)
+      if (tl.out_off < 0 || tl.out_off + (long)(tl.m_valid - 1) * tl.ldo + tl.nvalid > (long)T64.n || tl.n > nmax ||
+          tl.nvalid > tl.n || tl.t1 <= tl.t0)
+        throw Error(ST_ECUDA, "internal: exact stage-1 tile");
+    for (size_t ci = 0; ci < e2t.size(); ++ci)
+      for (const TmTile& tl : e2t[ci])
+        if (tl.out_off < 0 || (size_t)(tl.out_off + (long)(tl.m_valid - 1) * tl.ldo + tl.nvalid) > out.data[ci].n ||
+            tl.n > nmax || tl.nvalid > tl.n || tl.t1 <= tl.t0)
+          throw Error(ST_ECUDA, "internal: exact stage-2 tile");
+    auto check_m = [&](const std::vector<TmTerm>& mm) {
+      for (const TmTerm& m : mm)
+        if (m.amap < 0 || m.amap + NSL > (int)maps.size() || m.bmap < 0 || m.bmap + NSL > (int)maps.size() ||
+            m.k < 16 || m.k % 16 || m.k > 128 || m.ax % 16 || m.ea < 0 || m.ea >= nte || m.eb < 0 || m.eb >= nte ||
+            ((m.neg >> 4) & 15) != NSL)
+          throw Error(ST_ECUDA, "internal: exact term");
+    };
+    check_m(e1m);
+    check_m(e2m);
+    for (const SplitJob& j : split2)
+      if (j.rows < 1 || j.cols < 1 || j.expo < nexpo_fixed || j.expo >= nte) throw Error(ST_ECUDA, "internal: split job");
+    // run: E1, split T, E2 (one launch per output class of the new operators)
+    DArr<CUtensorMap> dmaps;
+    dmaps.upload(maps, c.stream);
+    DArr<TmTile> d1t;
+    DArr<TmTerm> d1m, d2m;
+    d1t.upload(e1t, c.stream);
+    d1m.upload(e1m, c.stream);
+    cuda_check(launch_gemm_tma(TM_MODE_EXACT_F64, d1t.p, (int)e1t.size(), d1m.p, dmaps.p, nullptr, nullptr, T64.p, 1, 0,
+                               err.p, c.stream, expo.p),
+               "exact stage 1");
+    DArr<SplitJob> dj2;
+    dj2.upload(split2, c.stream);
+    cuda_check(launch_split_exact(dj2.p, (int)split2.size(), NSL, expo.p, c.stream), "exact split of T");
+    d2m.upload(e2m, c.stream);
+    std::vector<DArr<TmTile>> d2t(out.cls.size());
+    for (size_t ci = 0; ci < out.cls.size(); ++ci) {
+      if (e2t[ci].empty()) continue;
+      d2t[ci].upload(e2t[ci], c.stream);
+      cuda_check(launch_gemm_tma(TM_MODE_EXACT_F64, d2t[ci].p, (int)e2t[ci].size(), d2m.p, dmaps.p, nullptr, nullptr,
+                                 out.data[ci].p, 1, 0, err.p, c.stream, expo.p),
+                 "exact stage 2");
+    }
+    // the host lists and the chunk's buffers must outlive the launches
     cuda_check(cudaStreamSynchronize(c.stream), "sync");
   }
+  c.other_flops_total += fl;
   int h = 0;
   cuda_check(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "d2h");
   cuda_check(cudaStreamSynchronize(c.stream), "sync");

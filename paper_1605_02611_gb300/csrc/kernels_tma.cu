@@ -238,10 +238,10 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
           if (lane == 0) {
             const uint32_t id = idesc_bf16(tl.n, (tm.neg & 1) != 0);
             const bool last_term = tb + q + 1 == tl.t1;
-            // exact mode: the term stands for all slice pairs (i, j), i + j < nsl, in
-            // order of the level l = i + j; one segment per level (slice i of a map is
-            // the map index + i).  Other modes: one pair.
-            const int nsl = EXACT ? max(1, (tm.neg >> 4) & 15) : 1;
+            // the term stands for all slice pairs (i, j), i + j < nsl, in order of the
+            // level l = i + j (slice i of a map is the map index + i); exact mode: one
+            // segment per level
+            const int nsl = max(1, (tm.neg >> 4) & 15);
             for (int l = 0; l < nsl && ok; ++l)
               for (int i = 0; i <= l && ok; ++i) {
                 const CUtensorMap* ma = maps + tm.amap + i;

@@ -9,7 +9,7 @@
 
 namespace gbdmrg {
 
-// One term of an output tile: C[128 x n] (-)= A[128 x k] B[n x k]^T, where A is the
+// One term of an output tile: C[128 x n] (-)= A[128 x k] B[n x k]^T (neg bit 0), where A is the
 // box of rows [ay, ay + 128) and columns [ax, ax + k) of tensor map amap and B the
 // rows [by, by + n) and columns [bx, bx + k) of tensor map bmap (both BF16,
 // row-major, 128-byte swizzled boxes of 64 columns; rows or columns outside a

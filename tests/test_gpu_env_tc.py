@@ -74,19 +74,22 @@ def test_tc_environment_sweeps_match_fp64():
     assert abs(e["tc"][-1] - e["fp64"][-1]) < 5e-5
 
 
-@pytest.mark.parametrize("K,N,two_sz,M,k", [
-    (8, 8, 0, 60, 3),
-    (9, 9, 1, 60, 4),
-    (10, 10, 0, 1000, 4),
+@pytest.mark.parametrize("K,N,two_sz,M,k,spread", [
+    (8, 8, 0, 60, 3, 0.5),
+    (9, 9, 1, 60, 4, 0.5),
+    (10, 10, 0, 1000, 4, 0.5),
+    (12, 12, 0, 1000, 3, 4.0),   # a sector of 400 states at bond 6: contractions cut into 128-column sums
 ])
-def test_exact_tc_environments_give_the_fp64_sigma(K, N, two_sz, M, k):
+def test_exact_tc_environments_give_the_fp64_sigma(K, N, two_sz, M, k, spread):
     """Five 7-bit slices carry every block to ~2^-35 of its largest element: the
     environments agree with the FP64 ones to ~1e-10, far below the tensor-core sigma's
     own error and the 1e-6 Eh energy target."""
     require_gpu()
     seed = 900 + K
     h, eri = synth.integrals(K, seed)
-    bonds, T = synth.random_isometric_mps(K, N, two_sz, M, seed + 1, k, 0.5)
+    bonds, T = synth.random_isometric_mps(K, N, two_sz, M, seed + 1, k, spread)
+    if spread > 1:
+        assert max(bonds[6].dim) > 128
     psi = synth.random_psi(bonds[k], bonds[k + 2], seed + 2)
     out = {}
     for envp in (0, 3):
