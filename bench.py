@@ -6,7 +6,9 @@ W-contracted operators, diagonal of H_eff, Davidson with a fixed iteration
 budget (16 by default, about what sweeps take per site; each iteration one
 H_eff.psi), decimation to M states and the environment update of the new bond.
 The default arithmetic is the one that meets the metric's accuracy: H_eff.psi on
-the tensor cores with three BF16 slices on the TMA-staged work lists (precision 5).  Inputs (integrals, a random QN-block MPS
+the tensor cores with three BF16 slices on the TMA-staged work lists (precision 5)
+and the environment update on the tensor cores with exactly split operands
+(environment precision 3, FP64-level results).  Inputs (integrals, a random QN-block MPS
 with bond dimension 2000 and its environments, tens of GB) are built before
 the timed region and stay resident in HBM; they are far larger than L2, so no
 explicit flush is needed.
@@ -183,7 +185,8 @@ def workload_name(args, sigma_calls_per_step=None):
     K = w["K"]
     k = K // 2 - 1
     ref = f", refinement by precision {args.refine} ({args.refine_iters} of the iterations)" if args.refine >= 0 else ""
-    env = ", tensor-core environment update" if args.env_precision else ""
+    env = {0: ", FP64 environment update", 2: ", tensor-core environment update (three BF16 slices)",
+           3: ", tensor-core environment update (exactly split operands)"}[args.env_precision]
     meas = f", {sigma_calls_per_step:.1f} sigma calls/step measured" if sigma_calls_per_step is not None else ""
     return (f"{args.workload}: K={K} N={w['N']} 2Sz={w['two_sz']} M={w['M']}, two-site step at sites "
             f"({k},{k + 1}), Davidson budget {args.dav_iters} iterations/step{meas}, precision {args.precision}"
@@ -310,12 +313,16 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    if args.profiler_range:
+        torch.cuda.cudart().cudaProfilerStart()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    if args.profiler_range:
+        torch.cuda.cudart().cudaProfilerStop()
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
@@ -611,7 +618,7 @@ def main():
     ap.add_argument("--fp64-w-sums", action="store_true",
                     help="form every W-contracted sum on the FP64 units (default: large sums that feed only "
                          "the tensor-core sigma run on the tensor cores)")
-    ap.add_argument("--env-precision", type=int, default=0, choices=[0, 2, 3],
+    ap.add_argument("--env-precision", type=int, default=3, choices=[0, 2, 3],
                     help="environment updates: 0 FP64 units, 2 tensor cores with three BF16 slices, "
                          "3 tensor cores with exactly split operands")
     ap.add_argument("--refine", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4, 5, 6],
@@ -620,6 +627,8 @@ def main():
                     help="Davidson iterations of the step budget given to the refinement phase")
     ap.add_argument("--autotune", action="store_true",
                     help="with --batched: choose the split-K granularity of the fused work lists by timing")
+    ap.add_argument("--profiler-range", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--profile-sigma", type=int, default=0,
                     help="after setup run this many H_eff.psi calls only (for ncu captures) and exit")
     args = ap.parse_args()

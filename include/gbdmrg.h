@@ -113,10 +113,10 @@ gbdmrg_status gbdmrg_set_tma_budget(gbdmrg_ctx* ctx, int64_t megabytes);
  * three BF16 slices (six products, FP32 accumulation, intermediates as three
  * BF16 slices of the FP32 results), the new operators stored in FP64 (FP32-level
  * accuracy); 3 = both GEMMs on the tensor cores with exactly split operands: every
- * block scaled by a power of two and split into five 7-bit integer slices (exact in
+ * block scaled by a power of two and split into six 7-bit integer slices (exact in
  * BF16), the slice products of each level summed exactly in the FP32 accumulators
  * and the levels added in two-float registers, stored in FP64 (operands carried to
- * ~2^-35 of each block's largest element; contractions longer than 128 are cut
+ * ~2^-42 of each block's largest element; contractions longer than 128 are cut
  * into exact sums of at most 128 products).  EINVAL for any other value. */
 gbdmrg_status gbdmrg_set_env_precision(gbdmrg_ctx* ctx, int32_t precision);
 /* Refinement of the Davidson solve of every later tensor-core two-site step

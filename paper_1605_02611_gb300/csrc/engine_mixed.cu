@@ -1734,12 +1734,12 @@ void env_update_tc(Context& c, Tilde& t, const SiteT& A, int site, Env& out, boo
 // the FP32 accumulators; pairs of slices of one level i + j share a weight and accumulate
 // together (still exact), and the levels are added with their powers of two in two-float
 // (hi + lo) registers and stored in FP64.  Dropped pairs (i + j >= slices) and the
-// remainder of the splitting are below 2^-35 of each block's largest element.
+// remainder of the splitting are below 2^-42 of each block's largest element.
 //   left : E1  T^T_beta[n1][j, ql] = sum_{n1'} At^{n1'}[j, ql'] Lt^{n1 n1'}[ql, ql']
 //          E2  L'[qa, qa']        = sum_{n1} At^{n1}[qa, ql] T^T_beta[n1][qa', ql]
 //   right: E1  T_beta[n2][j, qr]  = sum_{n2'} B^{n2'}[j, qr'] Rt^{n2 n2'}[qr, qr']
 //          E2  R'[qb, qb']        = sum_{n2} B^{n2}[qb, qr] T_beta[n2][qb', qr]
-constexpr int TM_EXACT_SLICES = 5;
+constexpr int TM_EXACT_SLICES = 6;
 
 namespace {
 

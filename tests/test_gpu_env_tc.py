@@ -1,7 +1,7 @@
 """Environment (renormalised-operator) updates on the tensor cores against the FP64
 updates: three BF16 slices (gbdmrg_set_env_precision(ctx, 2), FP32-level) and the
 exact splitting (precision 3: every block scaled by a power of two and split into
-five 7-bit integer slices, exact products and sums in the FP32 accumulators, the
+six 7-bit integer slices, exact products and sums in the FP32 accumulators, the
 levels added in two-float registers and stored in FP64).
 
 The updates of Eqs. leftrenorm/rightrenorm (blocking, then decimation with the
@@ -81,7 +81,7 @@ def test_tc_environment_sweeps_match_fp64():
     (12, 12, 0, 1000, 3, 4.0),   # a sector of 400 states at bond 6: contractions cut into 128-column sums
 ])
 def test_exact_tc_environments_give_the_fp64_sigma(K, N, two_sz, M, k, spread):
-    """Five 7-bit slices carry every block to ~2^-35 of its largest element: the
+    """Six 7-bit slices carry every block to ~2^-42 of its largest element: the
     environments agree with the FP64 ones to ~1e-10, far below the tensor-core sigma's
     own error and the 1e-6 Eh energy target."""
     require_gpu()
