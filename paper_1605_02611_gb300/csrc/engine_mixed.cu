@@ -44,18 +44,37 @@ struct ConvJob {
   int wcols;
 };
 
+// Elements of a job spread over the grid (32-bit division when the job has fewer than
+// 2^31 elements, as every job of these layouts has).  The FP64 value y is split once into
+// a + lo (two FP32 values, a = fl32(y), lo = fl32(y - a)), and the BF16 slices are taken
+// from a by exact FP32 subtractions, lo entering the last slice: two FP64 operations per
+// element instead of several per slice (the FP64 units of this GPU issue at a small
+// fraction of the FP32 rate).  The slices carry y to ~2^-25 relative for three slices,
+// as a direct FP64 splitting does.
+__device__ __forceinline__ void conv_element(const ConvJob& jb, long i, int j) {
+  const double y = j < jb.cols ? jb.scale * jb.src[i * jb.lds + j] : 0.0;
+  float a = __double2float_rn(y);
+  const float lo = jb.nsl > 1 ? __double2float_rn(y - (double)a) : 0.0f;
+  __nv_bfloat16* d = jb.dst + i * jb.ldd + j;
+  for (int sl = 0; sl < jb.nsl; ++sl) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(sl + 1 == jb.nsl ? a + lo : a);
+    d[(long)sl * jb.slice_stride] = h;
+    a -= __bfloat162float(h);
+  }
+}
+
 __global__ void conv_kernel(const ConvJob* __restrict__ jobs) {
   const ConvJob jb = jobs[blockIdx.y];
   const long n = (long)jb.rows * jb.wcols;
-  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(e / jb.wcols), j = (int)(e % jb.wcols);
-    double v = j < jb.cols ? jb.scale * jb.src[(long)i * jb.lds + j] : 0.0;
-    __nv_bfloat16* d = jb.dst + (long)i * jb.ldd + j;
-    for (int s = 0; s < jb.nsl; ++s) {
-      const __nv_bfloat16 h = __double2bfloat16(v);
-      d[s * jb.slice_stride] = h;
-      v -= (double)__bfloat162float(h);
+  if (n < (1L << 31)) {
+    const unsigned w = (unsigned)jb.wcols;
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < (unsigned)n; e += gridDim.x * blockDim.x) {
+      const unsigned i = e / w;
+      conv_element(jb, (long)i, (int)(e - i * w));
     }
+  } else {
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+      conv_element(jb, e / jb.wcols, (int)(e % jb.wcols));
   }
 }
 

@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
   // TM_SEG_KSTEPS K steps (a segment); the epilogue adds the segments in FP32
   // registers with round-to-nearest, so the rounding toward zero of the tensor-core
   // accumulation acts on short sums only
-  constexpr long SEG = STORE ? (1L << 40) : TM_SEG_KSTEPS;
+  constexpr int SEG = STORE ? (1 << 30) : TM_SEG_KSTEPS;
   extern __shared__ uint8_t dsm[];
   __shared__ __align__(8) uint64_t full_b[TM_MAX_STAGES], empty_b[TM_MAX_STAGES], tfull_b[TM_MAX_ACC],
       tempty_b[TM_MAX_ACC];
@@ -176,9 +176,9 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
   __shared__ int abort_sh;
   // per stage: instruction descriptor, K=16 steps, first K step of a segment, last K
   // step of a segment, last K step of the tile
-  __shared__ uint32_t meta_id[TM_MAX_STAGES];
-  __shared__ int meta_nk[TM_MAX_STAGES], meta_first[TM_MAX_STAGES], meta_seg_end[TM_MAX_STAGES],
-      meta_last[TM_MAX_STAGES];
+  // (packed into one 64-bit word: low half the instruction descriptor, high half the
+  // K=16 steps in bits 0-2 and the flags first / segment end / last in bits 3-5)
+  __shared__ uint64_t meta[TM_MAX_STAGES];
   const uint32_t base = (smem_u32(dsm) + 1023u) & ~1023u;
   uint8_t* const base_ptr = dsm + (base - smem_u32(dsm));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -208,20 +208,42 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
 
   if (warp == 0) {
     // ---------------- TMA producer: the warp loads the term descriptors of a tile 32 at
-    // a time (one per lane) and prefetches their tensor maps; lane 0 issues the copies
+    // a time (one per lane) and prefetches their tensor maps (every slice's); lane 0
+    // issues the copies.  Descriptor loads run ahead of their use: the tile after next
+    // and the next tile's first 32 terms while a tile is issued, the next 32 terms of a
+    // tile while the current 32 are issued.
     long j = 0;  // K steps issued (lane 0)
+    int st = 0;          // stage of the next K step (j % S)
+    uint32_t par = 0;    // its round's parity ((j / S) & 1)
+    bool wrapped = false;  // j >= S
     bool ok = true;
-    for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
-      const TmTile tl = tiles[ti];
+    const int G = (int)gridDim.x;
+    TmTile cur{}, nxt{};
+    TmTerm pre{};  // this lane's term of the current tile's first batch
+    if ((int)blockIdx.x < ntiles) {
+      cur = tiles[blockIdx.x];
+      if (lane < min(32, cur.t1 - cur.t0)) pre = terms[cur.t0 + lane];
+    }
+    if ((int)blockIdx.x + G < ntiles) nxt = tiles[blockIdx.x + G];
+    for (int ti = blockIdx.x; ti < ntiles && ok; ti += G) {
+      const TmTile tl = cur;
+      TmTile nn{};
+      if (ti + 2 * G < ntiles) nn = tiles[ti + 2 * G];
+      TmTerm pre_next{};
+      if (ti + G < ntiles && lane < min(32, nxt.t1 - nxt.t0)) pre_next = terms[nxt.t0 + lane];
       const uint32_t bbytes = (uint32_t)tl.n * TM_BOX_K * 2;
-      long ks = 0;  // K steps of this tile so far
+      int seg_pos = 0;  // K steps of the current segment so far
+      TmTerm mine = pre, ahead{};
       for (int tb = tl.t0; tb < tl.t1 && ok; tb += 32) {
         const int cnt = min(32, tl.t1 - tb);
-        TmTerm mine{};
+        if (tb != tl.t0) mine = ahead;
+        if (tb + 32 < tl.t1 && lane < min(32, tl.t1 - tb - 32)) ahead = terms[tb + 32 + lane];
         if (lane < cnt) {
-          mine = terms[tb + lane];
-          asm volatile("prefetch.tensormap [%0];\n" ::"l"(maps + mine.amap) : "memory");
-          asm volatile("prefetch.tensormap [%0];\n" ::"l"(maps + mine.bmap) : "memory");
+          const int nslp = max(1, (mine.neg >> 4) & 15);
+          for (int i = 0; i < nslp; ++i) {
+            asm volatile("prefetch.tensormap [%0];\n" ::"l"(maps + mine.amap + i) : "memory");
+            asm volatile("prefetch.tensormap [%0];\n" ::"l"(maps + mine.bmap + i) : "memory");
+          }
         }
         for (int q = 0; q < cnt && ok; ++q) {
           TmTerm tm;
@@ -246,35 +268,43 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
               for (int i = 0; i <= l && ok; ++i) {
                 const CUtensorMap* ma = maps + tm.amap + i;
                 const CUtensorMap* mb = maps + tm.bmap + (l - i);
-                for (int k0 = 0; k0 < tm.k; k0 += TM_BOX_K, ++ks) {
-                  const int s = (int)(j % S);
-                  if (j >= S && !mbar_wait(&empty_b[s], (uint32_t)(((j / S) - 1) & 1), abort_flag)) {
+                for (int k0 = 0; k0 < tm.k; k0 += TM_BOX_K) {
+                  if (wrapped && !mbar_wait(&empty_b[st], par ^ 1u, abort_flag)) {
                     ok = false;
                     break;
                   }
                   const bool kend = k0 + TM_BOX_K >= tm.k;
                   const bool last = last_term && kend && l + 1 == nsl && i == l;
-                  meta_id[s] = id;
-                  meta_nk[s] = min(TM_BOX_K / 16, (tm.k - k0) / 16);
+                  uint32_t fl = (uint32_t)min(TM_BOX_K / 16, (tm.k - k0) / 16);
                   if (EXACT) {
-                    meta_first[s] = (i == 0 && k0 == 0) ? 1 : 0;
-                    meta_seg_end[s] = (i == l && kend) ? 1 : 0;
+                    fl |= (i == 0 && k0 == 0) ? 8u : 0u;
+                    fl |= (i == l && kend) ? 16u : 0u;
                   } else {
-                    meta_first[s] = (ks % SEG == 0) ? 1 : 0;
-                    meta_seg_end[s] = (last || ks % SEG == SEG - 1) ? 1 : 0;
+                    fl |= seg_pos == 0 ? 8u : 0u;
+                    fl |= (last || seg_pos == SEG - 1) ? 16u : 0u;
                   }
-                  meta_last[s] = last ? 1 : 0;
-                  const uint32_t sa = base + s * STAGE_BYTES;
-                  mbar_arrive_expect_tx(&full_b[s], TM_A_BYTES + bbytes);
-                  tma_load_2d(sa, ma, tm.ax + k0, tm.ay, &full_b[s]);
-                  tma_load_2d(sa + TM_A_BYTES, mb, tm.bx + k0, tm.by, &full_b[s]);
+                  fl |= last ? 32u : 0u;
+                  meta[st] = (uint64_t)id | ((uint64_t)fl << 32);
+                  const uint32_t sa = base + st * STAGE_BYTES;
+                  mbar_arrive_expect_tx(&full_b[st], TM_A_BYTES + bbytes);
+                  tma_load_2d(sa, ma, tm.ax + k0, tm.ay, &full_b[st]);
+                  tma_load_2d(sa + TM_A_BYTES, mb, tm.bx + k0, tm.by, &full_b[st]);
                   ++j;
+                  if (++seg_pos == SEG) seg_pos = 0;
+                  if (++st == S) {
+                    st = 0;
+                    par ^= 1u;
+                    wrapped = true;
+                  }
                 }
               }
           }
           ok = __shfl_sync(0xffffffffu, ok, 0);
         }
       }
+      cur = nxt;
+      nxt = nn;
+      pre = pre_next;
     }
     if (lane == 0) {
       // every issued copy must land before the CTA may exit: the last (up to S)
@@ -288,9 +318,14 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer (one thread): one accumulator per segment
     if (lane == 0) {
-      long j = 0;
+      int st = 0;            // stage of the next K step
+      uint32_t par = 0;      // its round's parity
       int sg = 0;  // segments issued
       bool ok = true;
+      // shared-memory descriptors of stage 0's operands; stage s and K=16 step kk add
+      // (s * STAGE_BYTES + kk * 32) / 16 to the 14-bit address field (no carry: shared
+      // addresses stay below 256 KB)
+      const uint64_t ad0 = sdesc(base), bd0 = sdesc(base + TM_A_BYTES);
       for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
         bool tile_done = false;
         while (!tile_done && ok) {
@@ -302,28 +337,31 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
           const uint32_t dacc = tmem + (uint32_t)(acc * NMAX);
           for (;;) {
-            const int s = (int)(j % S);
-            if (!mbar_wait(&full_b[s], (uint32_t)((j / S) & 1), abort_flag)) {
+            if (!mbar_wait(&full_b[st], par, abort_flag)) {
               ok = false;
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-            const uint32_t id = meta_id[s];
-            const int nk = meta_nk[s], first = meta_first[s], seg_end = meta_seg_end[s], last = meta_last[s];
-            const uint32_t sa = base + s * STAGE_BYTES;
+            const uint64_t mw = meta[st];
+            const uint32_t id = (uint32_t)mw, fl = (uint32_t)(mw >> 32);
+            const int nk = (int)(fl & 7u);
+            const uint64_t off = (uint64_t)((st * STAGE_BYTES) >> 4);
             for (int kk = 0; kk < nk; ++kk) {
-              const uint64_t ad = sdesc(sa + kk * 32), bd = sdesc(sa + TM_A_BYTES + kk * 32);
-              const uint32_t accum = (first && kk == 0) ? 0u : 1u;
+              const uint64_t ad = ad0 + off + (uint64_t)(kk * 2), bd = bd0 + off + (uint64_t)(kk * 2);
+              const uint32_t accum = ((fl & 8u) && kk == 0) ? 0u : 1u;
               asm volatile(
                   "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                   " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dacc),
                   "l"(ad), "l"(bd), "r"(id), "r"(accum));
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                smem_u32(&empty_b[s])));
-            ++j;
-            if (seg_end) {
-              tile_done = last != 0;
+                smem_u32(&empty_b[st])));
+            if (++st == S) {
+              st = 0;
+              par ^= 1u;
+            }
+            if (fl & 16u) {
+              tile_done = (fl & 32u) != 0;
               break;
             }
           }
@@ -342,14 +380,15 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
         reinterpret_cast<__nv_bfloat16*>(base_ptr + S * STAGE_BYTES) + (STORE ? r * Cfg::STAGE_LD : 0);
     int sg = 0;
     bool ok = true;
+    // the next tile's descriptor is loaded one tile ahead; in store mode the row map and
+    // column blocks of a tile are read before its accumulator is waited for
+    TmTile tl_next{};
+    if ((int)blockIdx.x < ntiles) tl_next = tiles[blockIdx.x];
     for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
-      const TmTile tl = tiles[ti];
+      const TmTile tl = tl_next;
+      if (ti + (int)gridDim.x < ntiles) tl_next = tiles[ti + gridDim.x];
       if constexpr (STORE) {
         const int acc = sg % NACC;
-        ok = mbar_wait(&tfull_b[acc], (uint32_t)((sg / NACC) & 1), abort_flag);
-        ok = __all_sync(0xffffffffu, ok);
-        if (!ok) break;
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
         const long row_own = rowmap[tl.rowmap_off + r];
         // this lane's 8-column chunk of every row: its column block, base and width
         long lane_base = -1;
@@ -364,6 +403,10 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
             }
           }
         }
+        ok = mbar_wait(&tfull_b[acc], (uint32_t)((sg / NACC) & 1), abort_flag);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
         __nv_bfloat16* const wrows =
             reinterpret_cast<__nv_bfloat16*>(base_ptr + S * STAGE_BYTES) + sub * 32 * Cfg::STAGE_LD;
         if (out_slices == 1) {
@@ -396,45 +439,39 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
           __syncwarp();
         } else {
           // two or three slices x = s0 + s1 + s2 from one read of each value, stored
-          // directly: per 8 columns one 16-byte store per slice into this row (the
-          // tensor-memory loads are warp-wide, the stores only for rows that exist)
+          // directly: per 8 columns one 16-byte store per slice into this row.  The
+          // tensor-memory loads (32 columns, one wait) are warp-wide, the stores only for
+          // rows that exist; the column block of 8-column chunk c is lane c's (above)
 #pragma unroll 1
-          for (int c0 = 0; c0 < tl.n; c0 += 8) {
-            uint32_t v[8];
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                           "=r"(v[7])
-                         : "r"(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(acc * NMAX + c0)));
-            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-            uint32_t w[3][4];
+          for (int c0 = 0; c0 < tl.n; c0 += 32) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(acc * NMAX + c0), v);
 #pragma unroll
-            for (int u = 0; u < 8; u += 2) {
-              float a = __uint_as_float(v[u]), b = __uint_as_float(v[u + 1]);
+            for (int u8 = 0; u8 < 32; u8 += 8) {
+              const int ch = (c0 + u8) >> 3;  // < NMAX / 8 <= 32
+              const long cb_base = __shfl_sync(0xffffffffu, lane_base, ch);
+              const int cb_w = __shfl_sync(0xffffffffu, lane_w, ch);
+              if (c0 + u8 >= tl.n) break;
+              uint32_t w[3][4];
 #pragma unroll
-              for (int sl = 0; sl < 3; ++sl) {
-                const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-                w[sl][u / 2] = *reinterpret_cast<const uint32_t*>(&h);
-                a -= __low2float(h);
-                b -= __high2float(h);
+              for (int u = 0; u < 8; u += 2) {
+                float a = __uint_as_float(v[u8 + u]), b = __uint_as_float(v[u8 + u + 1]);
+#pragma unroll
+                for (int sl = 0; sl < 3; ++sl) {
+                  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+                  w[sl][u / 2] = *reinterpret_cast<const uint32_t*>(&h);
+                  a -= __low2float(h);
+                  b -= __high2float(h);
+                }
               }
-            }
-            // the column block of these 8 columns
-            const long col = tl.out_off + c0;
-            long cb_base = -1;
-            int cb_w = 0;
-            for (int e = tl.cb0; e < tl.cb1; ++e) {
-              const int2 cb = cbtab[e];
-              if (col >= cb.x && col < cb.x + cb.y) {
-                cb_base = tl.xbase + tl.xrows * cb.x + (col - cb.x);
-                cb_w = cb.y;
-              }
-            }
-            if (cb_base < 0 || row_own < 0) continue;
-            __nv_bfloat16* g = reinterpret_cast<__nv_bfloat16*>(out) + cb_base + row_own * cb_w;
+              if (cb_base < 0 || row_own < 0) continue;
+              __nv_bfloat16* g = reinterpret_cast<__nv_bfloat16*>(out) + cb_base + row_own * cb_w;
 #pragma unroll
-            for (int sl = 0; sl < 3; ++sl)
-              if (sl < out_slices)
-                *reinterpret_cast<uint4*>(g + sl * slice_stride) = make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
+              for (int sl = 0; sl < 3; ++sl)
+                if (sl < out_slices)
+                  *reinterpret_cast<uint4*>(g + sl * slice_stride) =
+                      make_uint4(w[sl][0], w[sl][1], w[sl][2], w[sl][3]);
+            }
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
@@ -560,41 +597,61 @@ cudaError_t launch_mode(const TmTile* d_tiles, int ntiles, const TmTerm* d_terms
   return cudaGetLastError();
 }
 
-// exact splitting: one block of threads per job (block maximum, then the slices)
+// exact splitting: one block of threads per job, warps over rows, lanes over columns.
+// The block maximum is taken on the bit patterns (|x| orders like its bits as an
+// unsigned integer), so the FP64 units see one multiply per element for the scaling by
+// scale * 2^-e (exact: a power of two times the rounding of scale * x) and the split
+// v = a + lo into two FP32 values; the 7-bit slices come from a by exact FP32 steps
+// (w *= 2^7, q = rint(w), w -= q), and lo joins the remainder after the third slice
+// (one FP32 rounding, below 2^-46 of the block's scale).  Slice magnitudes: the first
+// <= 128, the fourth <= 72, the others <= 64.
 __global__ void split_exact_kernel(const SplitJob* __restrict__ jobs, int nsl, int* __restrict__ expo_out) {
   const SplitJob jb = jobs[blockIdx.x];
-  __shared__ double red[256];
+  __shared__ unsigned long long red[32];
   __shared__ int e_sh;
-  const long n = (long)jb.rows * jb.cols;
-  double m = 0.0;
-  for (long i = threadIdx.x; i < n; i += blockDim.x) {
-    const int r = (int)(i / jb.cols), c = (int)(i % jb.cols);
-    m = fmax(m, fabs(jb.scale * jb.src[(long)r * jb.lds + c]));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  unsigned long long m = 0;
+  for (int r = warp; r < jb.rows; r += nw) {
+    const double* src = jb.src + (long)r * jb.lds;
+    for (int c = lane; c < jb.cols; c += 32) {
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(src[c]) & 0x7fffffffffffffffULL;
+      m = bits > m ? bits : m;
+    }
   }
-  red[threadIdx.x] = m;
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+    m = t > m ? t : m;
+  }
+  if (lane == 0) red[warp] = m;
   __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
-    __syncthreads();
-  }
   if (threadIdx.x == 0) {
+    unsigned long long mm = 0;
+    for (int w = 0; w < nw; ++w) mm = red[w] > mm ? red[w] : mm;
+    // fl(|scale| * max|x|) bounds every fl(|scale * x|) (rounding is monotone)
+    const double mx = fabs(jb.scale) * __longlong_as_double((long long)mm);
     int e = 0;
-    if (red[0] > 0.0) frexp(red[0], &e);  // red[0] = f 2^e with 0.5 <= f < 1: |x| < 2^e
+    if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e with 0.5 <= f < 1: |scale * x| < 2^e
     e_sh = e;
     expo_out[jb.expo] = e;
   }
   __syncthreads();
-  const int e = e_sh;
-  const long nw = (long)jb.rows * jb.wcols;
-  for (long i = threadIdx.x; i < nw; i += blockDim.x) {
-    const int r = (int)(i / jb.wcols), c = (int)(i % jb.wcols);
-    double v = c < jb.cols ? ldexp(jb.scale * jb.src[(long)r * jb.lds + c], -e) : 0.0;  // |v| < 1
-    __nv_bfloat16* d = jb.trans ? jb.dst + (long)c * jb.ldd + r : jb.dst + (long)r * jb.ldd + c;
-    for (int s = 0; s < nsl; ++s) {
-      v *= (double)(1 << TM_EXACT_BITS);
-      const double q = rint(v);  // |q| <= 128: exact in BF16
-      d[s * jb.slice_stride] = __double2bfloat16(q);
-      v -= q;
+  const double f = ldexp(jb.scale, -e_sh);
+  constexpr float STEP = (float)(1 << TM_EXACT_BITS);
+  constexpr float LO_SCALE = (float)(1 << (3 * TM_EXACT_BITS));  // lo at the scale of the remainder after three slices
+  for (int r = warp; r < jb.rows; r += nw) {
+    const double* src = jb.src + (long)r * jb.lds;
+    for (int c = lane; c < jb.wcols; c += 32) {
+      const double v = c < jb.cols ? f * src[c] : 0.0;  // |v| < 1
+      float w = __double2float_rn(v);
+      const float lo = __double2float_rn(v - (double)w);
+      __nv_bfloat16* d = jb.trans ? jb.dst + (long)c * jb.ldd + r : jb.dst + (long)r * jb.ldd + c;
+      for (int s = 0; s < nsl; ++s) {
+        if (s == 3) w += lo * LO_SCALE;
+        w *= STEP;
+        const float q = rintf(w);  // an integer of at most 128 in magnitude: exact in BF16
+        d[(long)s * jb.slice_stride] = __float2bfloat16_rn(q);
+        w -= q;
+      }
     }
   }
 }
@@ -619,6 +676,7 @@ EncodeTiledFn encoder() {
 
 cudaError_t launch_split_exact(const SplitJob* d_jobs, int njobs, int nsl, int* d_expo, cudaStream_t s) {
   if (njobs <= 0) return cudaSuccess;
+  if (nsl < 1 || nsl > 6) return cudaErrorInvalidValue;  // the remainder and level-sum bounds hold up to six slices
   count_tc_launches(1);
   split_exact_kernel<<<njobs, 256, 0, s>>>(d_jobs, nsl, d_expo);
   return cudaGetLastError();

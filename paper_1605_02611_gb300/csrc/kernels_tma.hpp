@@ -74,9 +74,10 @@ cudaError_t launch_gemm_tma(int mode, const TmTile* d_tiles, int ntiles, const T
                             const int* d_expo = nullptr);
 
 // Exact splitting of FP64 blocks for the exact mode: per job, e = the smallest
-// exponent with |scale * x| < 2^e over the block, then nsl integer slices d_s with
-// scale * x * 2^-e = sum_s d_s 2^(-7 (s + 1)) (+ remainder below 2^(-7 nsl)), each
-// stored exactly as BF16, nsl slices slice_stride elements apart; columns
+// exponent with |scale * x| < 2^e over the block, then nsl (1 to 6) integer slices d_s
+// with scale * x * 2^-e = sum_s d_s 2^(-7 (s + 1)) (+ remainder below 2^(-7 nsl)), each
+// stored exactly as BF16 (|d_0| <= 128, |d_3| <= 72, the others <= 64), nsl slices
+// slice_stride elements apart; columns
 // [cols, wcols) are zero.  trans: dst[j * ldd + i] holds element (i, j) (rows of
 // the source become columns).  expo[job.expo] receives e.
 struct SplitJob {
