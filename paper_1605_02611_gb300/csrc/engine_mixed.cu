@@ -751,9 +751,34 @@ struct TmaPlan {
   DArr<CUtensorMap> maps;
   DArr<long> rowmap;
   DArr<int2> cbtab;  // (first column, width) of the column blocks of every input group
+  // device copies of a launch's copy lists
+  struct Lists {
+    DArr<int> cta_stage;
+    DArr<long> tfirst;
+    DArr<TmStage> stages;
+    DArr<TmPiece> pieces;
+    int grid = 0;
+    // the stage counts on the host (reduce mode: sets the tiles' stages and segments,
+    // so it comes before the tiles are uploaded); throws on a malformed term
+    void plan(int mode, std::vector<TmTile>& tiles, const std::vector<TmTerm>& terms, cudaStream_t s) {
+      TmListPlan lp;
+      if (!tma_plan_lists(mode, tiles, terms, lp)) throw Error(ST_ECUDA, "internal: malformed TMA term list");
+      grid = lp.grid;
+      cta_stage.upload(lp.cta_stage, s);
+      tfirst.upload(lp.tfirst, s);
+      stages.alloc((size_t)std::max<long>(lp.total, 1), s);
+      pieces.alloc((size_t)std::max<long>(lp.total, 1) * tma_pieces(mode), s);
+    }
+    // the lists themselves, on the device, from the uploaded tiles and terms
+    void fill(int mode, const TmTile* d_tiles, int ntiles, const TmTerm* d_terms, cudaStream_t s) {
+      cuda_check(launch_fill_lists(mode, d_tiles, ntiles, d_terms, tfirst.p, stages.p, pieces.p, s), "list fill");
+    }
+    TmListsDev dev() const { return {grid, cta_stage.p, stages.p, pieces.p}; }
+  };
   struct Chunk {
     DArr<TmTile> t1, t2;
     DArr<TmTerm> m1, m2;
+    Lists l1, l2;
     int n1 = 0, n2 = 0;
     DArr<ZeroJob> z;
     int nz = 0;
@@ -781,6 +806,20 @@ static void check_conv_jobs(const std::vector<ConvJob>& jobs, const DArr<__nv_bf
         j.dst + (long)(j.rows - 1) * j.ldd + j.wcols > buf.p + buf.n)
       throw Error(ST_ECUDA, "internal: conversion job outside its buffer");
 }
+
+namespace {
+// stages of a reduce-mode tile: its 16-column pieces (k / 16 per slice pair of every
+// term) packed TM_PACK_SLOTS to a stage
+long packed_stages(const std::vector<TmTerm>& m, int t0, int t1) {
+  long pieces = 0;
+  for (int t = t0; t < t1; ++t) {
+    const int nsl = std::max(1, (m[t].neg >> 4) & 15);
+    pieces += (long)(m[t].k / 16) * (nsl * (nsl + 1) / 2);
+  }
+  return (pieces + TM_PACK_SLOTS - 1) / TM_PACK_SLOTS;
+}
+
+}  // namespace
 
 void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, int nsl) {
   const auto& mid = c.mpo.bonds[k + 1];
@@ -1092,12 +1131,12 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
   // but the extent itself is trusted by the hardware)
   struct MapInfo {
     long rows, cols;
-    int box;
+    int box, boxc;
   };
   std::vector<MapInfo> minfo;
   // one map per slice, at consecutive indices (slice i of a map m is m + i)
   auto add_map = [&](const DArr<__nv_bfloat16>& buf, long off, long stride, long rows, long cols, long ld,
-                     int box_rows) {
+                     int box_rows, int box_cols) {
     const int first = (int)maps.size();
     for (int sl = 0; sl < nsl; ++sl) {
       const long o = off + sl * stride;
@@ -1105,14 +1144,16 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
           (size_t)(o + (rows - 1) * ld + cols) > buf.n)
         throw Error(ST_ECUDA, "internal: tensor map outside its buffer");
       CUtensorMap m;
-      if (!encode_bf16_map(&m, buf.p + o, (uint64_t)rows, (uint64_t)cols, (uint64_t)ld, (uint32_t)box_rows))
+      if (!encode_bf16_map(&m, buf.p + o, (uint64_t)rows, (uint64_t)cols, (uint64_t)ld, (uint32_t)box_rows,
+                           (uint32_t)box_cols))
         throw Error(ST_ECUDA, "cuTensorMapEncodeTiled failed");
       maps.push_back(m);
-      minfo.push_back({rows, cols, box_rows});
+      minfo.push_back({rows, cols, box_rows, box_cols});
     }
     return first;
   };
   const int n1max = tma_max_n(TM_MODE_STORE_BF16), n2max = tma_max_n(TM_MODE_REDUCE_F32);
+  const int bc1 = tma_box_cols(TM_MODE_STORE_BF16), bc2 = tma_box_cols(TM_MODE_REDUCE_F32);
   std::vector<std::vector<std::array<int, 3>>> nt1(ng);  // per g': (row0, width, Psi map) of the stage-1 N tiles
   // A1 of g': one map per K block (column block of g', a1rows x its padded width)
   std::vector<std::vector<int>> a1map(ng);
@@ -1122,12 +1163,13 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
     int r0 = 0;
     for (int p = 0; p < parts; ++p) {
       const int w = std::min(gR[gp] - r0, pad16((gR[gp] - r0 + (parts - p) - 1) / (parts - p)));
-      nt1[gp].push_back({r0, w, add_map(tp->psi_b, goff[gp], std::max<long>(ptot, 8), gR[gp], gC[gp], gC[gp], w)});
+      nt1[gp].push_back(
+          {r0, w, add_map(tp->psi_b, goff[gp], std::max<long>(ptot, 8), gR[gp], gC[gp], gC[gp], w, bc1)});
       r0 += w;
     }
     for (const auto& cc : gcol[gp]) {
       const int w = pad16(Rb.dim[cc[1]]);
-      a1map[gp].push_back(add_map(tp->a1, a1off[gp] + a1rows[gp] * cc[2], a1s, a1rows[gp], w, w, 128));
+      a1map[gp].push_back(add_map(tp->a1, a1off[gp] + a1rows[gp] * cc[2], a1s, a1rows[gp], w, w, 128, bc1));
     }
   }
   // X^T region of (chunk, g'): one submatrix (and map) per column block (ql', n1') of g',
@@ -1146,14 +1188,14 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
         for (const auto& rr : grow[gp]) {
           const int w = pad16(Lb.dim[rr[0]]);
           xtmap[ci][gp].push_back(add_map(tp->xt, xreg[ci][gp] + xregrows[ci][gp] * rr[2], tp->x_stride,
-                                          xregrows[ci][gp], w, w, 128));
+                                          xregrows[ci][gp], w, w, 128, bc2));
         }
   // left mirror: per width class one map per box height
   std::vector<std::vector<int>> lmap(nwc, std::vector<int>(n2max / 16 + 1, -1));
   for (int wc = 0; wc < nwc; ++wc)
     if (lrows_c[wc] > 0)
       for (int h = 16; h <= n2max; h += 16)
-        lmap[wc][h / 16] = add_map(tp->lmir, lbase[wc], ls, lrows_c[wc], wcls_w[wc], wcls_w[wc], h);
+        lmap[wc][h / 16] = add_map(tp->lmir, lbase[wc], ls, lrows_c[wc], wcls_w[wc], wcls_w[wc], h, bc2);
   tp->cbtab.upload(cbtab, c.stream);
   tp->maps.alloc(std::max<size_t>(maps.size(), 1), c.stream);
   if (!maps.empty())
@@ -1268,8 +1310,8 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
           }
           if (base.empty()) continue;
           for (TmTerm& t : base) t.neg |= nsl << 4;  // all slice pairs, expanded by the kernel
-          long steps = 0;
-          for (const TmTerm& t : base) steps += (t.k + 63) / 64 * npair;
+          long steps = 0;  // 16-column pieces (stage 2 packs four per K step)
+          for (const TmTerm& t : base) steps += t.k / 16 * npair;
           for (int r0 = 0; r0 < gC[g]; r0 += 128) {
             Pending pd;
             pd.tl = TmTile{};
@@ -1290,7 +1332,7 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
       long acc = 0;
       size_t t0 = 0;
       for (size_t t = 0; t < pd.terms.size(); ++t) {
-        acc += (pd.terms[t].k + 63) / 64 * npair;
+        acc += pd.terms[t].k / 16 * npair;
         if (acc >= target || t + 1 == pd.terms.size()) {
           TmTile tl = pd.tl;
           tl.t0 = (int)m2.size();
@@ -1300,9 +1342,10 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
             ks += (long)pd.terms[u].k * npair;
           }
           tl.t1 = (int)m2.size();
-          tl.nseg = (int)((acc + TM_SEG_KSTEPS - 1) / TM_SEG_KSTEPS);
+          const long stages = packed_stages(m2, tl.t0, tl.t1);
+          if (stages > (1L << 30)) throw Error(ST_ECUDA, "internal: stage-2 tile too long");
           t2.push_back(tl);
-          st2_steps += acc;
+          st2_steps += stages;
           st2_fl += 2.0 * 128 * tl.n * ks;
           t0 = t + 1;
           acc = 0;
@@ -1326,12 +1369,16 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
     };
     order(t1, m1);
     order(t2, m2);
+    // the copy lists of both launches (stage 2: sets every tile's stages and segments);
+    // their pieces follow from the terms checked below
+    ch.l1.plan(TM_MODE_STORE_BF16, t1, m1, c.stream);
+    ch.l2.plan(TM_MODE_REDUCE_F32, t2, m2, c.stream);
     st1_tiles += (double)t1.size();
     st2_tiles += (double)t2.size();
     // every access of the kernels checked against its buffer before anything runs:
     // operand boxes (their coordinates, alignment and widths), the rows stage 1 stores
     // through the row map and the blocks stage 2 reduces into
-    auto check_terms = [&](const std::vector<TmTile>& tt, const std::vector<TmTerm>& mm, int nmax) {
+    auto check_terms = [&](const std::vector<TmTile>& tt, const std::vector<TmTerm>& mm, int nmax, int bc) {
       for (const TmTile& tl : tt) {
         if (tl.n < 16 || tl.n > nmax || tl.n % 16 || tl.t0 < 0 || tl.t1 <= tl.t0 || tl.t1 > (int)mm.size())
           throw Error(ST_ECUDA, "internal: malformed TMA tile");
@@ -1339,15 +1386,16 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
           const TmTerm& m = mm[t];
           if (((m.neg >> 4) & 15) != nsl || m.amap < 0 || m.amap + nsl > (int)minfo.size() || m.bmap < 0 ||
               m.bmap + nsl > (int)minfo.size() ||
-              minfo[m.amap].box != 128 || minfo[m.bmap].box != tl.n || m.k < 16 || m.k % 16 || m.ax % 16 ||
-              m.bx % 16 || m.ax < 0 || m.bx < 0 || m.ay < 0 || m.by < 0 || m.ax + m.k > minfo[m.amap].cols + 63 ||
-              m.bx + m.k > minfo[m.bmap].cols + 63)
+              minfo[m.amap].box != 128 || minfo[m.bmap].box != tl.n || minfo[m.amap].boxc != bc ||
+              minfo[m.bmap].boxc != bc || m.k < 16 || m.k % 16 || m.ax % 16 || m.bx % 16 || m.ax < 0 || m.bx < 0 ||
+              m.ay < 0 || m.by < 0 || m.ax + m.k > minfo[m.amap].cols + bc - 1 ||
+              m.bx + m.k > minfo[m.bmap].cols + bc - 1)
             throw Error(ST_ECUDA, "internal: malformed TMA term");
         }
       }
     };
-    check_terms(t1, m1, n1max);
-    check_terms(t2, m2, n2max);
+    check_terms(t1, m1, n1max, bc1);
+    check_terms(t2, m2, n2max, bc2);
     for (const TmTile& tl : t1) {
       if (tl.rowmap_off < 0 || tl.rowmap_off + 128 > (long)rowmap.size() || tl.cb0 < 0 || tl.cb1 > (int)cbtab.size() ||
           tl.cb0 >= tl.cb1)
@@ -1372,11 +1420,11 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
       }
     }
     for (const TmTile& tl : t2) {
-      long ks = 0;
-      for (int t = tl.t0; t < tl.t1; ++t) ks += (m2[t].k + 63) / 64 * npair;
-      if (tl.nseg != (int)((ks + TM_SEG_KSTEPS - 1) / TM_SEG_KSTEPS))
-        throw Error(ST_ECUDA, "internal: stage-2 segment count");
+      const long stages = packed_stages(m2, tl.t0, tl.t1);
+      if (tl.pad != stages || stages < 1 || tl.nseg != (int)((stages + TM_SEG_KSTEPS - 1) / TM_SEG_KSTEPS))
+        throw Error(ST_ECUDA, "internal: stage-2 stage or segment count");
     }
+
     for (const TmTile& tl : t2)
       if (tl.m_valid < 1 || tl.m_valid > 128 || tl.out_off < 0 || tl.out_off % 4 || tl.ldo % 4 ||
           tl.out_off + (long)(tl.m_valid - 1) * tl.ldo + tl.n > tp->sig_total)
@@ -1390,6 +1438,8 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
     ch.t2.upload(t2, c.stream);
     ch.m2.upload(m2, c.stream);
     ch.n2 = (int)t2.size();
+    ch.l1.fill(TM_MODE_STORE_BF16, ch.t1.p, ch.n1, ch.m1.p, c.stream);
+    ch.l2.fill(TM_MODE_REDUCE_F32, ch.t2.p, ch.n2, ch.m2.p, c.stream);
     ch.nz = (int)zj.size();
     for (const ZeroJob& z : zj) ch.zmax = std::max(ch.zmax, z.n);
     ch.z.upload(zj, c.stream);
@@ -1423,10 +1473,10 @@ void run_tma_sigma(Context& c, SigmaPlan& plan, const double* x, double* y) {
   for (auto& ch : tp.chunks) {
     if (ch.nz) launch_zero(ch.z.p, ch.nz, ch.zmax, c.stream);
     cuda_check(launch_gemm_tma(TM_MODE_STORE_BF16, ch.t1.p, ch.n1, ch.m1.p, tp.maps.p, tp.rowmap.p, tp.cbtab.p,
-                               tp.xt.p, tp.nsl, tp.x_stride, tp.err.p, c.stream),
+                               tp.xt.p, tp.nsl, tp.x_stride, tp.err.p, c.stream, ch.l1.dev()),
                "tma stage 1");
     cuda_check(launch_gemm_tma(TM_MODE_REDUCE_F32, ch.t2.p, ch.n2, ch.m2.p, tp.maps.p, tp.rowmap.p, tp.cbtab.p,
-                               tp.sig_t.p, 1, 0, tp.err.p, c.stream),
+                               tp.sig_t.p, 1, 0, tp.err.p, c.stream, ch.l2.dev()),
                "tma stage 2");
   }
   if (tp.n_sig_jobs) launch_unconv(tp.sig_jobs.p, tp.n_sig_jobs, tp.sig_maxel, c.stream);
@@ -2130,21 +2180,29 @@ void env_update_exact(Context& c, Tilde& t, const SiteT& A, int site, Env& out, 
     dmaps.upload(maps, c.stream);
     DArr<TmTile> d1t;
     DArr<TmTerm> d1m, d2m;
+    // copy lists of every launch; each piece reads through one of this update's maps
+    // copy lists of every launch (their pieces follow from the terms checked above)
+    TmaPlan::Lists dl1;
+    dl1.plan(TM_MODE_EXACT_F64, e1t, e1m, c.stream);
     d1t.upload(e1t, c.stream);
     d1m.upload(e1m, c.stream);
+    dl1.fill(TM_MODE_EXACT_F64, d1t.p, (int)e1t.size(), d1m.p, c.stream);
     cuda_check(launch_gemm_tma(TM_MODE_EXACT_F64, d1t.p, (int)e1t.size(), d1m.p, dmaps.p, nullptr, nullptr, T64.p, 1, 0,
-                               err.p, c.stream, expo.p),
+                               err.p, c.stream, dl1.dev(), expo.p),
                "exact stage 1");
     DArr<SplitJob> dj2;
     dj2.upload(split2, c.stream);
     cuda_check(launch_split_exact(dj2.p, (int)split2.size(), NSL, expo.p, c.stream), "exact split of T");
     d2m.upload(e2m, c.stream);
     std::vector<DArr<TmTile>> d2t(out.cls.size());
+    std::vector<TmaPlan::Lists> dl2(out.cls.size());
     for (size_t ci = 0; ci < out.cls.size(); ++ci) {
       if (e2t[ci].empty()) continue;
+      dl2[ci].plan(TM_MODE_EXACT_F64, e2t[ci], e2m, c.stream);
       d2t[ci].upload(e2t[ci], c.stream);
+      dl2[ci].fill(TM_MODE_EXACT_F64, d2t[ci].p, (int)e2t[ci].size(), d2m.p, c.stream);
       cuda_check(launch_gemm_tma(TM_MODE_EXACT_F64, d2t[ci].p, (int)e2t[ci].size(), d2m.p, dmaps.p, nullptr, nullptr,
-                                 out.data[ci].p, 1, 0, err.p, c.stream, expo.p),
+                                 out.data[ci].p, 1, 0, err.p, c.stream, dl2[ci].dev(), expo.p),
                  "exact stage 2");
     }
     // the host lists and the chunk's buffers must outlive the launches

@@ -31,9 +31,11 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
 #include <mutex>
+#include <thread>
 
 namespace gbdmrg {
 
@@ -45,12 +47,16 @@ namespace {
 constexpr int TM_THREADS = 192;
 constexpr int TM_BOX_K = 64;                       // columns per box (128 bytes)
 constexpr int TM_A_BYTES = 128 * TM_BOX_K * 2;     // 16 KB
+constexpr int TM_SLOT_A = 128 * 16 * 2;            // packed mode: one 16-column piece of A (or B, n <= 128), 4 KB
 constexpr long TM_WAIT_LIMIT = 1L << 24;
 
 template <int MODE>
 struct TmCfg {
   static constexpr bool STORE = MODE == TM_MODE_STORE_BF16;
   static constexpr bool EXACT = MODE == TM_MODE_EXACT_F64;
+  // reduce mode: a stage holds up to TM_PACK_SLOTS pieces of 16 columns (32-byte swizzled
+  // boxes), from any terms of the tile, one K=16 instruction each
+  static constexpr bool PACK = MODE == TM_MODE_REDUCE_F32;
   // exact mode: 64 columns, so that the two-float sums (128 registers) fit
   static constexpr int NMAX = STORE ? 256 : (EXACT ? 64 : 128);
   static constexpr int NACC = 512 / NMAX;
@@ -79,15 +85,14 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return d;
 }
 
-// instruction descriptor: D f32, A/B bf16, both K-major, M = 128, N = n
-__device__ __forceinline__ uint32_t idesc_bf16(int n, bool negA) {
-  uint32_t d = 0;
-  d |= 1u << 4;
-  d |= 1u << 7;
-  d |= 1u << 10;
-  if (negA) d |= 1u << 13;
-  d |= (uint32_t)(n >> 3) << 17;
-  d |= (uint32_t)(128 >> 4) << 24;
+// the same for a 32-byte swizzled K-major operand (16 columns per row, 8-row groups 256 B apart)
+__device__ __forceinline__ uint64_t sdesc32(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(256 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)6 << 61;
   return d;
 }
 
@@ -156,7 +161,8 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
     gemm_tma_kernel(const TmTile* __restrict__ tiles, int ntiles, const TmTerm* __restrict__ terms,
                     const CUtensorMap* __restrict__ maps, const long* __restrict__ rowmap,
                     const int2* __restrict__ cbtab, void* __restrict__ out, int out_slices, long slice_stride,
-                    int* __restrict__ err, const int* __restrict__ expo) {
+                    int* __restrict__ err, const int* __restrict__ expo, const int* __restrict__ cta_stage,
+                    const TmStage* __restrict__ stg, const TmPiece* __restrict__ pcs) {
   using Cfg = TmCfg<MODE>;
   constexpr int S = Cfg::STAGES;
   constexpr int STAGE_BYTES = Cfg::STAGE_BYTES;
@@ -164,11 +170,6 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
   constexpr int NMAX = Cfg::NMAX;
   constexpr bool STORE = Cfg::STORE;
   constexpr bool EXACT = Cfg::EXACT;
-  // reduce mode: a tile's products accumulate in tensor memory for at most
-  // TM_SEG_KSTEPS K steps (a segment); the epilogue adds the segments in FP32
-  // registers with round-to-nearest, so the rounding toward zero of the tensor-core
-  // accumulation acts on short sums only
-  constexpr int SEG = STORE ? (1 << 30) : TM_SEG_KSTEPS;
   extern __shared__ uint8_t dsm[];
   __shared__ __align__(8) uint64_t full_b[TM_MAX_STAGES], empty_b[TM_MAX_STAGES], tfull_b[TM_MAX_ACC],
       tempty_b[TM_MAX_ACC];
@@ -207,111 +208,67 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
   volatile int* abort_flag = &abort_sh;
 
   if (warp == 0) {
-    // ---------------- TMA producer: the warp loads the term descriptors of a tile 32 at
-    // a time (one per lane) and prefetches their tensor maps (every slice's); lane 0
-    // issues the copies.  Descriptor loads run ahead of their use: the tile after next
-    // and the next tile's first 32 terms while a tile is issued, the next 32 terms of a
-    // tile while the current 32 are issued.
-    long j = 0;  // K steps issued (lane 0)
-    int st = 0;          // stage of the next K step (j % S)
-    uint32_t par = 0;    // its round's parity ((j / S) & 1)
+    // ---------------- TMA producer: the CTA's stages from the copy lists, loaded two
+    // stages ahead (lane p < PIECES holds piece p).  Per stage lane 0 waits until the
+    // ring slot is free and posts the stage word and the expected bytes, then lane
+    // p < np issues the two box copies of piece p.
+    constexpr int PIECES = Cfg::PACK ? TM_PACK_SLOTS : 1;
+    constexpr uint32_t A_BOX = 128u * (Cfg::PACK ? 16 : TM_BOX_K) * 2;
+    constexpr unsigned FULL = 0xffffffffu;
+    long j = 0;            // stages issued
+    int st = 0;            // ring slot of the next one (j % S)
+    uint32_t par = 0;      // its round's parity ((j / S) & 1)
     bool wrapped = false;  // j >= S
     bool ok = true;
-    const int G = (int)gridDim.x;
-    TmTile cur{}, nxt{};
-    TmTerm pre{};  // this lane's term of the current tile's first batch
-    if ((int)blockIdx.x < ntiles) {
-      cur = tiles[blockIdx.x];
-      if (lane < min(32, cur.t1 - cur.t0)) pre = terms[cur.t0 + lane];
+    const int s_beg = cta_stage[blockIdx.x], s_end = cta_stage[blockIdx.x + 1];
+    TmStage h0{}, h1{};
+    TmPiece q0{}, q1{};
+    if (s_beg < s_end) {
+      h0 = stg[s_beg];
+      if (lane < PIECES) q0 = pcs[(long)s_beg * PIECES + lane];
     }
-    if ((int)blockIdx.x + G < ntiles) nxt = tiles[blockIdx.x + G];
-    for (int ti = blockIdx.x; ti < ntiles && ok; ti += G) {
-      const TmTile tl = cur;
-      TmTile nn{};
-      if (ti + 2 * G < ntiles) nn = tiles[ti + 2 * G];
-      TmTerm pre_next{};
-      if (ti + G < ntiles && lane < min(32, nxt.t1 - nxt.t0)) pre_next = terms[nxt.t0 + lane];
-      const uint32_t bbytes = (uint32_t)tl.n * TM_BOX_K * 2;
-      int seg_pos = 0;  // K steps of the current segment so far
-      TmTerm mine = pre, ahead{};
-      for (int tb = tl.t0; tb < tl.t1 && ok; tb += 32) {
-        const int cnt = min(32, tl.t1 - tb);
-        if (tb != tl.t0) mine = ahead;
-        if (tb + 32 < tl.t1 && lane < min(32, tl.t1 - tb - 32)) ahead = terms[tb + 32 + lane];
-        if (lane < cnt) {
-          const int nslp = max(1, (mine.neg >> 4) & 15);
-          for (int i = 0; i < nslp; ++i) {
-            asm volatile("prefetch.tensormap [%0];\n" ::"l"(maps + mine.amap + i) : "memory");
-            asm volatile("prefetch.tensormap [%0];\n" ::"l"(maps + mine.bmap + i) : "memory");
-          }
-        }
-        for (int q = 0; q < cnt && ok; ++q) {
-          TmTerm tm;
-          tm.amap = __shfl_sync(0xffffffffu, mine.amap, q);
-          tm.bmap = __shfl_sync(0xffffffffu, mine.bmap, q);
-          tm.ax = __shfl_sync(0xffffffffu, mine.ax, q);
-          tm.ay = __shfl_sync(0xffffffffu, mine.ay, q);
-          tm.bx = __shfl_sync(0xffffffffu, mine.bx, q);
-          tm.by = __shfl_sync(0xffffffffu, mine.by, q);
-          tm.k = __shfl_sync(0xffffffffu, mine.k, q);
-          tm.neg = __shfl_sync(0xffffffffu, mine.neg, q);
-          tm.ea = __shfl_sync(0xffffffffu, mine.ea, q);
-          tm.eb = __shfl_sync(0xffffffffu, mine.eb, q);
-          if (lane == 0) {
-            const uint32_t id = idesc_bf16(tl.n, (tm.neg & 1) != 0);
-            const bool last_term = tb + q + 1 == tl.t1;
-            // the term stands for all slice pairs (i, j), i + j < nsl, in order of the
-            // level l = i + j (slice i of a map is the map index + i); exact mode: one
-            // segment per level
-            const int nsl = max(1, (tm.neg >> 4) & 15);
-            for (int l = 0; l < nsl && ok; ++l)
-              for (int i = 0; i <= l && ok; ++i) {
-                const CUtensorMap* ma = maps + tm.amap + i;
-                const CUtensorMap* mb = maps + tm.bmap + (l - i);
-                for (int k0 = 0; k0 < tm.k; k0 += TM_BOX_K) {
-                  if (wrapped && !mbar_wait(&empty_b[st], par ^ 1u, abort_flag)) {
-                    ok = false;
-                    break;
-                  }
-                  const bool kend = k0 + TM_BOX_K >= tm.k;
-                  const bool last = last_term && kend && l + 1 == nsl && i == l;
-                  uint32_t fl = (uint32_t)min(TM_BOX_K / 16, (tm.k - k0) / 16);
-                  if (EXACT) {
-                    fl |= (i == 0 && k0 == 0) ? 8u : 0u;
-                    fl |= (i == l && kend) ? 16u : 0u;
-                  } else {
-                    fl |= seg_pos == 0 ? 8u : 0u;
-                    fl |= (last || seg_pos == SEG - 1) ? 16u : 0u;
-                  }
-                  fl |= last ? 32u : 0u;
-                  meta[st] = (uint64_t)id | ((uint64_t)fl << 32);
-                  const uint32_t sa = base + st * STAGE_BYTES;
-                  mbar_arrive_expect_tx(&full_b[st], TM_A_BYTES + bbytes);
-                  tma_load_2d(sa, ma, tm.ax + k0, tm.ay, &full_b[st]);
-                  tma_load_2d(sa + TM_A_BYTES, mb, tm.bx + k0, tm.by, &full_b[st]);
-                  ++j;
-                  if (++seg_pos == SEG) seg_pos = 0;
-                  if (++st == S) {
-                    st = 0;
-                    par ^= 1u;
-                    wrapped = true;
-                  }
-                }
-              }
-          }
-          ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (s_beg + 1 < s_end) {
+      h1 = stg[s_beg + 1];
+      if (lane < PIECES) q1 = pcs[(long)(s_beg + 1) * PIECES + lane];
+    }
+    for (int sidx = s_beg; sidx < s_end && ok; ++sidx) {
+      TmStage h2{};
+      TmPiece q2{};
+      if (sidx + 2 < s_end) {
+        h2 = stg[sidx + 2];
+        if (lane < PIECES) q2 = pcs[(long)(sidx + 2) * PIECES + lane];
+      }
+      if (lane == 0) {
+        if (wrapped && !mbar_wait(&empty_b[st], par ^ 1u, abort_flag)) ok = false;
+        if (ok) {
+          meta[st] = h0.word;
+          mbar_arrive_expect_tx(&full_b[st], h0.bytes);
         }
       }
-      cur = nxt;
-      nxt = nn;
-      pre = pre_next;
+      ok = __shfl_sync(FULL, ok, 0);
+      if (!ok) break;
+      if (lane < h0.np) {
+        const uint32_t sa = base + st * STAGE_BYTES;
+        tma_load_2d(sa + lane * A_BOX, maps + q0.amap, q0.ax, q0.ay, &full_b[st]);
+        tma_load_2d(sa + PIECES * A_BOX + lane * A_BOX, maps + q0.bmap, q0.bx, q0.by, &full_b[st]);
+      }
+      ++j;
+      if (++st == S) {
+        st = 0;
+        par ^= 1u;
+        wrapped = true;
+      }
+      h0 = h1;
+      q0 = q1;
+      h1 = h2;
+      q1 = q2;
     }
     if (lane == 0) {
       // every issued copy must land before the CTA may exit: the last (up to S)
       // issued stages complete their full phase when their bytes arrive
-      for (long q = j - 1; q >= 0 && q >= j - S; --q) {
-        const int s = (int)(q % S);
-        for (long it = 0; it < TM_WAIT_LIMIT && !mbar_test(&full_b[s], (uint32_t)((q / S) & 1)); ++it) {
+      for (long qq = j - 1; qq >= 0 && qq >= j - S; --qq) {
+        const int s2 = (int)(qq % S);
+        for (long it = 0; it < TM_WAIT_LIMIT && !mbar_test(&full_b[s2], (uint32_t)((qq / S) & 1)); ++it) {
         }
       }
     }
@@ -325,7 +282,8 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
       // shared-memory descriptors of stage 0's operands; stage s and K=16 step kk add
       // (s * STAGE_BYTES + kk * 32) / 16 to the 14-bit address field (no carry: shared
       // addresses stay below 256 KB)
-      const uint64_t ad0 = sdesc(base), bd0 = sdesc(base + TM_A_BYTES);
+      const uint64_t ad0 = Cfg::PACK ? sdesc32(base) : sdesc(base);
+      const uint64_t bd0 = Cfg::PACK ? sdesc32(base + TM_PACK_SLOTS * TM_SLOT_A) : sdesc(base + TM_A_BYTES);
       for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
         bool tile_done = false;
         while (!tile_done && ok) {
@@ -347,12 +305,22 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
             const int nk = (int)(fl & 7u);
             const uint64_t off = (uint64_t)((st * STAGE_BYTES) >> 4);
             for (int kk = 0; kk < nk; ++kk) {
-              const uint64_t ad = ad0 + off + (uint64_t)(kk * 2), bd = bd0 + off + (uint64_t)(kk * 2);
+              uint64_t ad, bd;
+              uint32_t idk = id;
+              if constexpr (Cfg::PACK) {
+                // slot kk: A at kk * 4 KB, B at 16 KB + kk * 4 KB of the stage
+                ad = ad0 + off + (uint64_t)(kk * (TM_SLOT_A >> 4));
+                bd = bd0 + off + (uint64_t)(kk * (TM_SLOT_A >> 4));
+                idk |= ((fl >> (8 + kk)) & 1u) << 13;
+              } else {
+                ad = ad0 + off + (uint64_t)(kk * 2);
+                bd = bd0 + off + (uint64_t)(kk * 2);
+              }
               const uint32_t accum = ((fl & 8u) && kk == 0) ? 0u : 1u;
               asm volatile(
                   "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                   " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dacc),
-                  "l"(ad), "l"(bd), "r"(id), "r"(accum));
+                  "l"(ad), "l"(bd), "r"(idk), "r"(accum));
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                 smem_u32(&empty_b[st])));
@@ -578,22 +546,17 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
 template <int MODE>
 cudaError_t launch_mode(const TmTile* d_tiles, int ntiles, const TmTerm* d_terms, const CUtensorMap* d_maps,
                         const long* d_rowmap, const int2* d_cbtab, void* out, int out_slices, long slice_stride,
-                        int* d_err, cudaStream_t s, const int* d_expo) {
-  static const int nsm = [] {
-    if (cudaFuncSetAttribute(gemm_tma_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TmCfg<MODE>::SMEM) !=
-        cudaSuccess)
-      return -1;
-    int dev = 0, n = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    return n > 0 ? n : 148;
-  }();
-  if (nsm < 0) return cudaErrorInvalidValue;
-  const int grid = ntiles < nsm ? ntiles : nsm;
+                        int* d_err, cudaStream_t s, const int* d_expo, const TmListsDev& lists) {
+  static const bool attr_ok = cudaFuncSetAttribute(gemm_tma_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   TmCfg<MODE>::SMEM) == cudaSuccess;
+  if (!attr_ok) return cudaErrorInvalidValue;
+  // the lists were built for this grid: every CTA's tiles and stages
+  if (lists.grid != tma_grid(ntiles) || !lists.cta_stage || !lists.stages || !lists.pieces)
+    return cudaErrorInvalidValue;
   count_tc_launches(1);
-  gemm_tma_kernel<MODE><<<grid, TM_THREADS, TmCfg<MODE>::SMEM, s>>>(d_tiles, ntiles, d_terms, d_maps, d_rowmap,
-                                                                     d_cbtab, out, out_slices, slice_stride, d_err,
-                                                                     d_expo);
+  gemm_tma_kernel<MODE><<<lists.grid, TM_THREADS, TmCfg<MODE>::SMEM, s>>>(
+      d_tiles, ntiles, d_terms, d_maps, d_rowmap, d_cbtab, out, out_slices, slice_stride, d_err, d_expo,
+      lists.cta_stage, lists.stages, lists.pieces);
   return cudaGetLastError();
 }
 
@@ -683,39 +646,168 @@ cudaError_t launch_split_exact(const SplitJob* d_jobs, int njobs, int nsl, int* 
 }
 
 int tma_max_n(int mode) { return mode == TM_MODE_STORE_BF16 ? 256 : (mode == TM_MODE_EXACT_F64 ? 64 : 128); }
+int tma_box_cols(int mode) { return mode == TM_MODE_REDUCE_F32 ? 16 : TM_BOX_K; }
 
 cudaError_t launch_gemm_tma(int mode, const TmTile* d_tiles, int ntiles, const TmTerm* d_terms,
                             const CUtensorMap* d_maps, const long* d_rowmap, const int2* d_cbtab, void* out,
-                            int out_slices, long slice_stride, int* d_err, cudaStream_t s, const int* d_expo) {
+                            int out_slices, long slice_stride, int* d_err, cudaStream_t s, const TmListsDev& lists,
+                            const int* d_expo) {
   if (ntiles <= 0) return cudaSuccess;
   if (out_slices < 1 || out_slices > 3) return cudaErrorInvalidValue;
   if (mode == TM_MODE_STORE_BF16)
     return launch_mode<TM_MODE_STORE_BF16>(d_tiles, ntiles, d_terms, d_maps, d_rowmap, d_cbtab, out, out_slices,
-                                           slice_stride, d_err, s, nullptr);
+                                           slice_stride, d_err, s, nullptr, lists);
   if (mode == TM_MODE_REDUCE_F32)
     return launch_mode<TM_MODE_REDUCE_F32>(d_tiles, ntiles, d_terms, d_maps, d_rowmap, d_cbtab, out, 1, 0, d_err, s,
-                                           nullptr);
+                                           nullptr, lists);
   if (mode == TM_MODE_EXACT_F64) {
-    if (!d_expo) return cudaErrorInvalidValue;
+    if (!d_expo || !d_terms) return cudaErrorInvalidValue;
     return launch_mode<TM_MODE_EXACT_F64>(d_tiles, ntiles, d_terms, d_maps, d_rowmap, d_cbtab, out, 1, 0, d_err, s,
-                                          d_expo);
+                                          d_expo, lists);
   }
   return cudaErrorInvalidValue;
 }
 
+int tma_grid(int ntiles) {
+  static const int nsm = [] {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess)
+      return 148;
+    return n > 0 ? n : 148;
+  }();
+  return ntiles < nsm ? ntiles : nsm;
+}
+
+int tma_pieces(int mode) { return mode == TM_MODE_REDUCE_F32 ? TM_PACK_SLOTS : 1; }
+
+namespace {
+__host__ __device__ inline long term_pieces(const TmTerm& m, int bc) {
+  const int nsl = ((m.neg >> 4) & 15) > 1 ? ((m.neg >> 4) & 15) : 1;
+  return (long)((m.k + bc - 1) / bc) * (nsl * (nsl + 1) / 2);
+}
+
+// One thread per tile fills the tile's stages.  A term's pieces: its slice pairs (i, j),
+// i + j < nsl, in level order, each its boxes along K.  Segments: store mode one per
+// tile; reduce mode TM_SEG_KSTEPS stages each (the products accumulate in tensor memory
+// over a segment only and the epilogue adds the segments in FP32 with round-to-nearest,
+// so the rounding toward zero of the tensor-core accumulation acts on short sums);
+// exact mode one per level of every term.
+__global__ void fill_lists_kernel(int mode, const TmTile* __restrict__ tiles, int ntiles,
+                                  const TmTerm* __restrict__ terms, const long* __restrict__ tfirst,
+                                  TmStage* __restrict__ stages, TmPiece* __restrict__ pieces) {
+  const int ti = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ti >= ntiles) return;
+  const bool pack = mode == TM_MODE_REDUCE_F32, exact = mode == TM_MODE_EXACT_F64;
+  const int bc = pack ? 16 : TM_BOX_K, P = pack ? TM_PACK_SLOTS : 1;
+  const uint32_t a_box = 128u * bc * 2;
+  const TmTile tl = tiles[ti];
+  const uint32_t b_box = (uint32_t)tl.n * bc * 2;
+  const long s0 = tfirst[ti];
+  long sidx = s0, left = 0;
+  for (int t = tl.t0; t < tl.t1; ++t) left += term_pieces(terms[t], bc);
+  int slot = 0, seg_pos = 0;
+  uint32_t negm = 0;
+  for (int t = tl.t0; t < tl.t1; ++t) {
+    const TmTerm m = terms[t];
+    const int nsl = max(1, (m.neg >> 4) & 15);
+    const int kp = (m.k + bc - 1) / bc;
+    for (int l = 0; l < nsl; ++l)
+      for (int i = 0; i <= l; ++i)
+        for (int kk = 0; kk < kp; ++kk) {
+          const int k0 = kk * bc;
+          pieces[sidx * P + slot] = TmPiece{m.amap + i, m.ax + k0, m.ay, m.bmap + (l - i), m.bx + k0, m.by};
+          negm |= (uint32_t)(m.neg & 1) << slot;
+          --left;
+          const long np_here = min((long)P, (long)slot + 1 + left);  // this stage's pieces
+          if (++slot < np_here) continue;
+          const bool last = left == 0;
+          uint32_t fl, id;
+          if (pack) {
+            fl = (uint32_t)slot | (negm << 8);
+            fl |= seg_pos == 0 ? 8u : 0u;
+            fl |= (last || seg_pos == TM_SEG_KSTEPS - 1) ? 16u : 0u;
+            id = tm_idesc_bf16(tl.n, false);
+          } else {
+            fl = (uint32_t)min(bc / 16, (m.k - k0) / 16);
+            if (exact) {
+              fl |= (i == 0 && kk == 0) ? 8u : 0u;
+              fl |= (i == l && kk == kp - 1) ? 16u : 0u;
+            } else {
+              fl |= sidx == s0 ? 8u : 0u;
+              fl |= last ? 16u : 0u;
+            }
+            id = tm_idesc_bf16(tl.n, (m.neg & 1) != 0);
+          }
+          fl |= last ? 32u : 0u;
+          stages[sidx] = TmStage{(uint64_t)id | ((uint64_t)fl << 32), (uint32_t)slot * (a_box + b_box), slot};
+          for (int p = slot; p < P; ++p) pieces[sidx * P + p] = TmPiece{0, 0, 0, 0, 0, 0};
+          ++sidx;
+          slot = 0;
+          negm = 0;
+          if (++seg_pos == TM_SEG_KSTEPS) seg_pos = 0;
+        }
+  }
+}
+}  // namespace
+
+bool tma_plan_lists(int mode, std::vector<TmTile>& tiles, const std::vector<TmTerm>& terms, TmListPlan& out) {
+  const int ntiles = (int)tiles.size();
+  const int grid = ntiles > 0 ? tma_grid(ntiles) : 0;
+  const int bc = tma_box_cols(mode), P = tma_pieces(mode);
+  for (const TmTerm& m : terms)
+    if (m.k < 16 || m.k % 16) return false;
+  std::vector<long> tst((size_t)ntiles);
+  for (int ti = 0; ti < ntiles; ++ti) {
+    const TmTile& tl = tiles[(size_t)ti];
+    if (tl.t0 < 0 || tl.t1 <= tl.t0 || tl.t1 > (int)terms.size()) return false;
+    long pc = 0;
+    for (int t = tl.t0; t < tl.t1; ++t) pc += term_pieces(terms[(size_t)t], bc);
+    tst[(size_t)ti] = (pc + P - 1) / P;
+  }
+  out.grid = grid;
+  out.cta_stage.assign((size_t)grid + 1, 0);
+  out.tfirst.assign((size_t)ntiles, 0);
+  long total = 0;
+  for (int c = 0; c < grid; ++c) {
+    out.cta_stage[(size_t)c] = (int)total;
+    for (int ti = c; ti < ntiles; ti += grid) {
+      out.tfirst[(size_t)ti] = total;
+      total += tst[(size_t)ti];
+    }
+    if (total >= (1L << 31) / P) return false;
+  }
+  out.cta_stage[(size_t)grid] = (int)total;
+  out.total = total;
+  if (mode == TM_MODE_REDUCE_F32)
+    for (int ti = 0; ti < ntiles; ++ti) {
+      tiles[(size_t)ti].pad = (int)tst[(size_t)ti];
+      tiles[(size_t)ti].nseg = (int)((tst[(size_t)ti] + TM_SEG_KSTEPS - 1) / TM_SEG_KSTEPS);
+    }
+  return true;
+}
+
+cudaError_t launch_fill_lists(int mode, const TmTile* d_tiles, int ntiles, const TmTerm* d_terms, const long* d_tfirst,
+                              TmStage* d_stages, TmPiece* d_pieces, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  count_tc_launches(1);
+  fill_lists_kernel<<<(ntiles + 127) / 128, 128, 0, s>>>(mode, d_tiles, ntiles, d_terms, d_tfirst, d_stages, d_pieces);
+  return cudaGetLastError();
+}
+
 bool encode_bf16_map(CUtensorMap* out, const void* base, uint64_t rows, uint64_t cols, uint64_t ld,
-                     uint32_t box_rows) {
+                     uint32_t box_rows, uint32_t box_cols) {
   EncodeTiledFn fn = encoder();
   if (!fn || rows == 0 || cols == 0 || (ld * 2) % 16 != 0 || ((uintptr_t)base & 15) != 0 || box_rows == 0 ||
-      box_rows > 256)
+      box_rows > 256 || (box_cols != 16 && box_cols != (uint32_t)TM_BOX_K))
     return false;
   const cuuint64_t dims[2] = {cols, rows};
   const cuuint64_t strides[1] = {ld * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)TM_BOX_K, box_rows};
+  const cuuint32_t box[2] = {box_cols, box_rows};
   const cuuint32_t estr[2] = {1, 1};
   return fn(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+            CU_TENSOR_MAP_INTERLEAVE_NONE, box_cols == 16 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace gbdmrg

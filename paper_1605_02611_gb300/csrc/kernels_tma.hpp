@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 namespace gbdmrg {
 
@@ -32,6 +33,10 @@ struct TmTerm {
 
 // Output tile over the terms [t0, t1).  n: MMA width (multiple of 16, <= the
 // kernel's maximum).
+//   reduce mode (packed): the tensor maps of the tile's terms have boxes of 16 columns
+//     (32-byte swizzle), and a K step (stage) holds up to TM_PACK_SLOTS consecutive
+//     pieces of 16 columns of the tile (a term has k / 16 pieces per slice pair);
+//     pad = the tile's stages, ceil(pieces / TM_PACK_SLOTS).
 //   store mode (X intermediates, BF16): the output matrix is split by columns into
 //     column blocks, each its own row-major submatrix of xrows rows: block e of
 //     cbtab[cb0..cb1) = (first column c0, width w) starts at element
@@ -40,9 +45,8 @@ struct TmTerm {
 //     columns are out_off .. out_off + n (every 8-column chunk inside one block).
 //   reduce mode (sigma^T, FP32): rows r < m_valid are added (vector reductions) to
 //     out + out_off + r * ldo, columns [0, n).
-//   nseg (reduce mode): segments of the tile, ceil(K steps / TM_SEG_KSTEPS) with one K
-//     step per 64 columns of every term; each segment accumulates in tensor memory
-//     on its own and the epilogue adds the segments in FP32.
+//   nseg (reduce mode): segments of the tile, ceil(stages / TM_SEG_KSTEPS); each segment
+//     accumulates in tensor memory on its own and the epilogue adds the segments in FP32.
 struct TmTile {
   int t0, t1;
   int n, m_valid;
@@ -51,7 +55,7 @@ struct TmTile {
   long rowmap_off;
   long xbase, xrows;
   int cb0, cb1;
-  int nvalid, pad;  // exact mode: valid columns of the output block
+  int nvalid, pad;  // exact mode: valid columns of the output block; reduce mode: pad = pieces
 };
 
 //   exact mode (FP64): rows r < m_valid, columns c < nvalid of
@@ -60,17 +64,82 @@ struct TmTile {
 constexpr int TM_MODE_STORE_BF16 = 1, TM_MODE_REDUCE_F32 = 2, TM_MODE_EXACT_F64 = 3;
 // bits of the slices of the exact mode
 constexpr int TM_EXACT_BITS = 7;
-// K steps (64 columns each) accumulated in tensor memory before the reduce-mode
-// epilogue takes the partial sum over
+// K steps (stages of up to TM_PACK_SLOTS 16-column pieces) accumulated in tensor memory
+// before the reduce-mode epilogue takes the partial sum over
 constexpr int TM_SEG_KSTEPS = 16;
+constexpr int TM_PACK_SLOTS = 4;
+
+// Copy lists.  The tiles' terms are expanded on the host into stages, each holding up
+// to tma_pieces(mode) pieces (a piece: one A box and one B box, both of tma_box_cols(mode)
+// columns; store and exact modes one piece of 64 columns, reduce mode up to
+// TM_PACK_SLOTS consecutive pieces of 16 columns).  A term expands into its slice pairs
+// (i, j), i + j < nsl, in the order of the level l = i + j (A map amap + i, B map
+// bmap + j), each into its boxes along K.  CTA c of a launch of `grid` CTAs takes the
+// tiles c, c + grid, ... and issues the stages [cta_stage[c], cta_stage[c + 1]), stage s
+// with the pieces pieces[s * tma_pieces(mode) + p], p < np.
+struct TmPiece {
+  int amap, ax, ay, bmap, bx, by;
+};
+// word: the stage word the MMA issuer reads, the instruction descriptor (negation of A in
+// the store and exact modes) in the low half, in the high half the K=16 instructions
+// (store and exact modes; 1 per piece in the reduce mode) in bits 0-2, flags first of a
+// segment (bit 3), end of a segment (4), last stage of the tile (5), and in the reduce
+// mode the negation of slot p in bit 8 + p.  bytes: the stage's expected copy bytes.
+struct TmStage {
+  uint64_t word;
+  uint32_t bytes;
+  int np;
+};
+struct TmListsDev {  // device copies, kept alive by the caller for the launches
+  int grid = 0;
+  const int* cta_stage = nullptr;
+  const TmStage* stages = nullptr;
+  const TmPiece* pieces = nullptr;
+};
+// host side of a launch's lists: its grid, every CTA's first stage (grid + 1 entries)
+// and every tile's first stage
+struct TmListPlan {
+  int grid = 0;
+  long total = 0;
+  std::vector<int> cta_stage;
+  std::vector<long> tfirst;
+};
+
+// instruction descriptor of tcgen05.mma kind::f16: D FP32, A and B BF16, both K-major,
+// M = 128, N = n; negA negates A
+__host__ __device__ inline uint32_t tm_idesc_bf16(int n, bool negA) {
+  uint32_t d = 0;
+  d |= 1u << 4;
+  d |= 1u << 7;
+  d |= 1u << 10;
+  if (negA) d |= 1u << 13;
+  d |= (uint32_t)(n >> 3) << 17;
+  d |= (uint32_t)(128 >> 4) << 24;
+  return d;
+}
+
+// Host: the stage counts of a launch of `mode` over these tiles (for the grid the launch
+// will use, tma_grid(tiles.size())); reduce mode: sets every tile's pad (its stages) and
+// nseg.  Returns false if a term is malformed (k not a positive multiple of 16) or the
+// lists would be too long.
+bool tma_plan_lists(int mode, std::vector<TmTile>& tiles, const std::vector<TmTerm>& terms, TmListPlan& out);
+// Device: fills the copy lists (stages: total entries, pieces: total * tma_pieces(mode)),
+// one thread per tile, from the tiles and terms the plan was made from (on the device).
+cudaError_t launch_fill_lists(int mode, const TmTile* d_tiles, int ntiles, const TmTerm* d_terms, const long* d_tfirst,
+                              TmStage* d_stages, TmPiece* d_pieces, cudaStream_t s);
+// CTAs of a launch over ntiles tiles (min(ntiles, SMs of the current device))
+int tma_grid(int ntiles);
+int tma_pieces(int mode);
 
 // maps: device array of encoded tensor maps (64-byte aligned).  Store mode:
 // out_slices (1-3) BF16 slices x = s0 + s1 + ... of every FP32 result, written
 // slice_stride elements apart.  err: set to 1 if a bounded wait ran out (the CTA
-// then stops, lets its copies land and frees its tensor memory).
+// then stops, lets its copies land and frees its tensor memory).  lists: the copy lists
+// of these tiles (tma_plan_lists, launch_fill_lists), on the device.  d_terms: read by the exact mode's
+// epilogue only.
 cudaError_t launch_gemm_tma(int mode, const TmTile* d_tiles, int ntiles, const TmTerm* d_terms,
                             const CUtensorMap* d_maps, const long* d_rowmap, const int2* d_cbtab, void* out,
-                            int out_slices, long slice_stride, int* d_err, cudaStream_t s,
+                            int out_slices, long slice_stride, int* d_err, cudaStream_t s, const TmListsDev& lists,
                             const int* d_expo = nullptr);
 
 // Exact splitting of FP64 blocks for the exact mode: per job, e = the smallest
@@ -90,11 +159,14 @@ struct SplitJob {
 cudaError_t launch_split_exact(const SplitJob* d_jobs, int njobs, int nsl, int* d_expo, cudaStream_t s);
 // maximum MMA width of a mode (256 for the BF16 store mode, 128 for the reduce mode)
 int tma_max_n(int mode);
+// box width in columns of the tensor maps a mode reads (16 for the reduce mode, else 64)
+int tma_box_cols(int mode);
 
 // Host: encode a 2D BF16 tensor map over a row-major matrix (rows x cols, leading
 // dimension ld elements, ld * 2 a multiple of 16 bytes, base 16-byte aligned), box
-// of 64 columns x box_rows rows, 128-byte swizzle.  Returns false on failure.
+// of box_cols columns x box_rows rows: 64 columns with 128-byte swizzle or 16 columns
+// with 32-byte swizzle.  Returns false on failure.
 bool encode_bf16_map(CUtensorMap* out, const void* base, uint64_t rows, uint64_t cols, uint64_t ld,
-                     uint32_t box_rows);
+                     uint32_t box_rows, uint32_t box_cols = 64);
 
 }  // namespace gbdmrg
