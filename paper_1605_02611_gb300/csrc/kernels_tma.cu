@@ -49,6 +49,7 @@ constexpr int TM_BOX_K = 64;                       // columns per box (128 bytes
 constexpr int TM_A_BYTES = 128 * TM_BOX_K * 2;     // 16 KB
 constexpr int TM_SLOT_A = 128 * 16 * 2;            // packed mode: one 16-column piece of A (or B, n <= 128), 4 KB
 constexpr long TM_WAIT_LIMIT = 1L << 24;
+constexpr int TM_REC_BATCH = 32;  // stages of the copy lists fetched per bulk copy
 
 template <int MODE>
 struct TmCfg {
@@ -132,6 +133,13 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// 1D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16), completing on bar
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
 __device__ __forceinline__ void red_add_v4(float* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
   asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(p), "f"(__uint_as_float(a)),
                "f"(__uint_as_float(b)), "f"(__uint_as_float(c)), "f"(__uint_as_float(d))
@@ -180,6 +188,12 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
   // (packed into one 64-bit word: low half the instruction descriptor, high half the
   // K=16 steps in bits 0-2 and the flags first / segment end / last in bits 3-5)
   __shared__ uint64_t meta[TM_MAX_STAGES];
+  // copy lists of the producer: batches of TM_REC_BATCH stages, double-buffered, each
+  // landing by bulk copy on rec_b[buffer]
+  constexpr int PCS = Cfg::PACK ? TM_PACK_SLOTS : 1;
+  __shared__ __align__(16) TmStage rec_stage[2][TM_REC_BATCH];
+  __shared__ __align__(16) TmPiece rec_piece[2][TM_REC_BATCH * PCS];
+  __shared__ __align__(8) uint64_t rec_b[2];
   const uint32_t base = (smem_u32(dsm) + 1023u) & ~1023u;
   uint8_t* const base_ptr = dsm + (base - smem_u32(dsm));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -198,6 +212,8 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
       mbar_init(&tfull_b[a], 1);
       mbar_init(&tempty_b[a], 128);
     }
+    mbar_init(&rec_b[0], 1);
+    mbar_init(&rec_b[1], 1);
     abort_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
   }
@@ -208,11 +224,11 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
   volatile int* abort_flag = &abort_sh;
 
   if (warp == 0) {
-    // ---------------- TMA producer: the CTA's stages from the copy lists, loaded two
-    // stages ahead (lane p < PIECES holds piece p).  Per stage lane 0 waits until the
-    // ring slot is free and posts the stage word and the expected bytes, then lane
-    // p < np issues the two box copies of piece p.
-    constexpr int PIECES = Cfg::PACK ? TM_PACK_SLOTS : 1;
+    // ---------------- TMA producer: the CTA's stages from the copy lists, fetched into
+    // shared memory TM_REC_BATCH stages at a time by bulk copies one batch ahead.  Per
+    // stage lane 0 waits until the ring slot is free and posts the stage word and the
+    // expected bytes, then lane p < np issues the two box copies of piece p.
+    constexpr int PIECES = PCS;
     constexpr uint32_t A_BOX = 128u * (Cfg::PACK ? 16 : TM_BOX_K) * 2;
     constexpr unsigned FULL = 0xffffffffu;
     long j = 0;            // stages issued
@@ -221,56 +237,65 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
     bool wrapped = false;  // j >= S
     bool ok = true;
     const int s_beg = cta_stage[blockIdx.x], s_end = cta_stage[blockIdx.x + 1];
-    TmStage h0{}, h1{};
-    TmPiece q0{}, q1{};
-    if (s_beg < s_end) {
-      h0 = stg[s_beg];
-      if (lane < PIECES) q0 = pcs[(long)s_beg * PIECES + lane];
-    }
-    if (s_beg + 1 < s_end) {
-      h1 = stg[s_beg + 1];
-      if (lane < PIECES) q1 = pcs[(long)(s_beg + 1) * PIECES + lane];
-    }
-    for (int sidx = s_beg; sidx < s_end && ok; ++sidx) {
-      TmStage h2{};
-      TmPiece q2{};
-      if (sidx + 2 < s_end) {
-        h2 = stg[sidx + 2];
-        if (lane < PIECES) q2 = pcs[(long)(sidx + 2) * PIECES + lane];
-      }
+    const int nbatch = (s_end - s_beg + TM_REC_BATCH - 1) / TM_REC_BATCH;
+    int fetched = 0;  // record batches whose copies were issued
+    auto fetch = [&](int b) {  // lane 0
+      const int f0 = s_beg + b * TM_REC_BATCH, n = min(TM_REC_BATCH, s_end - f0);
+      const uint32_t hb = (uint32_t)n * sizeof(TmStage), pb = (uint32_t)(n * PIECES) * sizeof(TmPiece);
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      mbar_arrive_expect_tx(&rec_b[b & 1], hb + pb);
+      bulk_load(smem_u32(&rec_stage[b & 1][0]), stg + f0, hb, &rec_b[b & 1]);
+      bulk_load(smem_u32(&rec_piece[b & 1][0]), pcs + (long)f0 * PIECES, pb, &rec_b[b & 1]);
+    };
+    if (lane == 0 && nbatch > 0) fetch(0);
+    fetched = nbatch > 0 ? 1 : 0;
+    for (int b = 0; b < nbatch && ok; ++b) {
+      __syncwarp();  // the lanes' reads of the buffer batch b + 1 reuses are done
       if (lane == 0) {
-        if (wrapped && !mbar_wait(&empty_b[st], par ^ 1u, abort_flag)) ok = false;
-        if (ok) {
-          meta[st] = h0.word;
-          mbar_arrive_expect_tx(&full_b[st], h0.bytes);
-        }
+        if (b + 1 < nbatch) fetch(b + 1);
+        if (!mbar_wait(&rec_b[b & 1], (uint32_t)((b >> 1) & 1), abort_flag)) ok = false;
       }
+      if (b + 1 < nbatch) fetched = b + 2;
       ok = __shfl_sync(FULL, ok, 0);
       if (!ok) break;
-      if (lane < h0.np) {
-        const uint32_t sa = base + st * STAGE_BYTES;
-        tma_load_2d(sa + lane * A_BOX, maps + q0.amap, q0.ax, q0.ay, &full_b[st]);
-        tma_load_2d(sa + PIECES * A_BOX + lane * A_BOX, maps + q0.bmap, q0.bx, q0.by, &full_b[st]);
+      const int f0 = s_beg + b * TM_REC_BATCH, n = min(TM_REC_BATCH, s_end - f0);
+      for (int i = 0; i < n && ok; ++i) {
+        const TmStage h = rec_stage[b & 1][i];
+        if (lane == 0) {
+          if (wrapped && !mbar_wait(&empty_b[st], par ^ 1u, abort_flag)) ok = false;
+          if (ok) {
+            meta[st] = h.word;
+            mbar_arrive_expect_tx(&full_b[st], h.bytes);
+          }
+        }
+        ok = __shfl_sync(FULL, ok, 0);
+        if (!ok) break;
+        if (lane < h.np) {
+          const TmPiece q = rec_piece[b & 1][i * PIECES + lane];
+          const uint32_t sa = base + st * STAGE_BYTES;
+          tma_load_2d(sa + lane * A_BOX, maps + q.amap, q.ax, q.ay, &full_b[st]);
+          tma_load_2d(sa + PIECES * A_BOX + lane * A_BOX, maps + q.bmap, q.bx, q.by, &full_b[st]);
+        }
+        ++j;
+        if (++st == S) {
+          st = 0;
+          par ^= 1u;
+          wrapped = true;
+        }
       }
-      ++j;
-      if (++st == S) {
-        st = 0;
-        par ^= 1u;
-        wrapped = true;
-      }
-      h0 = h1;
-      q0 = q1;
-      h1 = h2;
-      q1 = q2;
     }
     if (lane == 0) {
       // every issued copy must land before the CTA may exit: the last (up to S)
-      // issued stages complete their full phase when their bytes arrive
+      // issued stages complete their full phase when their bytes arrive, and so does
+      // the last record batch fetched
       for (long qq = j - 1; qq >= 0 && qq >= j - S; --qq) {
         const int s2 = (int)(qq % S);
         for (long it = 0; it < TM_WAIT_LIMIT && !mbar_test(&full_b[s2], (uint32_t)((qq / S) & 1)); ++it) {
         }
       }
+      for (int b = max(0, fetched - 2); b < fetched; ++b)
+        for (long it = 0; it < TM_WAIT_LIMIT && !mbar_test(&rec_b[b & 1], (uint32_t)((b >> 1) & 1)); ++it) {
+        }
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer (one thread): one accumulator per segment
@@ -716,7 +741,7 @@ __global__ void fill_lists_kernel(int mode, const TmTile* __restrict__ tiles, in
       for (int i = 0; i <= l; ++i)
         for (int kk = 0; kk < kp; ++kk) {
           const int k0 = kk * bc;
-          pieces[sidx * P + slot] = TmPiece{m.amap + i, m.ax + k0, m.ay, m.bmap + (l - i), m.bx + k0, m.by};
+          pieces[sidx * P + slot] = TmPiece{m.amap + i, m.ax + k0, m.ay, m.bmap + (l - i), m.bx + k0, m.by, 0, 0};
           negm |= (uint32_t)(m.neg & 1) << slot;
           --left;
           const long np_here = min((long)P, (long)slot + 1 + left);  // this stage's pieces
@@ -741,7 +766,7 @@ __global__ void fill_lists_kernel(int mode, const TmTile* __restrict__ tiles, in
           }
           fl |= last ? 32u : 0u;
           stages[sidx] = TmStage{(uint64_t)id | ((uint64_t)fl << 32), (uint32_t)slot * (a_box + b_box), slot};
-          for (int p = slot; p < P; ++p) pieces[sidx * P + p] = TmPiece{0, 0, 0, 0, 0, 0};
+          for (int p = slot; p < P; ++p) pieces[sidx * P + p] = TmPiece{0, 0, 0, 0, 0, 0, 0, 0};
           ++sidx;
           slot = 0;
           negm = 0;

@@ -77,8 +77,8 @@ constexpr int TM_PACK_SLOTS = 4;
 // bmap + j), each into its boxes along K.  CTA c of a launch of `grid` CTAs takes the
 // tiles c, c + grid, ... and issues the stages [cta_stage[c], cta_stage[c + 1]), stage s
 // with the pieces pieces[s * tma_pieces(mode) + p], p < np.
-struct TmPiece {
-  int amap, ax, ay, bmap, bx, by;
+struct TmPiece {  // 32 bytes, so that any run of pieces is a bulk copy of 16-byte multiples
+  int amap, ax, ay, bmap, bx, by, pad0, pad1;
 };
 // word: the stage word the MMA issuer reads, the instruction descriptor (negation of A in
 // the store and exact modes) in the low half, in the high half the K=16 instructions
