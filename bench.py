@@ -38,9 +38,9 @@ sys.path.insert(0, ROOT)
 METRIC = "H_eff·ψ TFLOP/s & sweep s at K=40 M=2000, mixed vs FP64 GPU at |ΔE|≤1e-6 Eh"
 # DRAM bytes (read + write) of one H_eff.psi of the K=40 centre workload, both stages,
 # per precision, from one ncu capture of dram__bytes_read.sum + dram__bytes_write.sum
-# (profiles/gemm_tma_kernel_sigma_k40_m2000.md); None where not captured for the
+# (profiles/gemm_tma_kernel_sigma_k40_m2000.md); absent where not captured for the
 # current kernels
-TRAFFIC = {}
+TRAFFIC = {5: 26.46e9 + 37.16e9 + 66.38e9 + 0.05e9, 4: 8.20e9 + 12.29e9 + 21.40e9 + 0.04e9}
 
 WORKLOADS = {
     # name: K, N, two_sz, M, spread of the synthetic sector dimensions, integral seed, h off-diagonal std,

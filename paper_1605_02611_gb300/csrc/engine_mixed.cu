@@ -94,10 +94,18 @@ __global__ void unconv_kernel(const UnconvJob* __restrict__ jobs) {
   }
 }
 
+// blocks per job of the per-job copy kernels (blockIdx.y = job): with many jobs one block
+// each (its threads stride over the job), so that no launch holds thousands of idle
+// blocks sized for its largest job; with few jobs enough blocks for the largest
+static long job_blocks(int njobs, long maxel) {
+  if (njobs >= 1024) return 1;
+  return std::min<long>(std::max<long>(1, (maxel + 255) / 256), 64);
+}
+
 void launch_unconv(const UnconvJob* jobs, int njobs, long maxel, cudaStream_t s) {
   for (int o0 = 0; o0 < njobs; o0 += 65535) {
     int no = std::min(65535, njobs - o0);
-    long g = std::min<long>(std::max<long>(1, (maxel + 255) / 256), 64);
+    const long g = job_blocks(njobs, maxel);
     unconv_kernel<<<dim3((unsigned)g, no), 256, 0, s>>>(jobs + o0);
     count_launches(1);
   }
@@ -122,7 +130,7 @@ __global__ void zero_kernel(const ZeroJob* __restrict__ jobs) {
 void launch_zero(const ZeroJob* jobs, int njobs, long maxel, cudaStream_t s) {
   for (int o0 = 0; o0 < njobs; o0 += 65535) {
     int no = std::min(65535, njobs - o0);
-    long g = std::min<long>(std::max<long>(1, (maxel + 255) / 256), 64);
+    const long g = job_blocks(njobs, maxel);
     zero_kernel<<<dim3((unsigned)g, no), 256, 0, s>>>(jobs + o0);
     count_launches(1);
   }
@@ -132,7 +140,7 @@ void launch_zero(const ZeroJob* jobs, int njobs, long maxel, cudaStream_t s) {
 void launch_conv(const DArr<ConvJob>& jobs, int njobs, long maxel, cudaStream_t s) {
   for (int o0 = 0; o0 < njobs; o0 += 65535) {
     int no = std::min(65535, njobs - o0);
-    long g = std::min<long>(std::max<long>(1, (maxel + 255) / 256), 64);
+    const long g = job_blocks(njobs, maxel);
     conv_kernel<<<dim3((unsigned)g, no), 256, 0, s>>>(jobs.p + o0);
     count_launches(1);
   }
@@ -808,13 +816,13 @@ static void check_conv_jobs(const std::vector<ConvJob>& jobs, const DArr<__nv_bf
 }
 
 namespace {
-// stages of a reduce-mode tile: its 16-column pieces (k / 16 per slice pair of every
+// stages of a reduce-mode tile: its pieces (ceil(k / TM_PACK_COLS) per slice pair of every
 // term) packed TM_PACK_SLOTS to a stage
 long packed_stages(const std::vector<TmTerm>& m, int t0, int t1) {
   long pieces = 0;
   for (int t = t0; t < t1; ++t) {
     const int nsl = std::max(1, (m[t].neg >> 4) & 15);
-    pieces += (long)(m[t].k / 16) * (nsl * (nsl + 1) / 2);
+    pieces += (long)((m[t].k + TM_PACK_COLS - 1) / TM_PACK_COLS) * (nsl * (nsl + 1) / 2);
   }
   return (pieces + TM_PACK_SLOTS - 1) / TM_PACK_SLOTS;
 }
@@ -1310,8 +1318,8 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
           }
           if (base.empty()) continue;
           for (TmTerm& t : base) t.neg |= nsl << 4;  // all slice pairs, expanded by the kernel
-          long steps = 0;  // 16-column pieces (stage 2 packs four per K step)
-          for (const TmTerm& t : base) steps += t.k / 16 * npair;
+          long steps = 0;  // pieces (stage 2 packs TM_PACK_SLOTS per K step)
+          for (const TmTerm& t : base) steps += (t.k + bc2 - 1) / bc2 * npair;
           for (int r0 = 0; r0 < gC[g]; r0 += 128) {
             Pending pd;
             pd.tl = TmTile{};
@@ -1332,7 +1340,7 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
       long acc = 0;
       size_t t0 = 0;
       for (size_t t = 0; t < pd.terms.size(); ++t) {
-        acc += pd.terms[t].k / 16 * npair;
+        acc += (pd.terms[t].k + bc2 - 1) / bc2 * npair;
         if (acc >= target || t + 1 == pd.terms.size()) {
           TmTile tl = pd.tl;
           tl.t0 = (int)m2.size();

@@ -47,7 +47,7 @@ namespace {
 constexpr int TM_THREADS = 192;
 constexpr int TM_BOX_K = 64;                       // columns per box (128 bytes)
 constexpr int TM_A_BYTES = 128 * TM_BOX_K * 2;     // 16 KB
-constexpr int TM_SLOT_A = 128 * 16 * 2;            // packed mode: one 16-column piece of A (or B, n <= 128), 4 KB
+constexpr int TM_SLOT_A = 128 * TM_PACK_COLS * 2;  // packed mode: one piece of A (or B, n <= 128)
 constexpr long TM_WAIT_LIMIT = 1L << 24;
 constexpr int TM_REC_BATCH = 32;  // stages of the copy lists fetched per bulk copy
 
@@ -86,14 +86,16 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return d;
 }
 
-// the same for a 32-byte swizzled K-major operand (16 columns per row, 8-row groups 256 B apart)
-__device__ __forceinline__ uint64_t sdesc32(uint32_t saddr) {
+// the same for the packed pieces: K-major rows of TM_PACK_COLS columns, swizzled over
+// their width (32 columns: 64-byte swizzle, 8-row groups 512 B apart; 16 columns: 32-byte
+// swizzle, 256 B apart)
+__device__ __forceinline__ uint64_t sdesc_pack(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
   d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(256 >> 4) << 32;
+  d |= (uint64_t)((8 * TM_PACK_COLS * 2) >> 4) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)6 << 61;
+  d |= (uint64_t)(TM_PACK_COLS == 32 ? 4 : 6) << 61;
   return d;
 }
 
@@ -229,7 +231,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
     // stage lane 0 waits until the ring slot is free and posts the stage word and the
     // expected bytes, then lane p < np issues the two box copies of piece p.
     constexpr int PIECES = PCS;
-    constexpr uint32_t A_BOX = 128u * (Cfg::PACK ? 16 : TM_BOX_K) * 2;
+    constexpr uint32_t A_BOX = 128u * (Cfg::PACK ? TM_PACK_COLS : TM_BOX_K) * 2;
     constexpr unsigned FULL = 0xffffffffu;
     long j = 0;            // stages issued
     int st = 0;            // ring slot of the next one (j % S)
@@ -307,8 +309,8 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
       // shared-memory descriptors of stage 0's operands; stage s and K=16 step kk add
       // (s * STAGE_BYTES + kk * 32) / 16 to the 14-bit address field (no carry: shared
       // addresses stay below 256 KB)
-      const uint64_t ad0 = Cfg::PACK ? sdesc32(base) : sdesc(base);
-      const uint64_t bd0 = Cfg::PACK ? sdesc32(base + TM_PACK_SLOTS * TM_SLOT_A) : sdesc(base + TM_A_BYTES);
+      const uint64_t ad0 = Cfg::PACK ? sdesc_pack(base) : sdesc(base);
+      const uint64_t bd0 = Cfg::PACK ? sdesc_pack(base + TM_PACK_SLOTS * TM_SLOT_A) : sdesc(base + TM_A_BYTES);
       for (int ti = blockIdx.x; ti < ntiles && ok; ti += gridDim.x) {
         bool tile_done = false;
         while (!tile_done && ok) {
@@ -329,23 +331,22 @@ __global__ void __launch_bounds__(TM_THREADS, 1)
             const uint32_t id = (uint32_t)mw, fl = (uint32_t)(mw >> 32);
             const int nk = (int)(fl & 7u);
             const uint64_t off = (uint64_t)((st * STAGE_BYTES) >> 4);
-            for (int kk = 0; kk < nk; ++kk) {
-              uint64_t ad, bd;
-              uint32_t idk = id;
-              if constexpr (Cfg::PACK) {
-                // slot kk: A at kk * 4 KB, B at 16 KB + kk * 4 KB of the stage
-                ad = ad0 + off + (uint64_t)(kk * (TM_SLOT_A >> 4));
-                bd = bd0 + off + (uint64_t)(kk * (TM_SLOT_A >> 4));
-                idk |= ((fl >> (8 + kk)) & 1u) << 13;
-              } else {
-                ad = ad0 + off + (uint64_t)(kk * 2);
-                bd = bd0 + off + (uint64_t)(kk * 2);
+            // (packed) slot sl: A at sl * TM_SLOT_A, B at TM_PACK_SLOTS * TM_SLOT_A + sl *
+            // TM_SLOT_A of the stage, its K=16 steps 32 bytes apart along the row
+            const int nslot = Cfg::PACK ? nk : 1;
+            int m = 0;
+            for (int sl = 0; sl < nslot; ++sl) {
+              const int nks = Cfg::PACK ? (int)((fl >> (12 + 2 * sl)) & 3u) : nk;
+              const uint32_t idk = Cfg::PACK ? (id | (((fl >> (8 + sl)) & 1u) << 13)) : id;
+              const uint64_t so = Cfg::PACK ? (uint64_t)((sl * TM_SLOT_A) >> 4) : 0;
+              for (int kk = 0; kk < nks; ++kk, ++m) {
+                const uint64_t ad = ad0 + off + so + (uint64_t)(kk * 2), bd = bd0 + off + so + (uint64_t)(kk * 2);
+                const uint32_t accum = ((fl & 8u) && m == 0) ? 0u : 1u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dacc),
+                    "l"(ad), "l"(bd), "r"(idk), "r"(accum));
               }
-              const uint32_t accum = ((fl & 8u) && kk == 0) ? 0u : 1u;
-              asm volatile(
-                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dacc),
-                  "l"(ad), "l"(bd), "r"(idk), "r"(accum));
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                 smem_u32(&empty_b[st])));
@@ -671,7 +672,7 @@ cudaError_t launch_split_exact(const SplitJob* d_jobs, int njobs, int nsl, int* 
 }
 
 int tma_max_n(int mode) { return mode == TM_MODE_STORE_BF16 ? 256 : (mode == TM_MODE_EXACT_F64 ? 64 : 128); }
-int tma_box_cols(int mode) { return mode == TM_MODE_REDUCE_F32 ? 16 : TM_BOX_K; }
+int tma_box_cols(int mode) { return mode == TM_MODE_REDUCE_F32 ? TM_PACK_COLS : TM_BOX_K; }
 
 cudaError_t launch_gemm_tma(int mode, const TmTile* d_tiles, int ntiles, const TmTerm* d_terms,
                             const CUtensorMap* d_maps, const long* d_rowmap, const int2* d_cbtab, void* out,
@@ -724,7 +725,7 @@ __global__ void fill_lists_kernel(int mode, const TmTile* __restrict__ tiles, in
   const int ti = blockIdx.x * blockDim.x + threadIdx.x;
   if (ti >= ntiles) return;
   const bool pack = mode == TM_MODE_REDUCE_F32, exact = mode == TM_MODE_EXACT_F64;
-  const int bc = pack ? 16 : TM_BOX_K, P = pack ? TM_PACK_SLOTS : 1;
+  const int bc = pack ? TM_PACK_COLS : TM_BOX_K, P = pack ? TM_PACK_SLOTS : 1;
   const uint32_t a_box = 128u * bc * 2;
   const TmTile tl = tiles[ti];
   const uint32_t b_box = (uint32_t)tl.n * bc * 2;
@@ -732,7 +733,7 @@ __global__ void fill_lists_kernel(int mode, const TmTile* __restrict__ tiles, in
   long sidx = s0, left = 0;
   for (int t = tl.t0; t < tl.t1; ++t) left += term_pieces(terms[t], bc);
   int slot = 0, seg_pos = 0;
-  uint32_t negm = 0;
+  uint32_t negm = 0, nkm = 0;
   for (int t = tl.t0; t < tl.t1; ++t) {
     const TmTerm m = terms[t];
     const int nsl = max(1, (m.neg >> 4) & 15);
@@ -743,13 +744,14 @@ __global__ void fill_lists_kernel(int mode, const TmTile* __restrict__ tiles, in
           const int k0 = kk * bc;
           pieces[sidx * P + slot] = TmPiece{m.amap + i, m.ax + k0, m.ay, m.bmap + (l - i), m.bx + k0, m.by, 0, 0};
           negm |= (uint32_t)(m.neg & 1) << slot;
+          nkm |= (uint32_t)min(bc / 16, (m.k - k0) / 16) << (12 + 2 * slot);
           --left;
           const long np_here = min((long)P, (long)slot + 1 + left);  // this stage's pieces
           if (++slot < np_here) continue;
           const bool last = left == 0;
           uint32_t fl, id;
           if (pack) {
-            fl = (uint32_t)slot | (negm << 8);
+            fl = (uint32_t)slot | (negm << 8) | nkm;
             fl |= seg_pos == 0 ? 8u : 0u;
             fl |= (last || seg_pos == TM_SEG_KSTEPS - 1) ? 16u : 0u;
             id = tm_idesc_bf16(tl.n, false);
@@ -770,6 +772,7 @@ __global__ void fill_lists_kernel(int mode, const TmTile* __restrict__ tiles, in
           ++sidx;
           slot = 0;
           negm = 0;
+          nkm = 0;
           if (++seg_pos == TM_SEG_KSTEPS) seg_pos = 0;
         }
   }
@@ -824,14 +827,16 @@ bool encode_bf16_map(CUtensorMap* out, const void* base, uint64_t rows, uint64_t
                      uint32_t box_rows, uint32_t box_cols) {
   EncodeTiledFn fn = encoder();
   if (!fn || rows == 0 || cols == 0 || (ld * 2) % 16 != 0 || ((uintptr_t)base & 15) != 0 || box_rows == 0 ||
-      box_rows > 256 || (box_cols != 16 && box_cols != (uint32_t)TM_BOX_K))
+      box_rows > 256 || (box_cols != 16 && box_cols != 32 && box_cols != (uint32_t)TM_BOX_K))
     return false;
   const cuuint64_t dims[2] = {cols, rows};
   const cuuint64_t strides[1] = {ld * 2};
   const cuuint32_t box[2] = {box_cols, box_rows};
   const cuuint32_t estr[2] = {1, 1};
   return fn(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, box_cols == 16 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE,
+            box_cols == 16 ? CU_TENSOR_MAP_SWIZZLE_32B
+                           : (box_cols == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B),
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

@@ -33,10 +33,10 @@ struct TmTerm {
 
 // Output tile over the terms [t0, t1).  n: MMA width (multiple of 16, <= the
 // kernel's maximum).
-//   reduce mode (packed): the tensor maps of the tile's terms have boxes of 16 columns
-//     (32-byte swizzle), and a K step (stage) holds up to TM_PACK_SLOTS consecutive
-//     pieces of 16 columns of the tile (a term has k / 16 pieces per slice pair);
-//     pad = the tile's stages, ceil(pieces / TM_PACK_SLOTS).
+//   reduce mode (packed): the tensor maps of the tile's terms have boxes of TM_PACK_COLS
+//     columns, and a K step (stage) holds up to TM_PACK_SLOTS consecutive pieces of the
+//     tile (a term has ceil(k / TM_PACK_COLS) pieces per slice pair); pad = the tile's
+//     stages, ceil(pieces / TM_PACK_SLOTS).
 //   store mode (X intermediates, BF16): the output matrix is split by columns into
 //     column blocks, each its own row-major submatrix of xrows rows: block e of
 //     cbtab[cb0..cb1) = (first column c0, width w) starts at element
@@ -67,12 +67,13 @@ constexpr int TM_EXACT_BITS = 7;
 // K steps (stages of up to TM_PACK_SLOTS 16-column pieces) accumulated in tensor memory
 // before the reduce-mode epilogue takes the partial sum over
 constexpr int TM_SEG_KSTEPS = 16;
-constexpr int TM_PACK_SLOTS = 4;
+constexpr int TM_PACK_SLOTS = 4;  // pieces per stage of the reduce mode
+constexpr int TM_PACK_COLS = 16;  // their width (32-byte swizzled boxes), one K=16 instruction each
 
 // Copy lists.  The tiles' terms are expanded on the host into stages, each holding up
 // to tma_pieces(mode) pieces (a piece: one A box and one B box, both of tma_box_cols(mode)
 // columns; store and exact modes one piece of 64 columns, reduce mode up to
-// TM_PACK_SLOTS consecutive pieces of 16 columns).  A term expands into its slice pairs
+// TM_PACK_SLOTS consecutive pieces of TM_PACK_COLS columns).  A term expands into its slice pairs
 // (i, j), i + j < nsl, in the order of the level l = i + j (A map amap + i, B map
 // bmap + j), each into its boxes along K.  CTA c of a launch of `grid` CTAs takes the
 // tiles c, c + grid, ... and issues the stages [cta_stage[c], cta_stage[c + 1]), stage s
@@ -82,9 +83,10 @@ struct TmPiece {  // 32 bytes, so that any run of pieces is a bulk copy of 16-by
 };
 // word: the stage word the MMA issuer reads, the instruction descriptor (negation of A in
 // the store and exact modes) in the low half, in the high half the K=16 instructions
-// (store and exact modes; 1 per piece in the reduce mode) in bits 0-2, flags first of a
+// (store and exact modes; the pieces in the reduce mode) in bits 0-2, flags first of a
 // segment (bit 3), end of a segment (4), last stage of the tile (5), and in the reduce
-// mode the negation of slot p in bit 8 + p.  bytes: the stage's expected copy bytes.
+// mode the negation of slot p in bit 8 + p and its K=16 instructions in bits 12 + 2p and
+// 13 + 2p.  bytes: the stage's expected copy bytes.
 struct TmStage {
   uint64_t word;
   uint32_t bytes;
@@ -159,13 +161,14 @@ struct SplitJob {
 cudaError_t launch_split_exact(const SplitJob* d_jobs, int njobs, int nsl, int* d_expo, cudaStream_t s);
 // maximum MMA width of a mode (256 for the BF16 store mode, 128 for the reduce mode)
 int tma_max_n(int mode);
-// box width in columns of the tensor maps a mode reads (16 for the reduce mode, else 64)
+// box width in columns of the tensor maps a mode reads (TM_PACK_COLS for the reduce mode,
+// else 64)
 int tma_box_cols(int mode);
 
 // Host: encode a 2D BF16 tensor map over a row-major matrix (rows x cols, leading
 // dimension ld elements, ld * 2 a multiple of 16 bytes, base 16-byte aligned), box
-// of box_cols columns x box_rows rows: 64 columns with 128-byte swizzle or 16 columns
-// with 32-byte swizzle.  Returns false on failure.
+// of box_cols columns x box_rows rows: 64, 32 or 16 columns with 128-, 64- or 32-byte
+// swizzle.  Returns false on failure.
 bool encode_bf16_map(CUtensorMap* out, const void* base, uint64_t rows, uint64_t cols, uint64_t ld,
                      uint32_t box_rows, uint32_t box_cols = 64);
 
