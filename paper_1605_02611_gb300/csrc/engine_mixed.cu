@@ -761,25 +761,31 @@ struct TmaPlan {
   DArr<int2> cbtab;  // (first column, width) of the column blocks of every input group
   // device copies of a launch's copy lists
   struct Lists {
-    DArr<int> cta_stage;
-    DArr<long> tfirst;
+    DArr<int> cta_stage, sorder, tpiece0;
+    DArr<long> sfirst;
     DArr<TmStage> stages;
     DArr<TmPiece> pieces;
     int grid = 0;
+    long total = 0;
     // the stage counts on the host (reduce mode: sets the tiles' stages and segments,
     // so it comes before the tiles are uploaded); throws on a malformed term
     void plan(int mode, std::vector<TmTile>& tiles, const std::vector<TmTerm>& terms, cudaStream_t s) {
       TmListPlan lp;
       if (!tma_plan_lists(mode, tiles, terms, lp)) throw Error(ST_ECUDA, "internal: malformed TMA term list");
       grid = lp.grid;
+      total = lp.total;
       cta_stage.upload(lp.cta_stage, s);
-      tfirst.upload(lp.tfirst, s);
+      sorder.upload(lp.sorder, s);
+      sfirst.upload(lp.sfirst, s);
+      tpiece0.upload(lp.tpiece0, s);
       stages.alloc((size_t)std::max<long>(lp.total, 1), s);
       pieces.alloc((size_t)std::max<long>(lp.total, 1) * tma_pieces(mode), s);
     }
     // the lists themselves, on the device, from the uploaded tiles and terms
     void fill(int mode, const TmTile* d_tiles, int ntiles, const TmTerm* d_terms, cudaStream_t s) {
-      cuda_check(launch_fill_lists(mode, d_tiles, ntiles, d_terms, tfirst.p, stages.p, pieces.p, s), "list fill");
+      cuda_check(launch_fill_lists(mode, d_tiles, ntiles, d_terms, tpiece0.p, sorder.p, sfirst.p, total, stages.p,
+                                   pieces.p, s),
+                 "list fill");
     }
     TmListsDev dev() const { return {grid, cta_stage.p, stages.p, pieces.p}; }
   };

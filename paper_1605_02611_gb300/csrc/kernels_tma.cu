@@ -713,69 +713,84 @@ __host__ __device__ inline long term_pieces(const TmTerm& m, int bc) {
   return (long)((m.k + bc - 1) / bc) * (nsl * (nsl + 1) / 2);
 }
 
-// One thread per tile fills the tile's stages.  A term's pieces: its slice pairs (i, j),
-// i + j < nsl, in level order, each its boxes along K.  Segments: store mode one per
-// tile; reduce mode TM_SEG_KSTEPS stages each (the products accumulate in tensor memory
-// over a segment only and the epilogue adds the segments in FP32 with round-to-nearest,
-// so the rounding toward zero of the tensor-core accumulation acts on short sums);
-// exact mode one per level of every term.
+// One thread per stage.  It finds its tile (stages in the launch order: sorder[i] has
+// the stages from sfirst[i]) and the term of its first piece (tpiece0: a term's first
+// piece within its tile), then walks the stage's pieces: a term's pieces are its slice
+// pairs (i, j), i + j < nsl, in level order, each its boxes along K.  Segments: store mode
+// one per tile; reduce mode TM_SEG_KSTEPS stages each (the products accumulate in tensor
+// memory over a segment only and the epilogue adds the segments in FP32 with
+// round-to-nearest, so the rounding toward zero of the tensor-core accumulation acts on
+// short sums); exact mode one per level of every term.
 __global__ void fill_lists_kernel(int mode, const TmTile* __restrict__ tiles, int ntiles,
-                                  const TmTerm* __restrict__ terms, const long* __restrict__ tfirst,
+                                  const TmTerm* __restrict__ terms, const int* __restrict__ tpiece0,
+                                  const int* __restrict__ sorder, const long* __restrict__ sfirst, long total,
                                   TmStage* __restrict__ stages, TmPiece* __restrict__ pieces) {
-  const int ti = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ti >= ntiles) return;
+  const long g = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
   const bool pack = mode == TM_MODE_REDUCE_F32, exact = mode == TM_MODE_EXACT_F64;
   const int bc = pack ? TM_PACK_COLS : TM_BOX_K, P = pack ? TM_PACK_SLOTS : 1;
-  const uint32_t a_box = 128u * bc * 2;
-  const TmTile tl = tiles[ti];
-  const uint32_t b_box = (uint32_t)tl.n * bc * 2;
-  const long s0 = tfirst[ti];
-  long sidx = s0, left = 0;
-  for (int t = tl.t0; t < tl.t1; ++t) left += term_pieces(terms[t], bc);
-  int slot = 0, seg_pos = 0;
-  uint32_t negm = 0, nkm = 0;
-  for (int t = tl.t0; t < tl.t1; ++t) {
-    const TmTerm m = terms[t];
+  int lo = 0, hi = ntiles - 1;  // the last tile (in stage order) starting at or before g
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (sfirst[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  const TmTile tl = tiles[sorder[lo]];
+  const long sl = g - sfirst[lo];
+  const long nst = (lo + 1 < ntiles ? sfirst[lo + 1] : total) - sfirst[lo];
+  const long p0 = sl * P;
+  int t = tl.t0, th = tl.t1 - 1;  // the last term whose first piece is at or before p0
+  while (t < th) {
+    const int mid = (t + th + 1) >> 1;
+    if (tpiece0[mid] <= p0) t = mid; else th = mid - 1;
+  }
+  const long tile_pieces = tpiece0[tl.t1 - 1] + term_pieces(terms[tl.t1 - 1], bc);
+  const int np = (int)min((long)P, tile_pieces - p0);
+  const uint32_t a_box = 128u * bc * 2, b_box = (uint32_t)tl.n * bc * 2;
+  const bool last = sl == nst - 1;
+  TmTerm m = terms[t];
+  long r = p0 - tpiece0[t];
+  uint32_t negm = 0, nkm = 0, fl = 0, id = 0;
+  for (int slot = 0; slot < np; ++slot, ++r) {
+    if (r >= term_pieces(m, bc)) {
+      m = terms[++t];
+      r = 0;
+    }
     const int nsl = max(1, (m.neg >> 4) & 15);
     const int kp = (m.k + bc - 1) / bc;
-    for (int l = 0; l < nsl; ++l)
-      for (int i = 0; i <= l; ++i)
-        for (int kk = 0; kk < kp; ++kk) {
-          const int k0 = kk * bc;
-          pieces[sidx * P + slot] = TmPiece{m.amap + i, m.ax + k0, m.ay, m.bmap + (l - i), m.bx + k0, m.by, 0, 0};
-          negm |= (uint32_t)(m.neg & 1) << slot;
-          nkm |= (uint32_t)min(bc / 16, (m.k - k0) / 16) << (12 + 2 * slot);
-          --left;
-          const long np_here = min((long)P, (long)slot + 1 + left);  // this stage's pieces
-          if (++slot < np_here) continue;
-          const bool last = left == 0;
-          uint32_t fl, id;
-          if (pack) {
-            fl = (uint32_t)slot | (negm << 8) | nkm;
-            fl |= seg_pos == 0 ? 8u : 0u;
-            fl |= (last || seg_pos == TM_SEG_KSTEPS - 1) ? 16u : 0u;
-            id = tm_idesc_bf16(tl.n, false);
-          } else {
-            fl = (uint32_t)min(bc / 16, (m.k - k0) / 16);
-            if (exact) {
-              fl |= (i == 0 && kk == 0) ? 8u : 0u;
-              fl |= (i == l && kk == kp - 1) ? 16u : 0u;
-            } else {
-              fl |= sidx == s0 ? 8u : 0u;
-              fl |= last ? 16u : 0u;
-            }
-            id = tm_idesc_bf16(tl.n, (m.neg & 1) != 0);
-          }
-          fl |= last ? 32u : 0u;
-          stages[sidx] = TmStage{(uint64_t)id | ((uint64_t)fl << 32), (uint32_t)slot * (a_box + b_box), slot};
-          for (int p = slot; p < P; ++p) pieces[sidx * P + p] = TmPiece{0, 0, 0, 0, 0, 0, 0, 0};
-          ++sidx;
-          slot = 0;
-          negm = 0;
-          nkm = 0;
-          if (++seg_pos == TM_SEG_KSTEPS) seg_pos = 0;
-        }
+    int q = (int)(r / kp);
+    const int kk = (int)(r - (long)q * kp);
+    int l = 0;
+    while (q > l) {
+      q -= l + 1;
+      ++l;
+    }
+    const int i = q, k0 = kk * bc;
+    const int nk = min(bc / 16, (m.k - k0) / 16);
+    pieces[g * P + slot] = TmPiece{m.amap + i, m.ax + k0, m.ay, m.bmap + (l - i), m.bx + k0, m.by, 0, 0};
+    negm |= (uint32_t)(m.neg & 1) << slot;
+    nkm |= (uint32_t)nk << (12 + 2 * slot);
+    if (!pack) {
+      fl = (uint32_t)nk;
+      if (exact) {
+        fl |= (i == 0 && kk == 0) ? 8u : 0u;
+        fl |= (i == l && kk == kp - 1) ? 16u : 0u;
+      } else {
+        fl |= sl == 0 ? 8u : 0u;
+        fl |= last ? 16u : 0u;
+      }
+      id = tm_idesc_bf16(tl.n, (m.neg & 1) != 0);
+    }
   }
+  for (int p = np; p < P; ++p) pieces[g * P + p] = TmPiece{0, 0, 0, 0, 0, 0, 0, 0};
+  if (pack) {
+    const long seg_pos = sl % TM_SEG_KSTEPS;
+    fl = (uint32_t)np | (negm << 8) | nkm;
+    fl |= seg_pos == 0 ? 8u : 0u;
+    fl |= (last || seg_pos == TM_SEG_KSTEPS - 1) ? 16u : 0u;
+    id = tm_idesc_bf16(tl.n, false);
+  }
+  fl |= last ? 32u : 0u;
+  stages[g] = TmStage{(uint64_t)id | ((uint64_t)fl << 32), (uint32_t)np * (a_box + b_box), np};
 }
 }  // namespace
 
@@ -785,22 +800,31 @@ bool tma_plan_lists(int mode, std::vector<TmTile>& tiles, const std::vector<TmTe
   const int bc = tma_box_cols(mode), P = tma_pieces(mode);
   for (const TmTerm& m : terms)
     if (m.k < 16 || m.k % 16) return false;
+  // every term belongs to one tile; its first piece within the tile
+  out.tpiece0.assign(terms.size(), -1);
   std::vector<long> tst((size_t)ntiles);
   for (int ti = 0; ti < ntiles; ++ti) {
     const TmTile& tl = tiles[(size_t)ti];
     if (tl.t0 < 0 || tl.t1 <= tl.t0 || tl.t1 > (int)terms.size()) return false;
     long pc = 0;
-    for (int t = tl.t0; t < tl.t1; ++t) pc += term_pieces(terms[(size_t)t], bc);
+    for (int t = tl.t0; t < tl.t1; ++t) {
+      if (out.tpiece0[(size_t)t] >= 0 || pc >= (1L << 31)) return false;
+      out.tpiece0[(size_t)t] = (int)pc;
+      pc += term_pieces(terms[(size_t)t], bc);
+    }
     tst[(size_t)ti] = (pc + P - 1) / P;
   }
+  // stages in launch order: CTA c takes the tiles c, c + grid, ...
   out.grid = grid;
   out.cta_stage.assign((size_t)grid + 1, 0);
-  out.tfirst.assign((size_t)ntiles, 0);
+  out.sorder.clear();
+  out.sfirst.clear();
   long total = 0;
   for (int c = 0; c < grid; ++c) {
     out.cta_stage[(size_t)c] = (int)total;
     for (int ti = c; ti < ntiles; ti += grid) {
-      out.tfirst[(size_t)ti] = total;
+      out.sorder.push_back(ti);
+      out.sfirst.push_back(total);
       total += tst[(size_t)ti];
     }
     if (total >= (1L << 31) / P) return false;
@@ -815,11 +839,13 @@ bool tma_plan_lists(int mode, std::vector<TmTile>& tiles, const std::vector<TmTe
   return true;
 }
 
-cudaError_t launch_fill_lists(int mode, const TmTile* d_tiles, int ntiles, const TmTerm* d_terms, const long* d_tfirst,
-                              TmStage* d_stages, TmPiece* d_pieces, cudaStream_t s) {
-  if (ntiles <= 0) return cudaSuccess;
+cudaError_t launch_fill_lists(int mode, const TmTile* d_tiles, int ntiles, const TmTerm* d_terms, const int* d_tpiece0,
+                              const int* d_sorder, const long* d_sfirst, long total, TmStage* d_stages,
+                              TmPiece* d_pieces, cudaStream_t s) {
+  if (ntiles <= 0 || total <= 0) return cudaSuccess;
   count_tc_launches(1);
-  fill_lists_kernel<<<(ntiles + 127) / 128, 128, 0, s>>>(mode, d_tiles, ntiles, d_terms, d_tfirst, d_stages, d_pieces);
+  fill_lists_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(mode, d_tiles, ntiles, d_terms, d_tpiece0, d_sorder,
+                                                                    d_sfirst, total, d_stages, d_pieces);
   return cudaGetLastError();
 }
 

@@ -98,13 +98,16 @@ struct TmListsDev {  // device copies, kept alive by the caller for the launches
   const TmStage* stages = nullptr;
   const TmPiece* pieces = nullptr;
 };
-// host side of a launch's lists: its grid, every CTA's first stage (grid + 1 entries)
-// and every tile's first stage
+// host side of a launch's lists: its grid, every CTA's first stage (grid + 1 entries),
+// the tiles in stage order (sorder) with their first stages (sfirst), and every term's
+// first piece within its tile (tpiece0; a term belongs to one tile)
 struct TmListPlan {
   int grid = 0;
   long total = 0;
   std::vector<int> cta_stage;
-  std::vector<long> tfirst;
+  std::vector<int> sorder;
+  std::vector<long> sfirst;
+  std::vector<int> tpiece0;
 };
 
 // instruction descriptor of tcgen05.mma kind::f16: D FP32, A and B BF16, both K-major,
@@ -122,13 +125,15 @@ __host__ __device__ inline uint32_t tm_idesc_bf16(int n, bool negA) {
 
 // Host: the stage counts of a launch of `mode` over these tiles (for the grid the launch
 // will use, tma_grid(tiles.size())); reduce mode: sets every tile's pad (its stages) and
-// nseg.  Returns false if a term is malformed (k not a positive multiple of 16) or the
-// lists would be too long.
+// nseg.  Returns false if a term is malformed (k not a positive multiple of 16), belongs
+// to two tiles, or the lists would be too long.
 bool tma_plan_lists(int mode, std::vector<TmTile>& tiles, const std::vector<TmTerm>& terms, TmListPlan& out);
 // Device: fills the copy lists (stages: total entries, pieces: total * tma_pieces(mode)),
-// one thread per tile, from the tiles and terms the plan was made from (on the device).
-cudaError_t launch_fill_lists(int mode, const TmTile* d_tiles, int ntiles, const TmTerm* d_terms, const long* d_tfirst,
-                              TmStage* d_stages, TmPiece* d_pieces, cudaStream_t s);
+// one thread per stage, from the tiles and terms the plan was made from and the plan's
+// tpiece0, sorder and sfirst (all on the device).
+cudaError_t launch_fill_lists(int mode, const TmTile* d_tiles, int ntiles, const TmTerm* d_terms, const int* d_tpiece0,
+                              const int* d_sorder, const long* d_sfirst, long total, TmStage* d_stages,
+                              TmPiece* d_pieces, cudaStream_t s);
 // CTAs of a launch over ntiles tiles (min(ntiles, SMs of the current device))
 int tma_grid(int ntiles);
 int tma_pieces(int mode);
