@@ -1581,12 +1581,34 @@ double two_site_step(Context& c, int k, int dir, int M, const DavidsonOpts& o, b
   };
   // the side that the environment update does not use feeds only the sigma and the diagonal
   Tilde lt, rt;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cuda_check(cudaEventCreate(&ev0), "event");
+  cuda_check(cudaEventCreate(&ev1), "event");
+  cuda_check(cudaEventRecord(ev0, c.stream), "event");
   build_tilde_left(c, c.left[k], k, lt, dir == 1);
   build_tilde_right(c, c.right[k + 2], k + 1, rt, dir == 0);
-  lap(0);
+  cuda_check(cudaEventRecord(ev1, c.stream), "event");
+  const double f_tilde = c.other_flops_total + c.sigma_flops_total;
+  // no synchronisation here: the host part of the sigma plan overlaps the GPU work of the
+  // W-contracted sums (all device work is ordered on the context stream); the sums' phase
+  // time is their event time, the plan's the rest until the plan is on the device
   SigmaPlan plan;
   build_sigma_plan(c, lt, rt, k, plan);
-  lap(1);
+  {
+    auto t1 = now();
+    float ms = 0.f;
+    cuda_check(cudaEventElapsedTime(&ms, ev0, ev1), "event time");
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    const double total = std::chrono::duration<double>(t1 - t0).count(), tsum = std::min(total, 1e-3 * ms);
+    const double f1 = c.other_flops_total + c.sigma_flops_total;
+    c.phase_s[0] += tsum;
+    c.phase_flops[0] += f_tilde - f0;
+    c.phase_s[1] += total - tsum;
+    c.phase_flops[1] += f1 - f_tilde;
+    t0 = t1;
+    f0 = f1;
+  }
   DArr<double> psi, diag;
   psi.alloc(plan.psi.nnz, c.stream);
   diag.alloc(plan.psi.nnz, c.stream);
