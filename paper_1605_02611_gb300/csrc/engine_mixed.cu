@@ -11,15 +11,15 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
-#include <exception>
-#include <thread>
-#include <mutex>
 #include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <exception>
 #include <limits>
 #include <map>
+#include <mutex>
+#include <thread>
 #include <unordered_map>
 #include <unordered_set>
 
@@ -1410,28 +1410,61 @@ void build_tma_plan(Context& c, Tilde& lt, Tilde& rt, int k, SigmaPlan& plan, in
     };
     check_terms(t1, m1, n1max, bc1);
     check_terms(t2, m2, n2max, bc2);
-    for (const TmTile& tl : t1) {
-      if (tl.rowmap_off < 0 || tl.rowmap_off + 128 > (long)rowmap.size() || tl.cb0 < 0 || tl.cb1 > (int)cbtab.size() ||
-          tl.cb0 >= tl.cb1)
-        throw Error(ST_ECUDA, "internal: stage-1 row map or column blocks out of range");
-      long dmax = -1;
-      for (int r = 0; r < 128; ++r) {
-        const long d = rowmap[(size_t)(tl.rowmap_off + r)];
-        if (d < -1 || d >= tl.xrows) throw Error(ST_ECUDA, "internal: stage-1 row outside its X region");
-        dmax = std::max(dmax, d);
-      }
-      // every 8-column chunk of the tile lies in one column block; its highest row
-      // stays inside the buffer (addresses grow with the row)
-      for (int cc = 0; cc < tl.n; cc += 8) {
-        const long col = tl.out_off + cc;
-        int hit = -1;
-        for (int e = tl.cb0; e < tl.cb1; ++e)
-          if (col >= cbtab[e].x && col + 8 <= cbtab[e].x + cbtab[e].y) hit = e;
-        if (hit < 0) throw Error(ST_ECUDA, "internal: stage-1 column outside the column blocks");
-        const long a0 = tl.xbase + tl.xrows * cbtab[hit].x + (col - cbtab[hit].x);
-        if (a0 < 0 || a0 % 8 || cbtab[hit].y % 8 || (dmax >= 0 && a0 + dmax * cbtab[hit].y + 8 > tp->x_stride))
-          throw Error(ST_ECUDA, "internal: stage-1 store outside the X buffer");
-      }
+    {
+      // the column blocks of every input group in increasing, disjoint column order, so
+      // that a chunk's block is found by binary search (the kernel takes the one block
+      // that holds the chunk)
+      for (int gp = 0; gp < ng; ++gp)
+        for (int e = cbt0[gp] + 1; e < cbt1[gp]; ++e)
+          if (cbtab[(size_t)e].x < cbtab[(size_t)e - 1].x + cbtab[(size_t)e - 1].y)
+            throw Error(ST_ECUDA, "internal: overlapping column blocks");
+      std::atomic<int> bad{0}, next{0};
+      auto check_range = [&]() {
+        for (int i0 = next.fetch_add(1024); i0 < (int)t1.size() && !bad.load(); i0 = next.fetch_add(1024))
+          for (int ti = i0; ti < std::min<int>((int)t1.size(), i0 + 1024); ++ti) {
+            const TmTile& tl = t1[(size_t)ti];
+            if (tl.rowmap_off < 0 || tl.rowmap_off + 128 > (long)rowmap.size() || tl.cb0 < 0 ||
+                tl.cb1 > (int)cbtab.size() || tl.cb0 >= tl.cb1) {
+              bad = 1;  // row map or column blocks out of range
+              return;
+            }
+            long dmax = -1;
+            for (int r = 0; r < 128; ++r) {
+              const long d = rowmap[(size_t)(tl.rowmap_off + r)];
+              if (d < -1 || d >= tl.xrows) {
+                bad = 2;  // row outside its X region
+                return;
+              }
+              dmax = std::max(dmax, d);
+            }
+            // every 8-column chunk of the tile lies in one column block; its highest row
+            // stays inside the buffer (addresses grow with the row)
+            for (int cc = 0; cc < tl.n; cc += 8) {
+              const long col = tl.out_off + cc;
+              int lo = tl.cb0, hi = tl.cb1 - 1;  // the last block starting at or before col
+              while (lo < hi) {
+                const int mid = (lo + hi + 1) / 2;
+                if (cbtab[(size_t)mid].x <= col) lo = mid; else hi = mid - 1;
+              }
+              const int2 cb = cbtab[(size_t)lo];
+              if (!(col >= cb.x && col + 8 <= cb.x + cb.y)) {
+                bad = 3;  // column outside the column blocks
+                return;
+              }
+              const long a0 = tl.xbase + tl.xrows * cb.x + (col - cb.x);
+              if (a0 < 0 || a0 % 8 || cb.y % 8 || (dmax >= 0 && a0 + dmax * cb.y + 8 > tp->x_stride)) {
+                bad = 4;  // store outside the X buffer
+                return;
+              }
+            }
+          }
+      };
+      const int nth = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+      std::vector<std::thread> th;
+      for (int w = 1; w < nth; ++w) th.emplace_back(check_range);
+      check_range();
+      for (auto& x : th) x.join();
+      if (bad) throw Error(ST_ECUDA, "internal: stage-1 tile check failed (" + std::to_string(bad.load()) + ")");
     }
     for (const TmTile& tl : t2) {
       const long stages = packed_stages(m2, tl.t0, tl.t1);
