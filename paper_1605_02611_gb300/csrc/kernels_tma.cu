@@ -1,31 +1,34 @@
 // TMA-staged tensor-core grouped GEMM (tcgen05, sm_103a): BF16 operands, FP32
 // accumulation in tensor memory.
 //
-// The operands of the single-pass sigma vector live in a few large row-major
-// BF16 matrices (per quantum-number group of the cut: the stacked two-site
-// wavefunction Psi_g, the stacked right operators, the X intermediates; one
-// matrix for all left-operator blocks), each described by one tensor map.  A
-// K step of a tile is then two TMA box copies (A: 128 rows x 64 columns, B: n
-// rows x 64 columns, 128-byte swizzle, zero fill outside the matrix) that
-// complete on the stage's mbarrier by transaction count: no producer threads
-// copy data, and a ragged edge costs nothing but the zero fill.
+// The operands of the sigma vector live in a few large row-major BF16 matrices (per
+// quantum-number group of the cut: the stacked two-site wavefunction Psi_g, the stacked
+// right operators, the X intermediates; one matrix for all left-operator blocks), each
+// described by one tensor map.  A stage of the ring is one or more pieces, each a pair of
+// TMA box copies (A: 128 rows, B: n rows; 64 columns with 128-byte swizzle, or in the
+// reduce mode up to four 16-column pieces with 32-byte swizzle) that complete on the
+// stage's mbarrier by transaction count; zero fill outside the matrix covers ragged edges.
+// The tiles' terms are expanded before the launch into per-CTA copy lists (stage word,
+// expected bytes, box coordinates: fill_lists_kernel), so the producer does no term
+// arithmetic.
 //
-// Persistent and warp-specialised, one CTA per SM (192 KB shared memory ring,
+// Persistent and warp-specialised, one CTA per SM (up to 212 KB of shared memory,
 // all 512 tensor-memory columns):
-//   warp 0     one thread: waits for a free stage, posts the expected bytes and
-//              the stage's MMA parameters, issues the two box copies
-//   warp 1     one thread issues tcgen05.mma (M = 128, N = n, K = 16 per
-//              instruction; instructions past the term's K are skipped) and
-//              commits to the stage's empty barrier / the accumulator's full
+//   warp 0     fetches its CTA's copy lists 32 stages at a time into shared memory
+//              (1D bulk copies, double-buffered); per stage lane 0 waits for the ring
+//              slot and posts the stage word and the expected bytes, then lane p issues
+//              the two box copies of piece p
+//   warp 1     one thread issues tcgen05.mma (M = 128, N = n, K = 16 per instruction)
+//              and commits to the stage's empty barrier / the accumulator's full
 //              barrier
 //   warps 2-5  epilogue: tcgen05.ld of their 32 tensor-memory lanes; BF16 rows
-//              (X intermediates, up to three slices) staged in shared memory and
-//              written row by row with coalesced stores to the rows a row map
-//              gives, or FP32 vector reductions (sigma^T, several tiles may add
-//              into one block) of per-segment partial sums
-// Two (store mode, N <= 256) or four (reduce mode, N <= 128) accumulators let
-// the epilogue of one tile overlap the MMAs of the next.  Every wait is
-// bounded: on timeout the CTA raises a shared abort flag, records an error,
+//              (X intermediates, up to three slices) written with 16-byte stores to
+//              the rows a row map gives, FP32 vector reductions (sigma^T, several
+//              tiles may add into one block) of per-segment partial sums, or (exact
+//              mode) two-float sums of exact integer segments stored in FP64
+// Two (store mode, N <= 256), four (reduce mode, N <= 128) or eight (exact mode, N <=
+// 64) accumulators let the epilogue of one tile overlap the MMAs of the next.  Every
+// wait is bounded: on timeout the CTA raises a shared abort flag, records an error,
 // waits (bounded) for the copies it issued, frees its tensor memory and returns.
 #include "kernels_tma.hpp"
 
